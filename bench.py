@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of Slim Graph Triangle p-1-Reduction + CSR rebuild on GB300.
+
+Workload (default): R-MAT scale 22, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
+seed 1, symmetrised uint32 CSR with int64 offsets; one step = one
+compress(G, edge-once TR, p = 0.5) -> H: degree-ordered orientation, triangle
+enumeration with the edge-once reservation rounds, mask resolution and the
+stream-compacted CSR rebuild.  Metric: input (undirected) edges per second.
+
+The JSON line also carries: the roofline of the dominant kernel (measured live
+with CUDA events on the library's stream), the end-to-end number through the
+C-ABI with host buffers, the oracle timed on the host cores, SM clocks sampled
+during the timed region, and per-row timings of the other kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+    "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+    "rmat14": dict(scale=14, ef=16, desc="R-MAT scale 14, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+}
+METRIC = "input edges/s compressed (TR + CSR rebuild)"
+CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than scale 22
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1])]
+        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def byte_model(n, m, A_out, probes_total, launches, kernel):
+    """Algorithmic bytes of one launch of a named kernel."""
+    A = 2 * m
+    if kernel == "tri_enum":
+        # off+ (8 B/vertex), N+(u) lists (4 B/arc), off+ pair of every v (8 B/arc),
+        # one 4-byte read per probe (W = sum over u->v of d+(v))
+        return (8 * (n + 1) + 4 * m + 8 * m) + 4.0 * probes_total / max(launches, 1)
+    if kernel == "compact_orient":
+        return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * m + A / 8
+    if kernel == "compact_trmask":
+        return 8 * (n + 1) + 4 * A + A / 8 + 4 * m + A + 8 * (n + 1) + 4 * A_out
+    return None
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_1912_08950_gb300 as sg
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WORKLOADS[args.workload]
+    seed = 1 + rank  # independent replica per GPU; rank 0 is the named workload
+    g = gg.rmat(wl["scale"], wl["ef"], seed=seed, device="cuda")
+    ctx = sg.Context(local)
+    G = sg.Graph.from_csr(ctx, g, copy=True)
+    n, m = G.n, G.m
+    work = sg.tr_work(G)
+
+    def step():
+        H = sg.compress(G, args.kernel, args.p, 1)
+        a = H.nnz
+        H.free()
+        return a
+
+    for _ in range(args.warmup):
+        A_out = step()
+    ctx.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ctx.stats(reset=True)
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    stream = ctx.torch_stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        A_out = step()
+    ev1.record(stream)
+    barrier()
+    clocks.stop()
+    ctx.set_profiling(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    st = ctx.stats()
+    kt = {}
+    for name in ("tri_light", "tri_heavy", "tri_eo_accept", "tri_classify", "compact_orient", "compact_trmask",
+                 "row_maps"):
+        kt[name] = ctx.kernel_time(name)
+    enum_ms = kt["tri_light"][0] + kt["tri_heavy"][0]
+    enum_launches = max(kt["tri_light"][1], 1)  # one enumeration pass = light + heavy launch
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    hbm, peak_src = peaks()
+    cand = {
+        "tri_enum": (enum_ms, enum_launches, byte_model(n, m, A_out, st["probes"], enum_launches, "tri_enum")),
+        "compact_orient": (kt["compact_orient"][0], kt["compact_orient"][1],
+                           byte_model(n, m, A_out, 0, 1, "compact_orient")),
+        "compact_trmask": (kt["compact_trmask"][0], kt["compact_trmask"][1],
+                           byte_model(n, m, A_out, 0, 1, "compact_trmask")),
+    }
+    dom = max(cand, key=lambda k: cand[k][0])
+    d_ms, d_launch, d_bytes = cand[dom]
+    per_launch_s = d_ms / max(d_launch, 1) / 1e3
+    achieved = d_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+
+    # other rows of the hot path, timed once each (not part of the metric)
+    rows = {}
+    for kern, p in (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5)):
+        for _ in range(2):
+            sg.compress(G, kern, p, 1).free()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            sg.compress(G, kern, p, 1).free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows[kern] = {"ms": e0.elapsed_time(e1) / 3, "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
+    H = sg.compress(G, args.kernel, args.p, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    div = sg.divergence(G, H)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rows["divergence"] = {"ms": e0.elapsed_time(e1), "kl_bits": div["kl_bits"], "cc_g": div["cc_g"],
+                          "cc_h": div["cc_h"]}
+    H.free()
+
+    # end to end through the C-ABI with pinned host buffers
+    off_h = g.off.cpu().pin_memory()
+    col_h = g.col.cpu().pin_memory()
+    out_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    out_col = torch.empty(max(2 * m, 1), dtype=torch.int32).pin_memory()
+    L = sg.lib()
+    import ctypes
+
+    def e2e_step():
+        h = ctypes.c_void_p()
+        sg._check(L.sg_graph_from_host(ctx.handle, n, 2 * m, off_h.data_ptr(), col_h.data_ptr(), None,
+                                       ctypes.byref(h)))
+        gi = sg.Graph(ctx, h)
+        H = sg.compress(gi, args.kernel, args.p, 1)
+        sg._check(L.sg_graph_download(ctx.handle, H.handle, out_off.data_ptr(), out_col.data_ptr(), None))
+        nnz_out = H.nnz
+        H.free()
+        gi.free()
+        return nnz_out
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        nnz_out = e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    cpu = cpu_baseline(args) if rank == 0 and not args.no_cpu else None
+    clk = clocks.summary()
+    res = {
+        "metric": METRIC,
+        "value": world * m / (ms / 1e3),
+        "unit": "edges/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "n": n, "m": m,
+                   "arcs": 2 * m, "triangles": work["triangles"], "probes_per_pass": work["probes"],
+                   "max_out_degree": work["max_out_degree"], "kept_arcs": int(A_out),
+                   "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": d_bytes,
+                     "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "eo_rounds_per_step": st["eo_rounds"] / args.steps,
+        "gpu_launches": st["kernel_launches"],
+        "clocks": clk,
+        "e2e": {"value": world * m / e2e_s, "unit": "edges/s",
+                "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
+                "d2h_bytes_per_step": 8 * (n + 1) + 4 * int(nnz_out)},
+        "rows": rows,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    G.free()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(kernel, p):
+    """One bounded oracle run: the same generator at scale 16 (a 64x smaller sample)."""
+    import graphgen as gg
+    import oracle
+
+    g = gg.rmat(CPU_SAMPLE_SCALE, 16, seed=1)
+    t0 = time.perf_counter()
+    oracle.compress(g, kernel, p, 1)
+    dt = time.perf_counter() - t0
+    return g.m, dt
+
+
+def cpu_baseline(args):
+    m, dt = _oracle_sample(args.kernel, args.p)
+    return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {CPU_SAMPLE_SCALE}, edge factor 16, seed 1 ({m} edges), "
+                      f"{args.kernel} p={args.p}; single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        _oracle_sample(args.kernel, args.p)
+    tot_m, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        m, dt = _oracle_sample(args.kernel, args.p)
+        tot_m += m
+        tot_s += dt
+    v = tot_m / tot_s
+    wl = WORKLOADS[args.workload]
+    sample = (f"R-MAT scale {CPU_SAMPLE_SCALE}, edge factor 16, seed 1 per step, {args.kernel} p={args.p}; "
+              "single-threaded C oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22")
+    ap.add_argument("--kernel", default="tr_eo")
+    ap.add_argument("--p", type=float, default=0.5)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * slimgraph.h -- C ABI of the GB300 (sm_103a) Slim Graph compression library.
+ *
+ * Slim Graph (Besta et al., arXiv 1912.08950) compresses a graph lossily by
+ * running small "compression kernels" over its edges or triangles (Sec. 3.1,
+ * Sec. 4.1, Listing 1) in one concurrent pass (Listing 2: run_kernels once for
+ * every scheme except summarisation), and judges the result with accuracy
+ * metrics such as the KL divergence of PageRank distributions (Sec. 5.2.3).
+ * This library implements that data-parallel hot path with hand-written CUDA
+ * kernels: compress(graph, kernel, p, seed) -> graph, and divergence(G, H).
+ *
+ * Conventions shared by every entry point
+ *  - Graphs are undirected, simple and stored as a symmetric CSR: row offsets
+ *    off[n+1] (int64, off[0] = 0, non-decreasing), column ids col[nnz]
+ *    (uint32, each row strictly increasing, no self-loops, every arc (x,y)
+ *    matched by (y,x)), optional weights w[nnz] (float32, equal on both arcs
+ *    of an edge).  nnz = 2m arcs for m undirected edges.  n < 2^32.
+ *  - "device" pointers are CUDA global-memory addresses on the context's
+ *    device; "host" pointers are ordinary CPU memory (pinned memory makes the
+ *    copies faster but is not required).
+ *  - Every call returns an sg_status.  Nothing throws, traps or aborts; on a
+ *    non-OK status sg_last_error() returns a message for the calling thread.
+ *  - All device work is ordered on the context's stream.  Calls that return
+ *    results to the host (counts, sizes, scalars) synchronise that stream.
+ *  - Randomness: every decision draws Philox4x32-10 (Salmon et al., SC'11)
+ *    keyed by the 64-bit seed (key = low word, high word).  An edge {lo<hi}
+ *    uses counter (lo, hi, 0, 0x45444745); a triangle {a<b<c} uses counter
+ *    (a, b, c, 0x54524931).  A probability p becomes the threshold
+ *    floor(p * 2^32) and an event fires iff a 32-bit draw is below it.  Keys
+ *    are original vertex ids, so results do not depend on launch shape.
+ */
+#ifndef SLIMGRAPH_H
+#define SLIMGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sg_status {
+    SG_OK = 0,
+    SG_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter (p outside [0,1], NaN, ...) */
+    SG_ERR_INVALID_GRAPH = 2, /* CSR fails validation (only checked when asked) */
+    SG_ERR_NEEDS_WEIGHTS = 3, /* a max-weight kernel on an unweighted graph */
+    SG_ERR_OOM = 4,           /* device allocation failed */
+    SG_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    SG_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired; outputs are invalid */
+    SG_ERR_UNSUPPORTED = 7    /* outside the supported envelope (n >= 2^32, ...) */
+} sg_status;
+
+/*
+ * Compression kernels (Listing 1; Table 4).
+ *  SG_UNIFORM          random_uniform(E e): each edge stays with probability p
+ *                      (Sec. 4.2.2).
+ *  SG_SPECTRAL_LOGN    spectral_sparsify(E e) with Y = p ln n (Sec. 4.2.1):
+ *                      edge (u,v) stays with probability min(1, Y/min(d_u,d_v));
+ *                      kept edges get weight 1/p_uv when weights are wanted.
+ *  SG_SPECTRAL_AVGDEG  the same with Y = p m / n.
+ *  SG_TR_RANDOM        Triangle p-1-Reduction (Sec. 4.3): every triangle of the
+ *                      input is selected with probability p and deletes one
+ *                      uniformly chosen edge; deletions accumulate (union).
+ *  SG_TR_MAXW          as SG_TR_RANDOM, deleting the heaviest edge of each
+ *                      selected triangle (ties by endpoint pair); keeps the
+ *                      MST weight and the connected components (Sec. 4.3, 6).
+ *  SG_TR_EO            Edge-Once p-1-TR (Sec. 4.3; Sec. 6): only edge-disjoint
+ *                      triangles are considered -- selected triangles in order
+ *                      of (r2, a, b, c), each accepted iff none of its edges was
+ *                      already considered; keeps the connected components.
+ *  SG_TR_EO_MAXW       Edge-Once with the max-weight choice.
+ */
+typedef enum sg_kernel {
+    SG_UNIFORM = 0,
+    SG_SPECTRAL_LOGN = 1,
+    SG_SPECTRAL_AVGDEG = 2,
+    SG_TR_RANDOM = 3,
+    SG_TR_MAXW = 4,
+    SG_TR_EO = 5,
+    SG_TR_EO_MAXW = 6
+} sg_kernel;
+
+/* Opaque context: device, stream, device error word, launch statistics. */
+typedef struct sg_ctx sg_ctx;
+/* Opaque device-resident CSR graph, owned by the library unless borrowed. */
+typedef struct sg_graph sg_graph;
+
+/* Borrowed view of a device CSR (all pointers are device pointers). */
+typedef struct sg_csr_view {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *off;
+    const uint32_t *col;
+    const float *w; /* may be NULL */
+} sg_csr_view;
+
+/* Result of the accuracy analytics of one compression (Sec. 5). */
+typedef struct sg_div_result {
+    double kl_bits;       /* D_KL(PR_G || PR_H) in bits (Sec. 5.2.3) */
+    int64_t cc_g, cc_h;   /* connected components of G and H (Table 1) */
+    int64_t m_g, m_h;     /* undirected edge counts of G and H */
+    double pr_residual_g; /* FP64 L1 norm of the last PageRank update of G */
+    double pr_residual_h; /* ... of H */
+} sg_div_result;
+
+/* Launch accounting of a context (for benchmarks and profiles). */
+typedef struct sg_stats {
+    uint64_t kernel_launches; /* kernels this library launched on the context */
+    uint64_t probes;          /* wedge-closing probes done by triangle kernels */
+    uint64_t triangles;       /* triangles found by triangle kernels */
+    uint64_t eo_rounds;       /* Edge-Once reservation rounds run */
+} sg_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller (NULL: the library creates and owns a stream).  The
+ * context must outlive every graph created through it.
+ * Errors: SG_ERR_INVALID_ARG (out == NULL), SG_ERR_CUDA. */
+sg_status sg_ctx_create(int device, void *cuda_stream, sg_ctx **out);
+/* Destroy a context (synchronises its stream first).  NULL is ignored. */
+void sg_ctx_destroy(sg_ctx *ctx);
+/* Block until all work queued on the context's stream has finished. */
+sg_status sg_ctx_synchronize(sg_ctx *ctx);
+/* Read (and optionally reset) the launch accounting of the context. */
+sg_status sg_ctx_stats(sg_ctx *ctx, sg_stats *out, int reset);
+/* Per-kernel timing: when on, every launch is bracketed by CUDA events on the
+ * context stream.  sg_ctx_kernel_time returns the summed device time (ms) and
+ * launch count of kernels whose name starts with `prefix` since the last reset. */
+sg_status sg_ctx_set_profiling(sg_ctx *ctx, int on);
+sg_status sg_ctx_kernel_time(sg_ctx *ctx, const char *prefix, double *ms, int64_t *launches);
+sg_status sg_ctx_reset_profile(sg_ctx *ctx);
+
+/* ----------------------------------------------------------------- graphs */
+
+/* Wrap or copy a device CSR.  copy = 0 borrows the caller's buffers (they must
+ * stay alive and unchanged until sg_graph_free); copy = 1 makes library-owned
+ * copies.  validate = 1 checks the CSR conventions above on the device and
+ * returns SG_ERR_INVALID_GRAPH on a violation.
+ * Errors: SG_ERR_INVALID_ARG, SG_ERR_UNSUPPORTED (n >= 2^32), SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_graph_from_device(sg_ctx *ctx, const sg_csr_view *in, int copy, int validate, sg_graph **out);
+/* Copy a host CSR to the device (library-owned).  w may be NULL. */
+sg_status sg_graph_from_host(sg_ctx *ctx, int64_t n, int64_t nnz, const int64_t *off, const uint32_t *col,
+                             const float *w, sg_graph **out);
+/* Borrow the device pointers of a graph (valid until sg_graph_free). */
+sg_status sg_graph_view(const sg_graph *g, sg_csr_view *out);
+/* Copy a graph to caller-owned host buffers off[n+1], col[nnz] and, if the
+ * graph is weighted and w != NULL, w[nnz].  Synchronises the stream. */
+sg_status sg_graph_download(sg_ctx *ctx, const sg_graph *g, int64_t *off, uint32_t *col, float *w);
+/* Free a graph (stream-ordered on the context stream).  NULL is ignored. */
+void sg_graph_free(sg_graph *g);
+
+/* ------------------------------------------------------------ compression */
+
+/* compress(G, kernel, p, seed) -> H  (Listing 1 kernels, one run_kernels pass,
+ * Listing 2).  H is a new library-owned graph with the same n whose edge set is
+ * a subset of G's; G is never modified (the paper's SG.del mutates in place).
+ * Weights of H: the spectral kernels with want_weights = 1 produce 1/p_uv
+ * (Sec. 4.2.1); otherwise the input weights of the kept edges are carried.
+ * Errors: SG_ERR_INVALID_ARG (p not in [0,1] or NaN, bad kernel),
+ * SG_ERR_NEEDS_WEIGHTS, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT. */
+sg_status sg_compress(sg_ctx *ctx, const sg_graph *g, sg_kernel kernel, double p, uint64_t seed,
+                      int want_weights, sg_graph **out);
+
+/* ------------------------------------------------------------- analytics */
+
+/* divergence(G, H): PageRank of both graphs (damping, iters; FP32 values,
+ * deterministic order), KL divergence of the two distributions summed in FP64
+ * (Sec. 5.2.3), and the connected-component counts (Table 1).  Graphs are
+ * treated as unweighted.  G and H must have the same n. */
+sg_status sg_divergence(sg_ctx *ctx, const sg_graph *g, const sg_graph *h, float damping, int iters,
+                        sg_div_result *out);
+/* PageRank (Table 1): x0 = 1/n, x' = (1-d)/n + d (sum_{u in N(v)} x_u/d_u + D/n),
+ * D = rank held by degree-0 vertices.  x_out: device float[n].  residual_out
+ * (may be NULL): FP64 L1 norm of the last update. */
+sg_status sg_pagerank(sg_ctx *ctx, const sg_graph *g, float damping, int iters, float *x_out,
+                      double *residual_out);
+/* D_KL(P || Q) = sum_i P_i log2(P_i / Q_i) of two device float[n] vectors,
+ * each normalised by its FP64 sum (Sec. 5.2.3). */
+sg_status sg_kl_divergence(sg_ctx *ctx, int64_t n, const float *P, const float *Q, double *kl_out);
+/* Number of connected components (isolated vertices count).  labels_out: a
+ * device uint32[n] receiving the smallest vertex id of each component, or NULL. */
+sg_status sg_cc_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out, uint32_t *labels_out);
+/* Number of triangles of G (each counted once), with the degree-ordered
+ * enumeration used by the TR kernels. */
+sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out);
+/* Work model of the degree-ordered enumeration of G: m, the probe count
+ * W = sum over oriented arcs u->v of d+(v), the maximum out-degree and the
+ * triangle count.  Used to turn kernel times into algorithmic bytes. */
+sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out,
+                     int64_t *max_out_degree, int64_t *triangles_out);
+
+/* Message describing the last non-OK status returned on this thread. */
+const char *sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLIMGRAPH_H */

@@ -1,0 +1,266 @@
+"""Slim Graph lossy graph compression on one GB300 (sm_103a).
+
+A thin ctypes binding over ``libslimgraph.so`` (declared in
+``include/slimgraph.h``).  Every step of compression and analytics runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch is used
+for device memory and streams.  There is no CPU fallback: if the library has
+not been built, importing this package raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libslimgraph.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = C.CDLL(LIB_PATH)
+
+SG_OK, SG_ERR_INVALID_ARG, SG_ERR_INVALID_GRAPH, SG_ERR_NEEDS_WEIGHTS, SG_ERR_OOM, SG_ERR_CUDA, \
+    SG_ERR_TIMEOUT, SG_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_INVALID_GRAPH", 3: "SG_ERR_NEEDS_WEIGHTS",
+                4: "SG_ERR_OOM", 5: "SG_ERR_CUDA", 6: "SG_ERR_TIMEOUT", 7: "SG_ERR_UNSUPPORTED"}
+
+KERNELS = {"uniform": 0, "spectral_logn": 1, "spectral_avgdeg": 2, "tr_random": 3, "tr_maxw": 4,
+           "tr_eo": 5, "tr_eo_maxw": 6}
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CsrView(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("off", C.c_void_p), ("col", C.c_void_p),
+                ("w", C.c_void_p)]
+
+
+class DivResult(C.Structure):
+    _fields_ = [("kl_bits", C.c_double), ("cc_g", C.c_int64), ("cc_h", C.c_int64), ("m_g", C.c_int64),
+                ("m_h", C.c_int64), ("pr_residual_g", C.c_double), ("pr_residual_h", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("probes", C.c_uint64), ("triangles", C.c_uint64),
+                ("eo_rounds", C.c_uint64)]
+
+
+_vp, _i64, _u64, _int, _dbl, _flt = C.c_void_p, C.c_int64, C.c_uint64, C.c_int, C.c_double, C.c_float
+_PP = C.POINTER(C.c_void_p)
+_SIGS = {
+    "sg_ctx_create": [_int, _vp, _PP],
+    "sg_ctx_synchronize": [_vp],
+    "sg_ctx_stats": [_vp, C.POINTER(Stats), _int],
+    "sg_ctx_set_profiling": [_vp, _int],
+    "sg_ctx_kernel_time": [_vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+    "sg_ctx_reset_profile": [_vp],
+    "sg_graph_from_device": [_vp, C.POINTER(CsrView), _int, _int, _PP],
+    "sg_graph_from_host": [_vp, _i64, _i64, _vp, _vp, _vp, _PP],
+    "sg_graph_view": [_vp, C.POINTER(CsrView)],
+    "sg_graph_download": [_vp, _vp, _vp, _vp, _vp],
+    "sg_compress": [_vp, _vp, _int, _dbl, _u64, _int, _PP],
+    "sg_divergence": [_vp, _vp, _vp, _flt, _int, C.POINTER(DivResult)],
+    "sg_pagerank": [_vp, _vp, _flt, _int, _vp, C.POINTER(C.c_double)],
+    "sg_kl_divergence": [_vp, _i64, _vp, _vp, C.POINTER(C.c_double)],
+    "sg_cc_count": [_vp, _vp, C.POINTER(C.c_int64), _vp],
+    "sg_triangle_count": [_vp, _vp, C.POINTER(C.c_int64)],
+    "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                   C.POINTER(C.c_int64)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _int
+_lib.sg_ctx_destroy.argtypes = [_vp]
+_lib.sg_ctx_destroy.restype = None
+_lib.sg_graph_free.argtypes = [_vp]
+_lib.sg_graph_free.restype = None
+_lib.sg_last_error.argtypes = []
+_lib.sg_last_error.restype = C.c_char_p
+
+
+def lib():
+    """The loaded ctypes library (for callers that want the raw C-ABI)."""
+    return _lib
+
+
+def _check(st: int):
+    if st != SG_OK:
+        raise SgError(st, (_lib.sg_last_error() or b"").decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+class Context:
+    """A device, a stream and the library's per-context state."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.torch_stream = stream
+        h = C.c_void_p()
+        _check(_lib.sg_ctx_create(device, C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.sg_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        _check(_lib.sg_ctx_synchronize(self.handle))
+
+    def stats(self, reset: bool = False) -> dict:
+        s = Stats()
+        _check(_lib.sg_ctx_stats(self.handle, C.byref(s), int(reset)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_profiling(self, on: bool):
+        _check(_lib.sg_ctx_set_profiling(self.handle, int(on)))
+
+    def kernel_time(self, prefix: str):
+        ms, n = C.c_double(), C.c_int64()
+        _check(_lib.sg_ctx_kernel_time(self.handle, prefix.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def reset_profile(self):
+        _check(_lib.sg_ctx_reset_profile(self.handle))
+
+
+class Graph:
+    """A device-resident symmetric CSR owned (or borrowed) by the library."""
+
+    def __init__(self, ctx: Context, handle, keepalive=None):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keepalive
+        v = CsrView()
+        _check(_lib.sg_graph_view(self.handle, C.byref(v)))
+        self.n, self.nnz = v.n, v.nnz
+        self.weighted = bool(v.w)
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+    @classmethod
+    def from_host(cls, ctx: Context, n: int, off: np.ndarray, col: np.ndarray, w: Optional[np.ndarray] = None):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        col = np.ascontiguousarray(col).view(np.uint32)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        h = C.c_void_p()
+        _check(_lib.sg_graph_from_host(ctx.handle, n, col.size, _ptr(off), _ptr(col), _ptr(w), C.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def from_tensors(cls, ctx: Context, n: int, off, col, w=None, copy: bool = False, validate: bool = False):
+        """Wrap (copy=False) or copy CUDA tensors: off int64[n+1], col int32/uint32[nnz], w float32[nnz]."""
+        v = CsrView(n, col.numel(), off.data_ptr(), col.data_ptr(), None if w is None else w.data_ptr())
+        h = C.c_void_p()
+        _check(_lib.sg_graph_from_device(ctx.handle, C.byref(v), int(copy), int(validate), C.byref(h)))
+        return cls(ctx, h, keepalive=None if copy else (off, col, w))
+
+    @classmethod
+    def from_csr(cls, ctx: Context, g, copy: bool = True, validate: bool = False):
+        """From a graphgen.CSR (on any device)."""
+        import torch
+
+        dev = torch.device("cuda", ctx.device)
+        off, col = g.off.to(dev).contiguous(), g.col.to(dev).contiguous()
+        w = None if g.w is None else g.w.to(dev).contiguous()
+        return cls.from_tensors(ctx, g.n, off, col, w, copy=copy, validate=validate)
+
+    def download(self):
+        off = np.zeros(self.n + 1, dtype=np.int64)
+        col = np.zeros(max(self.nnz, 1), dtype=np.uint32)
+        w = np.zeros(max(self.nnz, 1), dtype=np.float32) if self.weighted else None
+        _check(_lib.sg_graph_download(self.ctx.handle, self.handle, _ptr(off), _ptr(col), _ptr(w)))
+        return off, col[:self.nnz], (None if w is None else w[:self.nnz])
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _lib.sg_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def compress(g: Graph, kernel, p: float, seed: int, want_weights: bool = False) -> Graph:
+    """compress(G, kernel, p, seed) -> H (Listing 1 kernels; see slimgraph.h)."""
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    h = C.c_void_p()
+    _check(_lib.sg_compress(g.ctx.handle, g.handle, k, float(p), int(seed) & (2**64 - 1), int(want_weights),
+                            C.byref(h)))
+    return Graph(g.ctx, h)
+
+
+def divergence(g: Graph, h: Graph, damping: float = 0.85, iters: int = 50) -> dict:
+    r = DivResult()
+    _check(_lib.sg_divergence(g.ctx.handle, g.handle, h.handle, float(damping), int(iters), C.byref(r)))
+    return {k: getattr(r, k) for k, _ in DivResult._fields_}
+
+
+def pagerank(g: Graph, damping: float = 0.85, iters: int = 50):
+    """FP32 PageRank vector (a CUDA tensor) and the FP64 residual of the last update."""
+    import torch
+
+    x = torch.empty(max(g.n, 1), dtype=torch.float32, device=torch.device("cuda", g.ctx.device))
+    r = C.c_double()
+    _check(_lib.sg_pagerank(g.ctx.handle, g.handle, float(damping), int(iters), x.data_ptr(), C.byref(r)))
+    return x[:g.n], r.value
+
+
+def kl_divergence(ctx: Context, P, Q) -> float:
+    out = C.c_double()
+    _check(_lib.sg_kl_divergence(ctx.handle, P.numel(), P.data_ptr(), Q.data_ptr(), C.byref(out)))
+    return out.value
+
+
+def cc_count(g: Graph, labels: bool = False):
+    import torch
+
+    cnt = C.c_int64()
+    lab = torch.empty(max(g.n, 1), dtype=torch.int32, device=torch.device("cuda", g.ctx.device)) if labels else None
+    _check(_lib.sg_cc_count(g.ctx.handle, g.handle, C.byref(cnt), None if lab is None else lab.data_ptr()))
+    return (cnt.value, lab[:g.n]) if labels else cnt.value
+
+
+def triangle_count(g: Graph) -> int:
+    t = C.c_int64()
+    _check(_lib.sg_triangle_count(g.ctx.handle, g.handle, C.byref(t)))
+    return t.value
+
+
+def tr_work(g: Graph) -> dict:
+    m, w, md, t = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t)))
+    return {"m": m.value, "probes": w.value, "max_out_degree": md.value, "triangles": t.value}

@@ -1,0 +1,551 @@
+// Arc-tiled stream compaction of a symmetric CSR with a single-pass
+// decoupled-lookback prefix scan (Merrill & Garland, "Single-pass parallel
+// prefix scan with decoupled look-back", NVIDIA TR 2016), written without CUB.
+//
+// One pass over the arc array decides, for every arc (x, y), whether it stays,
+// scatters the kept column ids (and weights) to their final positions and
+// writes the new row offsets: off'[v] = number of kept arcs before off[v].
+// Rows stay sorted because arcs keep their order.  The same engine serves
+//   * the edge kernels of Listing 1 (random_uniform, spectral_sparsify),
+//   * the degree-ordered orientation E+ that triangle listing needs (Sec. 4.3:
+//     O(m^{3/2}) listing), and
+//   * the final mask resolution of the Triangle p-1-Reduction kernels, which
+//     replaces the paper's "atomic SG.del(e)" by per-edge flags read here.
+//
+// Layout: a tile is kTile consecutive arcs handled by one CTA; warp w owns
+// arcs [t0 + w*kWarpSpan, +kWarpSpan) as CI slabs of 32 consecutive arcs, one
+// per lane, so every global read of col[] is a 128-byte coalesced access and
+// ballots give the slab's keep mask directly.  Tiles are claimed through an
+// atomic ticket, so a CTA only ever waits on tiles already owned by running
+// CTAs; every wait is bounded and reports a device error instead of hanging.
+#include <climits>
+
+#include "sg_internal.cuh"
+
+namespace sg {
+
+constexpr unsigned long long kStAgg = 1ull << 62;
+constexpr unsigned long long kStInc = 2ull << 62;
+constexpr unsigned long long kStVal = (1ull << 62) - 1;
+
+uint64_t prob_threshold(double p) {
+    const double t = std::floor(p * 4294967296.0);
+    if (t >= 4294967296.0) return 4294967296ull;
+    if (t <= 0.0) return 0;
+    return (uint64_t)t;
+}
+
+static uint64_t scaled_threshold(double y) {
+    const double t = std::floor(y * 4294967296.0);
+    if (t >= 18446744073709551615.0) return UINT64_MAX;
+    if (t <= 0.0) return 0;
+    return (uint64_t)t;
+}
+
+// --------------------------------------------------------------- row maps
+// chunk_row[c] = the row holding arc c*kWarpSpan; tile_vlo[t] = first row v
+// with off[v] >= t*kTile (tile_vlo[num_tiles] = n + 1).  One thread per row,
+// no searches: row v owns the chunk and tile starts that fall in its range.
+__global__ void row_maps_kernel(const int64_t *__restrict__ off, int64_t n, uint32_t *__restrict__ chunk_row,
+                                int64_t num_chunks, int64_t *__restrict__ tile_vlo, int64_t num_tiles) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+        const int64_t b = off[v];
+        const int64_t a = (v == 0) ? -1 : off[v - 1];
+        for (int64_t t = (a < 0) ? 0 : a / kTile + 1; t < num_tiles && t * kTile <= b; ++t) tile_vlo[t] = v;
+        if (v < n) {
+            const int64_t e = off[v + 1];
+            for (int64_t c = (b + kWarpSpan - 1) / kWarpSpan; c < num_chunks && c * kWarpSpan < e; ++c)
+                chunk_row[c] = (uint32_t)v;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tile_vlo[num_tiles] = n + 1;
+}
+
+sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm) {
+    rm->num_tiles = (g->nnz + kTile - 1) / kTile;
+    rm->num_chunks = (g->nnz + kWarpSpan - 1) / kWarpSpan;
+    sg_status st = dalloc(c, (void **)&rm->chunk_row, sizeof(uint32_t) * (size_t)(rm->num_chunks + 1));
+    if (st != SG_OK) return st;
+    st = dalloc(c, (void **)&rm->tile_vlo, sizeof(int64_t) * (size_t)(rm->num_tiles + 1));
+    if (st != SG_OK) return st;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((g->n + 1 + threads - 1) / threads, (int64_t)c->num_sms * 16);
+    {
+        SG_LAUNCH(c, "row_maps");
+        row_maps_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, c->stream>>>(
+            g->off, g->n, rm->chunk_row, rm->num_chunks, rm->tile_vlo, rm->num_tiles);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+void free_row_maps(Ctx *c, RowMaps *rm) {
+    dfree(c, rm->chunk_row);
+    dfree(c, rm->tile_vlo);
+    rm->chunk_row = nullptr;
+    rm->tile_vlo = nullptr;
+}
+
+// ------------------------------------------------------------ device parts
+struct CompactArgs {
+    const int64_t *off;
+    const uint32_t *col;
+    const float *w;
+    int64_t n, nnz, num_tiles;
+    const uint32_t *chunk_row;
+    const int64_t *tile_vlo;
+    int64_t *off_out;
+    uint32_t *col_out;
+    float *w_out;
+    unsigned long long *status;
+    unsigned int *ticket;
+    int *err;
+    uint32_t *keep_bits;  // optional: the keep mask of every 32-arc slab
+};
+
+struct SlabCtx {
+    uint32_t or_word;  // forward-arc bits of this slab (mask resolution only)
+    int64_t or_base;   // E+ index of the slab's first forward arc
+};
+
+// Row of position sbase + q (q in [0,32), non-decreasing across lanes).
+// `cursor` is a row starting at or before sbase; it advances to the row of
+// lane 31 so the next slab starts its search there.
+__device__ __forceinline__ int64_t warp_row(const int64_t *__restrict__ off, int64_t n, int64_t &cursor,
+                                            int64_t sbase, int q) {
+    const int lane = threadIdx.x & 31;
+    int64_t cur = cursor;
+    int64_t row = -1;
+    for (;;) {
+        const int64_t bi = cur + 1 + lane;  // lane j holds the start of row cur+1+j
+        const int64_t b = (bi <= n) ? __ldg(off + bi) : LLONG_MAX;
+        const int64_t rel = b - sbase;
+        const int r = rel < 0 ? -1 : (rel > 32 ? 32 : (int)rel);
+        int cnt = 0;  // boundaries at or before sbase + q
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const int v = __shfl_sync(kFull, r, cnt + s - 1);
+            if (v <= q) cnt += s;
+        }
+        const int r31 = __shfl_sync(kFull, r, 31);
+        if (cnt == 31 && r31 <= q) cnt = 32;
+        if (row < 0 && cnt < 32) row = cur + cnt;
+        if (!__any_sync(kFull, row < 0)) break;
+        cur += 32;
+    }
+    cursor = __shfl_sync(kFull, row, 31);
+    return row;
+}
+
+// Decoupled look-back by one warp: publish this tile's aggregate, sum the
+// predecessors' values back to the first inclusive prefix, publish our own
+// inclusive prefix, return the exclusive one.  Polls are bounded.
+__device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64_t agg, int *err) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_volatile_u64(status, kStInc | (unsigned long long)agg);
+        return 0;
+    }
+    if (lane == 0) st_volatile_u64(status + tile, kStAgg | (unsigned long long)agg);
+    int64_t excl = 0;
+    int64_t idx = tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t j = idx - lane;
+        const unsigned long long s = (j >= 0) ? ld_volatile_u64(status + j) : kStInc;
+        const unsigned flag = (unsigned)(s >> 62);
+        if (__any_sync(kFull, flag == 0)) {
+            ++spins;
+            // give up after kSpinLimit polls, or at once if another tile already
+            // gave up; publish a (meaningless) inclusive value so that no
+            // successor waits on this tile either
+            bool quit = spins > kSpinLimit;
+            if ((spins & 1023u) == 0) quit = quit || (*(volatile int *)err != 0);
+            if (__any_sync(kFull, quit)) {
+                if (lane == 0) {
+                    atomicExch(err, (int)kDevLookbackTimeout);
+                    st_volatile_u64(status + tile, kStInc | (unsigned long long)agg);
+                }
+                return excl;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        const unsigned inc = __ballot_sync(kFull, flag == 2);
+        const int first = inc ? __ffs(inc) - 1 : 32;
+        const int64_t v = (lane <= first) ? (int64_t)(s & kStVal) : 0;
+        excl += warp_sum(v);
+        if (inc) break;
+        idx -= 32;
+    }
+    if (lane == 0) st_volatile_u64(status + tile, kStInc | (unsigned long long)(excl + agg));
+    return excl;
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol) {
+    __shared__ uint32_t s_mask[CW][CI];
+    __shared__ int s_slab_excl[CW][CI];
+    __shared__ int s_warp_cnt[CW];
+    __shared__ int s_warp_excl[CW + 1];
+    __shared__ int s_or_cnt[CW];
+    __shared__ long long s_tile_excl;
+    __shared__ long long s_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= a.num_tiles) break;
+        const int64_t t0 = tile * kTile;
+        const int64_t t1 = min(t0 + (int64_t)kTile, a.nnz);
+        const int64_t wbase = t0 + (int64_t)warp * kWarpSpan;
+
+        int64_t or_run = 0;
+        if constexpr (Pol::kOrPrefix) {
+            uint32_t wd = 0;
+            if (lane < CI && wbase + lane * 32 < t1) wd = __ldg(pol.fwd_bits + (wbase >> 5) + lane);
+            const int cnt = warp_sum(__popc(wd));
+            if (lane == 0) s_or_cnt[warp] = cnt;
+            __syncthreads();
+            int64_t base = pol.tile_or_excl(tile);
+            for (int i = 0; i < warp; ++i) base += s_or_cnt[i];
+            or_run = base;
+        }
+
+        uint32_t ys[CI];
+        float ws[CI];
+        uint32_t masks[CI];
+        int wcnt = 0;
+        int64_t cursor = (wbase < t1) ? (int64_t)__ldg(a.chunk_row + wbase / kWarpSpan) : 0;
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            const int64_t sbase = wbase + k * 32;
+            masks[k] = 0;
+            ys[k] = 0;
+            ws[k] = 0.f;
+            if (sbase < t1) {  // warp-uniform
+                const int64_t p = sbase + lane;
+                const bool valid = p < t1;
+                const int q = valid ? lane : (int)(t1 - 1 - sbase);
+                const int64_t x = warp_row(a.off, a.n, cursor, sbase, q);
+                const int64_t pe = sbase + q;
+                const uint32_t y = __ldg(a.col + pe);
+                float wv = a.w ? __ldg(a.w + pe) : 0.f;
+                SlabCtx sc{0u, 0};
+                if constexpr (Pol::kOrPrefix) {
+                    sc.or_word = __ldg(pol.fwd_bits + (sbase >> 5));
+                    sc.or_base = or_run;
+                    or_run += __popc(sc.or_word);
+                }
+                const bool keep = valid && pol.keep(x, y, p, sc, wv);
+                masks[k] = __ballot_sync(kFull, keep);
+                ys[k] = y;
+                ws[k] = wv;
+                wcnt += __popc(masks[k]);
+                if (a.keep_bits != nullptr && lane == 0) a.keep_bits[sbase >> 5] = masks[k];
+            }
+        }
+        if (lane == 0) {
+            int run = 0;
+#pragma unroll
+            for (int k = 0; k < CI; ++k) {
+                s_mask[warp][k] = masks[k];
+                s_slab_excl[warp][k] = run;
+                run += __popc(masks[k]);
+            }
+            s_warp_cnt[warp] = run;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int agg = 0;
+            if (lane == 0) {
+                for (int i = 0; i < CW; ++i) {
+                    s_warp_excl[i] = agg;
+                    agg += s_warp_cnt[i];
+                }
+                s_warp_excl[CW] = agg;
+            }
+            agg = __shfl_sync(kFull, agg, 0);
+            const int64_t excl = tile_lookback(a.status, tile, agg, a.err);
+            if (lane == 0) s_tile_excl = excl;
+        }
+        __syncthreads();
+        const int64_t texcl = s_tile_excl;
+        const int64_t wexcl = texcl + s_warp_excl[warp];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            if ((masks[k] >> lane) & 1u) {
+                const int64_t g = wexcl + s_slab_excl[warp][k] + __popc(masks[k] & lt);
+                a.col_out[g] = ys[k];
+                if (a.w_out) a.w_out[g] = ws[k];
+            }
+        }
+        // new row offsets for the rows whose start lies in this tile
+        const int64_t v0 = __ldg(a.tile_vlo + tile), v1 = __ldg(a.tile_vlo + tile + 1);
+        const int64_t tlen = t1 - t0;
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            const int64_t q = __ldg(a.off + v) - t0;
+            int local;
+            if (q >= tlen) {
+                local = s_warp_excl[CW];
+            } else {
+                const int wq = (int)(q / kWarpSpan), kq = (int)((q >> 5) % CI), lq = (int)(q & 31);
+                local = s_warp_excl[wq] + s_slab_excl[wq][kq] + __popc(s_mask[wq][kq] & ((1u << lq) - 1u));
+            }
+            a.off_out[v] = texcl + local;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- policies
+struct UniformPol {
+    static constexpr bool kOrPrefix = false;
+    uint32_t k0, k1;
+    unsigned long long tp;
+    // random_uniform(E e): the edge stays iff its draw is below floor(p 2^32)
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
+        const uint32_t ux = (uint32_t)x;
+        const uint4 r = philox4x32_10(make_uint4(min(ux, y), max(ux, y), 0u, kTagEdge), k0, k1);
+        return (unsigned long long)r.x < tp;
+    }
+};
+
+struct SpectralPol {
+    static constexpr bool kOrPrefix = false;
+    const int64_t *off;
+    uint32_t k0, k1;
+    unsigned long long ty;  // floor(Y 2^32)
+    float yf;               // Y rounded to float
+    bool reweight;
+    // spectral_sparsify(E e): stays with probability min(1, Y / min(d_u, d_v)),
+    // i.e. iff r * min(d_u, d_v) < Y 2^32; kept edges may take weight 1/p_uv.
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &w) const {
+        const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
+        const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
+        const uint64_t dmin = dx < dy ? dx : dy;
+        const uint32_t ux = (uint32_t)x;
+        const uint4 r = philox4x32_10(make_uint4(min(ux, y), max(ux, y), 0u, kTagEdge), k0, k1);
+        if (reweight) w = (dmin * 4294967296ull <= ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), yf);
+        return (unsigned long long)r.x * dmin < ty;
+    }
+};
+
+struct OrientPol {
+    static constexpr bool kOrPrefix = false;
+    const int64_t *off;
+    // x precedes y in the degree order (d_x, x) < (d_y, y)
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
+        const int64_t dx = __ldg(off + x + 1) - __ldg(off + x);
+        const int64_t dy = __ldg(off + y + 1) - __ldg(off + y);
+        return dx < dy || (dx == dy && (uint32_t)x < y);
+    }
+};
+
+struct MaskPol {
+    static constexpr bool kOrPrefix = true;
+    const uint32_t *fwd_bits;
+    const unsigned long long *or_status;
+    const int64_t *offp;
+    const uint32_t *colp;
+    const uint8_t *del;
+    int *err;
+    __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const {
+        return tile == 0 ? 0 : (int64_t)(ld_volatile_u64(or_status + tile - 1) & kStVal);
+    }
+    // the arc stays iff its edge's oriented arc carries no deletion flag
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t p, const SlabCtx &s, float &) const {
+        const int lane = (int)(p & 31);
+        int64_t idx;
+        if ((s.or_word >> lane) & 1u) {
+            idx = s.or_base + __popc(s.or_word & lanemask_lt());
+        } else {
+            const int64_t end = __ldg(offp + y + 1);
+            idx = lower_bound_u32(colp, __ldg(offp + y), end, (uint32_t)x);
+            if (idx >= end || __ldg(colp + idx) != (uint32_t)x) {  // no reverse arc: not a symmetric CSR
+                atomicExch(err, (int)kDevBadGraph);
+                return true;
+            }
+        }
+        return __ldg(del + idx) == 0;
+    }
+};
+
+// ------------------------------------------------------------------ driver
+template <class Pol>
+static int blocks_per_sm() {
+    static int cached = -1;
+    if (cached < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, compact_kernel<Pol>, CW * 32, 0) != cudaSuccess || b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+template <class Pol>
+static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Pol &pol, const float *w_in,
+                             int64_t *off_out, uint32_t *col_out, float *w_out, uint32_t *keep_bits,
+                             unsigned long long *status, const char *name) {
+    if (g->nnz == 0) {
+        SG_CUDA(cudaMemsetAsync(off_out, 0, sizeof(int64_t) * (size_t)(g->n + 1), c->stream));
+        return SG_OK;
+    }
+    // status words for every tile + the tile ticket, zeroed together
+    SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1), c->stream));
+    CompactArgs a;
+    a.off = g->off;
+    a.col = g->col;
+    a.w = w_in;
+    a.n = g->n;
+    a.nnz = g->nnz;
+    a.num_tiles = rm.num_tiles;
+    a.chunk_row = rm.chunk_row;
+    a.tile_vlo = rm.tile_vlo;
+    a.off_out = off_out;
+    a.col_out = col_out;
+    a.w_out = w_out;
+    a.status = status;
+    a.ticket = reinterpret_cast<unsigned int *>(status + rm.num_tiles);
+    a.err = c->d_err;
+    a.keep_bits = keep_bits;
+    const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * blocks_per_sm<Pol>());
+    {
+        SG_LAUNCH(c, name);
+        compact_kernel<Pol><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+static sg_status read_i64(Ctx *c, const int64_t *dptr, int64_t *out) {
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, dptr, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaStreamSynchronize(c->stream));
+    *out = c->h_pinned[0];
+    return SG_OK;
+}
+
+static sg_status new_graph(Ctx *c, int64_t n, int64_t nnz_cap, bool weighted, Graph **out) {
+    Graph *h = new Graph;
+    h->ctx = c;
+    h->n = n;
+    h->owned = true;
+    sg_status st = dalloc(c, (void **)&h->off, sizeof(int64_t) * (size_t)(n + 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&h->col, sizeof(uint32_t) * (size_t)std::max<int64_t>(nnz_cap, 1));
+    if (st == SG_OK && weighted) st = dalloc(c, (void **)&h->w, sizeof(float) * (size_t)std::max<int64_t>(nnz_cap, 1));
+    if (st != SG_OK) {
+        dfree(c, h->off);
+        dfree(c, h->col);
+        dfree(c, h->w);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+static void delete_graph(Ctx *c, Graph *h) {
+    if (!h) return;
+    dfree(c, h->off);
+    dfree(c, h->col);
+    dfree(c, h->w);
+    delete h;
+}
+
+sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t seed, int want_weights,
+                         Graph **out) {
+    RowMaps rm;
+    sg_status st = build_row_maps(c, g, &rm);
+    unsigned long long *status = nullptr;
+    Graph *h = nullptr;
+    const bool spectral = (k == SG_SPECTRAL_LOGN || k == SG_SPECTRAL_AVGDEG);
+    const bool out_w = (spectral && want_weights) || g->w != nullptr;
+    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = new_graph(c, g->n, g->nnz, out_w, &h);
+    if (st == SG_OK) {
+        const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+        if (k == SG_UNIFORM) {
+            UniformPol pol{k0, k1, prob_threshold(p)};
+            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_uniform");
+        } else {
+            const int64_t m = g->nnz / 2;
+            const double y = (k == SG_SPECTRAL_LOGN) ? p * std::log((double)g->n)
+                                                     : (g->n > 0 ? p * (double)m / (double)g->n : 0.0);
+            SpectralPol pol{g->off, k0, k1, scaled_threshold(y), (float)y, want_weights != 0};
+            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_spectral");
+        }
+    }
+    if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
+    if (st == SG_OK) st = check_device_error(c);
+    dfree(c, status);
+    free_row_maps(c, &rm);
+    if (st != SG_OK) {
+        delete_graph(c, h);
+        return st;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Oriented *o) {
+    o->n = g->n;
+    o->m = g->nnz / 2;
+    sg_status st = dalloc(c, (void **)&o->off, sizeof(int64_t) * (size_t)(g->n + 1));
+    // capacity nnz, not m: an asymmetric input could orient more than m arcs
+    if (st == SG_OK) st = dalloc(c, (void **)&o->col, sizeof(uint32_t) * (size_t)std::max<int64_t>(g->nnz, 1));
+    if (st == SG_OK && weights) st = dalloc(c, (void **)&o->w, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1));
+    if (st == SG_OK)
+        st = dalloc(c, (void **)&o->fwd_bits, sizeof(uint32_t) * (size_t)(rm.num_chunks * CI + 1));
+    if (st == SG_OK)
+        st = dalloc(c, (void **)&o->status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st != SG_OK) return st;
+    OrientPol pol{g->off};
+    st = run_compact(c, g, rm, pol, weights ? g->w : nullptr, o->off, o->col, weights ? o->w : nullptr,
+                     o->fwd_bits, o->status, "compact_orient");
+    if (st != SG_OK) return st;
+    int64_t mp = 0;
+    st = read_i64(c, o->off + g->n, &mp);
+    if (st != SG_OK) return st;
+    st = check_device_error(c);
+    if (st != SG_OK) return st;
+    if (mp != o->m)
+        return fail(SG_ERR_INVALID_GRAPH, "graph is not symmetric: oriented arcs != nnz/2");
+    return SG_OK;
+}
+
+void free_oriented(Ctx *c, Oriented *o) {
+    dfree(c, o->off);
+    dfree(c, o->col);
+    dfree(c, o->w);
+    dfree(c, o->fwd_bits);
+    dfree(c, o->status);
+    *o = Oriented{};
+}
+
+sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
+                       Graph **out) {
+    Graph *h = nullptr;
+    unsigned long long *status = nullptr;
+    sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
+    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) {
+        MaskPol pol{o.fwd_bits, o.status, o.off, o.col, del, c->d_err};
+        st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_trmask");
+    }
+    if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
+    if (st == SG_OK) st = check_device_error(c);
+    dfree(c, status);
+    if (st != SG_OK) {
+        delete_graph(c, h);
+        return st;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+}  // namespace sg

@@ -1,0 +1,189 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "slimgraph.h"
+
+namespace sg {
+
+// ---------------------------------------------------------------- constants
+constexpr uint32_t kTagEdge = 0x45444745u;  // Philox counter word 3 for edges
+constexpr uint32_t kTagTri = 0x54524931u;   // Philox counter word 3 for triangles
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// device error word values (set by kernels, read after a stream sync)
+enum DevErr : int { kDevOk = 0, kDevLookbackTimeout = 1, kDevBadGraph = 2, kDevTableFull = 3 };
+
+// bounded spin: polls of a not-yet-published status word before giving up
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// compaction geometry: CW warps x 32 lanes x CI items per tile
+constexpr int CW = 8;
+constexpr int CI = 8;
+constexpr int kWarpSpan = 32 * CI;       // arcs per warp per tile
+constexpr int kTile = CW * kWarpSpan;    // arcs per tile
+
+// ------------------------------------------------------------- host objects
+struct ProfRec {
+    const char *name;
+    cudaEvent_t beg, end;
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int *d_err = nullptr;                  // device error word
+    unsigned long long *d_ctr = nullptr;   // device counters [kCtrCount]
+    int64_t *h_pinned = nullptr;           // pinned host scratch (small reads)
+    uint64_t launches = 0;
+    uint64_t eo_rounds = 0;
+    bool profiling = false;
+    std::vector<ProfRec> prof;             // events of launches since reset
+    std::vector<cudaEvent_t> event_pool;   // recycled events
+};
+
+enum CtrIdx { kCtrProbes = 0, kCtrTriangles = 1, kCtrLive = 2, kCtrHeavy = 3, kCtrMaxDeg = 4, kCtrAux = 5,
+              kCtrCount = 8 };
+
+struct Graph {
+    Ctx *ctx = nullptr;
+    int64_t n = 0, nnz = 0;
+    int64_t *off = nullptr;
+    uint32_t *col = nullptr;
+    float *w = nullptr;
+    bool owned = true;
+};
+
+// ------------------------------------------------------------ error plumbing
+void set_error(const std::string &msg);
+sg_status fail(sg_status st, const std::string &msg);
+sg_status cuda_fail(cudaError_t e, const char *what);
+
+#define SG_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::sg::cuda_fail(_e, #call);       \
+    } while (0)
+
+// stream-ordered device allocation on the context stream
+sg_status dalloc(Ctx *c, void **p, size_t bytes);
+void dfree(Ctx *c, void *p);
+
+// launch bookkeeping: brackets a launch with events when profiling
+struct LaunchScope {
+    Ctx *c;
+    const char *name;
+    cudaEvent_t b = nullptr, e = nullptr;
+    LaunchScope(Ctx *c_, const char *n_);
+    ~LaunchScope();
+};
+#define SG_CAT2_(a, b) a##b
+#define SG_CAT_(a, b) SG_CAT2_(a, b)
+#define SG_LAUNCH(ctx, name) ::sg::LaunchScope SG_CAT_(sg_scope_, __LINE__)((ctx), (name))
+
+// read the device error word and reset it; map it to a status
+sg_status check_device_error(Ctx *c);
+
+// -------------------------------------------------------------- device code
+#ifdef __CUDACC__
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of a
+// multiply-xor Feistel step on four 32-bit words; the two key words advance by
+// Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// first index in sorted a[lo, hi) with a[i] >= key
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t lo, int64_t hi, uint32_t key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------- internal entry
+// compaction / edge kernels (sg_compact.cu)
+struct RowMaps {
+    uint32_t *chunk_row = nullptr;  // row containing arc c * kWarpSpan
+    int64_t *tile_vlo = nullptr;    // first row v with off[v] >= t * kTile; [num_tiles] = n + 1
+    int64_t num_tiles = 0, num_chunks = 0;
+};
+sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm);
+void free_row_maps(Ctx *c, RowMaps *rm);
+
+sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t seed, int want_weights,
+                         Graph **out);
+
+// the degree-ordered orientation E+ (sg_compact.cu)
+struct Oriented {
+    int64_t n = 0, m = 0;
+    int64_t *off = nullptr;      // off+[n+1]
+    uint32_t *col = nullptr;     // col+[m]
+    float *w = nullptr;          // w+[m] (weighted TR only)
+    uint32_t *fwd_bits = nullptr;  // bit per symmetric arc: 1 iff x precedes y
+    unsigned long long *status = nullptr;  // inclusive prefix of forward arcs per tile
+};
+sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Oriented *o);
+void free_oriented(Ctx *c, Oriented *o);
+// H = G minus the edges whose oriented arc has del[] != 0
+sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
+                       Graph **out);
+
+// triangles (sg_triangles.cu)
+sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed,
+                  uint8_t *del);
+sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg);
+
+// analytics (sg_analytics.cu)
+sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_out, double *resid);
+sg_status kl_divergence(Ctx *c, int64_t n, const float *P, const float *Q, double *kl);
+sg_status cc_count(Ctx *c, const Graph *g, int64_t *count, uint32_t *labels);
+sg_status validate_graph(Ctx *c, const Graph *g);
+
+uint64_t prob_threshold(double p);
+
+}  // namespace sg

@@ -1,0 +1,504 @@
+// Triangle enumeration over the degree-ordered orientation E+ and the
+// Triangle p-1-Reduction kernels of Slim Graph (Sec. 4.3; Listing 1
+// p-1-reduction and p-1-reduction-EO).
+//
+// Enumeration.  Every triangle {u, v, w} with u < v < w in the degree order
+// (d, id) is found exactly once, at the oriented arc u->v, as w in
+// N+(u) ∩ N+(v) (the forward algorithm behind the O(m^{3/2}) bound the paper
+// quotes).  For each u the set N+(u) is staged in a shared-memory hash table
+// (linear probing, load <= 1/4) and the warp streams every list N+(v),
+// v in N+(u), through it with coalesced 128-byte reads: one probe per element
+// of N+(v), W = sum_{u->v} d+(v) probes in all.  Vertices with d+(u) <= 64
+// get one warp each; larger ones get a whole CTA whose warps split N+(u).
+//
+// Decisions.  A hit (a triangle) is pushed to a per-warp queue; whenever 32
+// hits are queued the warp decides all of them at once with full lanes:
+// Philox4x32-10 on the sorted original ids (a, b, c) selects the triangle
+// (r0 < floor(p 2^32)) and picks the edge to delete (r1, or the heaviest edge).
+// Union kernels store del[arc] = 1 (a plain, idempotent byte store).  The
+// Edge-Once kernel instead reserves each edge of every live selected triangle
+// with a 64-bit atomicMin of (r2 << 32 | third vertex); an edge pass then
+// accepts every triangle that holds all three of its reservations.  Accepted
+// triangles are edge-disjoint, mark their edges considered, delete their
+// chosen edge, and the rounds repeat until no selected triangle is live.
+// This reproduces exactly the sequential scan of the selected triangles in
+// increasing (r2, a, b, c) order (for two triangles sharing an edge, the
+// lexicographic order of (a, b, c) equals the order of their third vertices).
+#include <climits>
+#include <cstring>
+
+#include "sg_internal.cuh"
+
+namespace sg {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kLightMax = 64;     // largest out-degree processed by one warp
+constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
+constexpr int kTW = 8;            // warps per CTA
+constexpr int kQ = 64;            // per-warp hit queue entries
+
+enum class Mode { Count, UnionRandom, UnionMaxw, EoReserve };
+
+struct TriArgs {
+    const int64_t *offp;
+    const uint32_t *colp;
+    const float *wp;
+    int64_t n;
+    uint32_t k0, k1;
+    unsigned long long tp;
+    uint8_t *del;
+    const uint8_t *considered;
+    unsigned long long *resv;
+    unsigned long long *ctr;
+    const uint32_t *heavy;
+    int64_t n_heavy;
+    int heavy_log_slots;
+};
+
+struct HitQueue {
+    uint32_t u[kQ], v[kQ], w[kQ];
+    long long iuv[kQ], iuw[kQ], ivw[kQ];
+};
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t key, int log_slots) {
+    return (key * 0x9E3779B1u) >> (32 - log_slots);
+}
+
+__device__ __forceinline__ int ceil_log2(int x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
+
+template <typename T>
+__device__ __forceinline__ void swap2(T &a, T &b) {
+    const T t = a;
+    a = b;
+    b = t;
+}
+
+// One triangle (u, v, w) with its three oriented arcs: selection and action.
+template <Mode M>
+__device__ __forceinline__ void decide(const TriArgs &a, uint32_t u, uint32_t v, uint32_t w, int64_t iuv,
+                                       int64_t iuw, int64_t ivw, unsigned &live) {
+    if constexpr (M == Mode::Count) {
+        return;
+    } else {
+        // sort the vertices, keeping e_ij = the arc joining x_i and x_j
+        uint32_t x0 = u, x1 = v, x2 = w;
+        int64_t e01 = iuv, e02 = iuw, e12 = ivw;
+        if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+        if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+        if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+        const uint4 r = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), a.k0, a.k1);
+        if ((unsigned long long)r.x >= a.tp) return;  // triangle not selected
+        if constexpr (M == Mode::UnionRandom) {
+            const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
+            a.del[k == 0 ? e01 : (k == 1 ? e02 : e12)] = 1;
+        } else if constexpr (M == Mode::UnionMaxw) {
+            // heaviest edge under (weight, lo, hi)
+            const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
+            int64_t best = e01;
+            float bw = w01;
+            uint32_t bl = x0, bh = x1;
+            if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
+            if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
+            a.del[best] = 1;
+        } else {  // EoReserve
+            if (a.considered[e01] | a.considered[e02] | a.considered[e12]) return;
+            const unsigned long long hi = (unsigned long long)r.z << 32;
+            atomicMin(a.resv + e01, hi | x2);
+            atomicMin(a.resv + e02, hi | x1);
+            atomicMin(a.resv + e12, hi | x0);
+            ++live;
+        }
+    }
+}
+
+// Queue one hit per lane flag; decide 32 queued triangles whenever full.
+template <Mode M>
+__device__ __forceinline__ void push_hits(const TriArgs &a, HitQueue &q, int &qn, bool hit, uint32_t u, uint32_t v,
+                                          uint32_t w, int64_t iuv, int64_t iuw, int64_t ivw, unsigned &live,
+                                          unsigned long long &tris) {
+    const unsigned hm = __ballot_sync(kFull, hit);
+    if (!hm) return;
+    const int lane = threadIdx.x & 31;
+    if (hit) {
+        const int s = qn + __popc(hm & lanemask_lt());
+        q.u[s] = u; q.v[s] = v; q.w[s] = w;
+        q.iuv[s] = iuv; q.iuw[s] = iuw; q.ivw[s] = ivw;
+    }
+    qn += __popc(hm);
+    tris += hit ? 1 : 0;
+    __syncwarp();
+    if (qn >= 32) {
+        decide<M>(a, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live);
+        __syncwarp();
+        const int rest = qn - 32;
+        if (lane < rest) {
+            q.u[lane] = q.u[lane + 32]; q.v[lane] = q.v[lane + 32]; q.w[lane] = q.w[lane + 32];
+            q.iuv[lane] = q.iuv[lane + 32]; q.iuw[lane] = q.iuw[lane + 32]; q.ivw[lane] = q.ivw[lane + 32];
+        }
+        qn = rest;
+        __syncwarp();
+    }
+}
+
+template <Mode M>
+__device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn, unsigned &live) {
+    const int lane = threadIdx.x & 31;
+    if (lane < qn) decide<M>(a, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live);
+    __syncwarp();
+}
+
+// Stream N+(v) for v = N+(u)[i] through the table of N+(u).
+template <Mode M>
+__device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key, const uint16_t *idx, int log_slots,
+                                           uint32_t u, int64_t ou, int i, uint32_t v, HitQueue &q, int &qn,
+                                           unsigned &live, unsigned long long &probes, unsigned long long &tris) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t mask = (1u << log_slots) - 1u;
+    const int64_t ov = __ldg(a.offp + v);
+    const int64_t dv = __ldg(a.offp + v + 1) - ov;
+    for (int64_t j0 = 0; j0 < dv; j0 += 32) {
+        const int64_t j = j0 + lane;
+        bool hit = false;
+        uint32_t w = 0, t = 0;
+        if (j < dv) {
+            w = __ldg(a.colp + ov + j);
+            ++probes;
+            uint32_t s = slot_of(w, log_slots);
+            for (;;) {
+                const uint32_t k = key[s];
+                if (k == w) { hit = true; t = idx[s]; break; }
+                if (k == kEmpty) break;
+                s = (s + 1) & mask;
+            }
+        }
+        push_hits<M>(a, q, qn, hit, u, v, w, ou + i, ou + t, ov + j, live, tris);
+    }
+}
+
+__device__ __forceinline__ void table_insert(uint32_t *key, uint16_t *idx, int log_slots, uint32_t w, int i) {
+    const uint32_t mask = (1u << log_slots) - 1u;
+    uint32_t s = slot_of(w, log_slots);
+    for (;;) {
+        const uint32_t old = atomicCAS(key + s, kEmpty, w);
+        if (old == kEmpty) { idx[s] = (uint16_t)i; return; }
+        s = (s + 1) & mask;
+    }
+}
+
+template <Mode M>
+__device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, unsigned live,
+                                       unsigned long long probes, unsigned long long tris) {
+    flush_hits<M>(a, q, qn, live);
+    const unsigned long long P = warp_sum(probes), T = warp_sum(tris);
+    const unsigned L = warp_sum(live);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.ctr + kCtrProbes, P);
+        atomicAdd(a.ctr + kCtrTriangles, T);
+        if (L) atomicAdd(a.ctr + kCtrLive, (unsigned long long)L);
+    }
+}
+
+// warp per vertex u with 2 <= d+(u) <= kLightMax
+template <Mode M>
+__global__ void __launch_bounds__(kTW * 32) tri_light_kernel(TriArgs a) {
+    __shared__ uint32_t s_key[kTW][kLightSlots];
+    __shared__ uint16_t s_idx[kTW][kLightSlots];
+    __shared__ HitQueue s_q[kTW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *key = s_key[warp];
+    uint16_t *idx = s_idx[warp];
+    HitQueue &q = s_q[warp];
+    int qn = 0;
+    unsigned live = 0;
+    unsigned long long probes = 0, tris = 0;
+    const int64_t nw = (int64_t)gridDim.x * kTW;
+    for (int64_t u = (int64_t)blockIdx.x * kTW + warp; u < a.n; u += nw) {
+        const int64_t ou = __ldg(a.offp + u);
+        const int d = (int)(__ldg(a.offp + u + 1) - ou);
+        if (d < 2 || d > kLightMax) continue;
+        const int log_slots = max(3, ceil_log2(4 * d));
+        for (int s = lane; s < (1 << log_slots); s += 32) key[s] = kEmpty;
+        __syncwarp();
+        const uint32_t n0 = lane < d ? __ldg(a.colp + ou + lane) : 0u;
+        const uint32_t n1 = lane + 32 < d ? __ldg(a.colp + ou + lane + 32) : 0u;
+        if (lane < d && (M != Mode::EoReserve || !a.considered[ou + lane])) table_insert(key, idx, log_slots, n0, lane);
+        if (lane + 32 < d && (M != Mode::EoReserve || !a.considered[ou + lane + 32]))
+            table_insert(key, idx, log_slots, n1, lane + 32);
+        __syncwarp();
+        for (int i = 0; i < d; ++i) {
+            const uint32_t v = __shfl_sync(kFull, i < 32 ? n0 : n1, i & 31);
+            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
+            probe_list<M>(a, key, idx, log_slots, (uint32_t)u, ou, i, v, q, qn, live, probes, tris);
+        }
+        __syncwarp();
+    }
+    finish<M>(a, q, qn, live, probes, tris);
+}
+
+// CTA per heavy vertex (d+(u) > kLightMax); the table lives in dynamic smem
+template <Mode M>
+__global__ void __launch_bounds__(kTW * 32) tri_heavy_kernel(TriArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
+    uint32_t *key = reinterpret_cast<uint32_t *>(smem + sizeof(HitQueue) * kTW);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(key + (1 << a.heavy_log_slots));
+    const int warp = threadIdx.x >> 5;
+    HitQueue &q = qs[warp];
+    int qn = 0;
+    unsigned live = 0;
+    unsigned long long probes = 0, tris = 0;
+    for (int64_t h = blockIdx.x; h < a.n_heavy; h += gridDim.x) {
+        const uint32_t u = __ldg(a.heavy + h);
+        const int64_t ou = __ldg(a.offp + u);
+        const int d = (int)(__ldg(a.offp + u + 1) - ou);
+        const int log_slots = min(a.heavy_log_slots, ceil_log2(4 * d));
+        __syncthreads();  // previous vertex finished with the table
+        for (int s = threadIdx.x; s < (1 << log_slots); s += blockDim.x) key[s] = kEmpty;
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
+            table_insert(key, idx, log_slots, __ldg(a.colp + ou + i), i);
+        }
+        __syncthreads();
+        for (int i = warp; i < d; i += kTW) {
+            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
+            const uint32_t v = __ldg(a.colp + ou + i);
+            probe_list<M>(a, key, idx, log_slots, u, ou, i, v, q, qn, live, probes, tris);
+        }
+    }
+    finish<M>(a, q, qn, live, probes, tris);
+}
+
+// heavy-vertex list and the maximum out-degree
+__global__ void classify_kernel(const int64_t *__restrict__ offp, int64_t n, uint32_t *heavy,
+                                unsigned long long *ctr) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long dmax = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t u = base + threadIdx.x;
+        int64_t d = 0;
+        if (u < n) d = offp[u + 1] - offp[u];
+        dmax = d > (int64_t)dmax ? (unsigned long long)d : dmax;
+        const bool hv = d > kLightMax;
+        const unsigned hm = __ballot_sync(kFull, hv);
+        if (hm) {
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(ctr + kCtrHeavy, (unsigned long long)__popc(hm));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (hv) heavy[pos + __popc(hm & lanemask_lt())] = (uint32_t)u;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, dmax, o);
+        dmax = t > dmax ? t : dmax;
+    }
+    if (lane == 0) atomicMax(ctr + kCtrMaxDeg, dmax);
+}
+
+// Edge-Once acceptance: an oriented arc e = u->y holding reservation
+// (r2, z) belongs to the accepted triangle {u, y, z} iff that triangle also
+// holds the reservations of its two other edges.
+// returns -1 when the arc is missing (never for a symmetric CSR)
+__device__ __forceinline__ int64_t arc_between(const int64_t *off, const int64_t *offp, const uint32_t *colp,
+                                               uint32_t p, uint32_t q) {
+    const int64_t dp = __ldg(off + p + 1) - __ldg(off + p);
+    const int64_t dq = __ldg(off + q + 1) - __ldg(off + q);
+    const bool pq = dp < dq || (dp == dq && p < q);
+    const uint32_t row = pq ? p : q, key = pq ? q : p;
+    const int64_t end = __ldg(offp + row + 1);
+    const int64_t i = lower_bound_u32(colp, __ldg(offp + row), end, key);
+    return (i < end && __ldg(colp + i) == key) ? i : -1;
+}
+
+template <bool MAXW>
+__global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uint8_t *considered) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < a.n; u += nw) {
+        const int64_t ou = __ldg(a.offp + u), d = __ldg(a.offp + u + 1) - ou;
+        for (int64_t i = lane; i < d; i += 32) {
+            const int64_t e = ou + i;
+            const unsigned long long r = a.resv[e];
+            if (r == ~0ull) continue;
+            const uint32_t y = __ldg(a.colp + e);
+            const uint32_t z = (uint32_t)r;
+            const unsigned long long hi = r & 0xFFFFFFFF00000000ull;
+            const int64_t f1 = arc_between(off, a.offp, a.colp, (uint32_t)u, z);
+            const int64_t f2 = arc_between(off, a.offp, a.colp, y, z);
+            if (f1 < 0 || f2 < 0) continue;
+            if (a.resv[f1] != (hi | y) || a.resv[f2] != (hi | (uint32_t)u)) continue;
+            considered[e] = 1;
+            // which edge of the accepted triangle goes
+            uint32_t x0 = (uint32_t)u, x1 = y, x2 = z;
+            int64_t e01 = e, e02 = f1, e12 = f2;
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            int64_t chosen;
+            if constexpr (MAXW) {
+                const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
+                chosen = e01;
+                float bw = w01;
+                uint32_t bl = x0, bh = x1;
+                if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { chosen = e02; bw = w02; bl = x0; bh = x2; }
+                if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { chosen = e12; }
+            } else {
+                const uint4 rr = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), a.k0, a.k1);
+                const int k = (int)(((unsigned long long)rr.y * 3ull) >> 32);
+                chosen = k == 0 ? e01 : (k == 1 ? e02 : e12);
+            }
+            if (chosen == e) a.del[e] = 1;
+        }
+    }
+}
+
+// -------------------------------------------------------------------- host
+struct Plan {
+    uint32_t *heavy = nullptr;
+    int64_t n_heavy = 0, max_deg = 0;
+    int log_slots = 3;
+    size_t heavy_smem = 0;
+};
+
+static sg_status read_ctr(Ctx *c, int first, int count, unsigned long long *out) {
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, c->d_ctr + first, sizeof(unsigned long long) * count,
+                            cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, c->h_pinned, sizeof(unsigned long long) * count);
+    return SG_OK;
+}
+
+static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
+    sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    if (st != SG_OK) return st;
+    // per-call counters only: the probe and triangle totals accumulate
+    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrHeavy, 0, sizeof(unsigned long long) * 2, c->stream));
+    if (o.n > 0) {
+        const int64_t blocks = std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8);
+        SG_LAUNCH(c, "tri_classify");
+        classify_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->heavy, c->d_ctr);
+    }
+    SG_CUDA(cudaGetLastError());
+    unsigned long long v[kCtrCount];
+    st = read_ctr(c, 0, kCtrCount, v);
+    if (st != SG_OK) return st;
+    pl->n_heavy = (int64_t)v[kCtrHeavy];
+    pl->max_deg = (int64_t)v[kCtrMaxDeg];
+    if (pl->max_deg > 65535)
+        return fail(SG_ERR_UNSUPPORTED, "an oriented out-degree above 65535 is not supported");
+    const size_t queue_bytes = sizeof(HitQueue) * kTW;
+    int ls = 3;
+    while ((1ll << ls) < 4 * std::max<int64_t>(pl->max_deg, 2)) ++ls;
+    const size_t limit = 220 * 1024;
+    while (ls > 3 && queue_bytes + (size_t)(1ll << ls) * 6 > limit && (1ll << (ls - 1)) >= 2 * pl->max_deg) --ls;
+    if (queue_bytes + (size_t)(1ll << ls) * 6 > limit)
+        return fail(SG_ERR_UNSUPPORTED, "oriented out-degree too large for the shared-memory table");
+    pl->log_slots = ls;
+    pl->heavy_smem = queue_bytes + (size_t)(1ll << ls) * 6;
+    return SG_OK;
+}
+
+template <Mode M>
+static sg_status launch_enum(Ctx *c, const TriArgs &base, const Plan &pl) {
+    TriArgs a = base;
+    a.heavy = pl.heavy;
+    a.n_heavy = pl.n_heavy;
+    a.heavy_log_slots = pl.log_slots;
+    if (pl.n_heavy > 0) {
+        SG_CUDA(cudaFuncSetAttribute(tri_heavy_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pl.heavy_smem));
+        int per_sm = 0;
+        SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_heavy_kernel<M>, kTW * 32,
+                                                              pl.heavy_smem));
+        const int64_t grid = std::min<int64_t>(pl.n_heavy, (int64_t)c->num_sms * std::max(per_sm, 1));
+        SG_LAUNCH(c, "tri_heavy");
+        tri_heavy_kernel<M><<<(unsigned)grid, kTW * 32, pl.heavy_smem, c->stream>>>(a);
+    }
+    SG_CUDA(cudaGetLastError());
+    if (a.n > 0) {
+        int per_sm = 0;
+        SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_light_kernel<M>, kTW * 32, 0));
+        const int64_t grid = std::min<int64_t>((a.n + kTW - 1) / kTW, (int64_t)c->num_sms * std::max(per_sm, 1));
+        SG_LAUNCH(c, "tri_light");
+        tri_light_kernel<M><<<(unsigned)grid, kTW * 32, 0, c->stream>>>(a);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+static TriArgs base_args(Ctx *c, const Oriented &o) {
+    TriArgs a{};
+    a.offp = o.off;
+    a.colp = o.col;
+    a.wp = o.w;
+    a.n = o.n;
+    a.ctr = c->d_ctr;
+    return a;
+}
+
+sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed, uint8_t *del) {
+    Plan pl;
+    sg_status st = make_plan(c, o, &pl);
+    TriArgs a = base_args(c, o);
+    a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    a.k1 = (uint32_t)(seed >> 32);
+    a.tp = prob_threshold(p);
+    a.del = del;
+    uint8_t *considered = nullptr;
+    unsigned long long *resv = nullptr;
+    if (st == SG_OK && (k == SG_TR_RANDOM || k == SG_TR_MAXW)) {
+        st = (k == SG_TR_RANDOM) ? launch_enum<Mode::UnionRandom>(c, a, pl) : launch_enum<Mode::UnionMaxw>(c, a, pl);
+    } else if (st == SG_OK) {
+        const size_t m = (size_t)std::max<int64_t>(o.m, 1);
+        st = dalloc(c, (void **)&considered, m);
+        if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
+        if (st == SG_OK) {
+            SG_CUDA(cudaMemsetAsync(considered, 0, m, c->stream));
+            a.considered = considered;
+            a.resv = resv;
+        }
+        for (int round = 0; st == SG_OK; ++round) {
+            SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
+            SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+            st = launch_enum<Mode::EoReserve>(c, a, pl);
+            if (st != SG_OK) break;
+            unsigned long long live = 0;
+            st = read_ctr(c, kCtrLive, 1, &live);
+            if (st != SG_OK || live == 0) break;
+            ++c->eo_rounds;
+            const int64_t blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
+            {
+                SG_LAUNCH(c, "tri_eo_accept");
+                if (k == SG_TR_EO_MAXW)
+                    eo_accept_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a, g->off, considered);
+                else
+                    eo_accept_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            }
+            SG_CUDA(cudaGetLastError());
+            if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
+        }
+    }
+    dfree(c, considered);
+    dfree(c, resv);
+    dfree(c, pl.heavy);
+    return st;
+}
+
+sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg) {
+    (void)g;
+    Plan pl;
+    sg_status st = make_plan(c, o, &pl);
+    unsigned long long v0[2] = {0, 0}, v1[2] = {0, 0};
+    if (st == SG_OK) st = read_ctr(c, 0, 2, v0);
+    if (st == SG_OK) st = launch_enum<Mode::Count>(c, base_args(c, o), pl);
+    if (st == SG_OK) st = read_ctr(c, 0, 2, v1);
+    if (count) *count = (int64_t)(v1[kCtrTriangles] - v0[kCtrTriangles]);
+    if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
+    if (maxdeg) *maxdeg = pl.max_deg;
+    dfree(c, pl.heavy);
+    return st;
+}
+
+}  // namespace sg

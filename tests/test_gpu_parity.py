@@ -1,0 +1,236 @@
+"""CUDA path vs the CPU oracle, through the C-ABI.
+
+Compressed edge sets must match bit for bit (integer work); PageRank values
+and the KL divergence must lie within 1e-5 relative of the FP64 oracle
+(|kl - kl*| <= 1e-5 kl* + 1e-12); component counts must match exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["uniform", "spectral_logn", "spectral_avgdeg", "tr_random", "tr_eo"]
+WKERNELS = ["tr_maxw", "tr_eo_maxw"]
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import paper_1912_08950_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sg):
+    assert torch.cuda.is_available()
+    c = sg.Context(0)
+    yield c
+    c.close()
+
+
+def _same(sg, ctx, g, kern, p, seed, want_weights=False):
+    G = sg.Graph.from_csr(ctx, g)
+    H = sg.compress(G, kern, p, seed, want_weights)
+    off, col, w = H.download()
+    o_off, o_col, o_w = oracle.compress(g, kern, p, seed, want_weights)
+    assert np.array_equal(off, o_off), f"{kern} p={p} seed={seed}: offsets differ"
+    assert np.array_equal(col, o_col), f"{kern} p={p} seed={seed}: columns differ"
+    if o_w is not None or w is not None:
+        assert w is not None and o_w is not None
+        assert np.array_equal(w.view(np.uint32), o_w.view(np.uint32)), f"{kern}: weights differ"
+    H.free()
+    G.free()
+    return off, col
+
+
+# ------------------------------------------------------------- small graphs
+SMALL = {
+    "K3": gg.complete(3), "K4": gg.complete(4), "K7": gg.complete(7), "bowtie": gg.bowtie(),
+    "diamond": gg.diamond(), "star": gg.star(40), "path": gg.path(50), "cycle": gg.cycle(33),
+    "isolated": gg.from_edge_list(9, []), "one_edge": gg.from_edge_list(5, [(1, 3)]),
+    "gnp": gg.gnp(90, 0.2, 3), "union": gg.disjoint_union(gg.complete(5), gg.star(7), gg.path(4), gg.complete(3)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("kern", KERNELS)
+def test_small_graphs_bit_exact(sg, ctx, name, kern):
+    for p, seed in ((0.0, 1), (0.5, 2), (1.0, 3)):
+        _same(sg, ctx, SMALL[name], kern, p, seed)
+
+
+def test_empty_vertex_set(sg, ctx):
+    g = gg.from_edge_list(0, [])
+    for kern in KERNELS:
+        _same(sg, ctx, g, kern, 0.5, 1)
+
+
+# ------------------------------------------------- R-MAT scale 14 (workload)
+@pytest.fixture(scope="module")
+def rmat14():
+    return gg.rmat(14, 16, seed=1)
+
+
+@pytest.mark.parametrize("kern", ["uniform", "tr_random"])
+def test_rmat14_named_workload(sg, ctx, rmat14, kern):
+    _same(sg, ctx, rmat14, kern, 0.5, 1)
+
+
+@pytest.mark.parametrize("kern", KERNELS)
+@pytest.mark.parametrize("p", [0.2, 0.5, 0.8])
+def test_rmat14_all_kernels(sg, ctx, rmat14, kern, p):
+    _same(sg, ctx, rmat14, kern, p, 7)
+
+
+@pytest.mark.parametrize("kern", ["spectral_logn", "spectral_avgdeg"])
+def test_spectral_weights_bit_exact(sg, ctx, rmat14, kern):
+    _same(sg, ctx, rmat14, kern, 0.5, 3, want_weights=True)
+
+
+@pytest.mark.parametrize("kern", WKERNELS + ["uniform", "tr_random", "tr_eo"])
+def test_weighted_bit_exact(sg, ctx, kern):
+    g = gg.attach_weights(gg.rmat(12, 16, seed=4), seed=4)
+    _same(sg, ctx, g, kern, 0.6, 5)
+    _same(sg, ctx, g, kern, 1.0, 6)
+
+
+def test_maxw_preserves_mst(sg, ctx):
+    g = gg.attach_weights(gg.rmat(13, 16, seed=2), seed=2)
+    G = sg.Graph.from_csr(ctx, g)
+    for kern in WKERNELS:
+        H = sg.compress(G, kern, 1.0, 9)
+        off, col, w = H.download()
+        assert oracle.mst_weight_units((g.n, off, col, w)) == oracle.mst_weight_units(g)
+        assert sg.cc_count(H) == oracle.cc_count(g)
+        H.free()
+
+
+def test_rmat_seeds_and_scales(sg, ctx):
+    for scale, ef, seed in ((8, 8, 11), (11, 32, 12), (12, 4, 13), (15, 16, 14)):
+        g = gg.rmat(scale, ef, seed=seed)
+        for kern in KERNELS:
+            _same(sg, ctx, g, kern, 0.5, seed)
+
+
+def test_chung_lu_and_rgg(sg, ctx):
+    cl = gg.attach_weights(gg.chung_lu(13, 2.1, 32.0, seed=1), seed=1)
+    rg = gg.attach_weights(gg.rgg3d(12, 48.0, seed=1), seed=1)
+    for g in (cl, rg):
+        for kern in ["tr_maxw", "tr_eo", "tr_random", "uniform"]:
+            _same(sg, ctx, g, kern, 1.0 if kern == "tr_maxw" else 0.5, 2)
+
+
+def test_triangle_count(sg, ctx, rmat14):
+    for g in (rmat14, SMALL["K7"], SMALL["gnp"], SMALL["path"], gg.rgg3d(11, 48.0, seed=2)):
+        G = sg.Graph.from_csr(ctx, g)
+        assert sg.triangle_count(G) == oracle.triangle_count(g)
+        G.free()
+
+
+def test_deterministic_repeats(sg, ctx, rmat14):
+    G = sg.Graph.from_csr(ctx, rmat14)
+    ref = None
+    for _ in range(3):
+        H = sg.compress(G, "tr_eo", 0.5, 42)
+        out = H.download()[1]
+        H.free()
+        if ref is None:
+            ref = out
+        assert np.array_equal(ref, out)
+    G.free()
+
+
+# ---------------------------------------------------------------- analytics
+def _pr_check(sg, ctx, g):
+    G = sg.Graph.from_csr(ctx, g)
+    x, r = sg.pagerank(G)
+    ref, rr = oracle.pagerank(g)
+    x = x.cpu().numpy().astype(np.float64)
+    rel = np.abs(x - ref) / ref
+    assert rel.max() <= 1e-5, rel.max()
+    G.free()
+
+
+@pytest.mark.parametrize("name", ["star", "cycle", "union", "gnp", "isolated"])
+def test_pagerank_small(sg, ctx, name):
+    _pr_check(sg, ctx, SMALL[name])
+
+
+def test_pagerank_rmat14(sg, ctx, rmat14):
+    _pr_check(sg, ctx, rmat14)
+
+
+def test_pagerank_regular_is_uniform(sg, ctx):
+    G = sg.Graph.from_csr(ctx, gg.cycle(64))
+    x, _ = sg.pagerank(G)
+    assert torch.all(x == x[0]) and abs(float(x[0]) - 1 / 64) < 1e-9
+    G.free()
+
+
+@pytest.mark.parametrize("kern,p", [("uniform", 0.5), ("tr_eo", 0.5), ("tr_random", 0.8), ("spectral_avgdeg", 0.5)])
+def test_divergence_rmat14(sg, ctx, rmat14, kern, p):
+    G = sg.Graph.from_csr(ctx, rmat14)
+    H = sg.compress(G, kern, p, 3)
+    d = sg.divergence(G, H)
+    off, col, _ = H.download()
+    ref = oracle.divergence(rmat14, (rmat14.n, off, col, None))
+    assert abs(d["kl_bits"] - ref["kl_bits"]) <= 1e-5 * ref["kl_bits"] + 1e-12, (d["kl_bits"], ref["kl_bits"])
+    assert d["cc_g"] == ref["cc_g"] and d["cc_h"] == ref["cc_h"]
+    assert d["m_g"] == rmat14.m and d["m_h"] == col.size // 2
+    H.free()
+    G.free()
+
+
+def test_kl_of_identity_is_zero(sg, ctx, rmat14):
+    G = sg.Graph.from_csr(ctx, rmat14)
+    assert sg.divergence(G, G)["kl_bits"] == 0.0
+    G.free()
+
+
+def test_cc_labels(sg, ctx):
+    g = SMALL["union"]
+    G = sg.Graph.from_csr(ctx, g)
+    cnt, lab = sg.cc_count(G, labels=True)
+    n_ref, lab_ref = oracle.cc_count(g, return_labels=True)
+    assert cnt == n_ref
+    assert np.array_equal(lab.cpu().numpy().astype(np.int64), lab_ref)
+    G.free()
+
+
+# --------------------------------------------------------- argument checks
+def test_errors(sg, ctx):
+    g = gg.rmat(8, 8, seed=1)
+    G = sg.Graph.from_csr(ctx, g)
+    for bad in (-0.1, 1.5, float("nan")):
+        with pytest.raises(sg.SgError) as e:
+            sg.compress(G, "uniform", bad, 1)
+        assert e.value.status == sg.SG_ERR_INVALID_ARG
+    with pytest.raises(sg.SgError) as e:
+        sg.compress(G, "tr_maxw", 0.5, 1)
+    assert e.value.status == sg.SG_ERR_NEEDS_WEIGHTS
+    with pytest.raises(sg.SgError) as e:
+        sg.compress(G, 99, 0.5, 1)
+    assert e.value.status == sg.SG_ERR_INVALID_ARG
+    G.free()
+    # offsets that do not end at nnz fail validation
+    off = torch.tensor([0, 1, 1, 1], dtype=torch.int64)
+    with pytest.raises(sg.SgError) as e:
+        sg.Graph.from_tensors(ctx, 3, off.cuda(), torch.tensor([1, 2], dtype=torch.int32).cuda(), validate=True)
+    assert e.value.status == sg.SG_ERR_INVALID_GRAPH
+    # an asymmetric CSR fails validation
+    bad = gg.CSR(3, torch.tensor([0, 1, 2, 2]), torch.tensor([1, 2], dtype=torch.int32))
+    with pytest.raises(sg.SgError) as e:
+        sg.Graph.from_csr(ctx, bad, validate=True)
+    assert e.value.status == sg.SG_ERR_INVALID_GRAPH
+    # an unsorted row fails validation
+    bad = gg.CSR(3, torch.tensor([0, 2, 3, 4]), torch.tensor([2, 1, 0, 0], dtype=torch.int32))
+    with pytest.raises(sg.SgError):
+        sg.Graph.from_csr(ctx, bad, validate=True)
+    # the context is still usable afterwards
+    G = sg.Graph.from_csr(ctx, g, validate=True)
+    _ = sg.compress(G, "uniform", 0.5, 1)
+    G.free()
