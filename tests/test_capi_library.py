@@ -13,9 +13,9 @@ HEADER = os.path.join(ROOT, "include", "slimgraph.h")
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_1912_08950_gb300 import _build
+    import __graft_entry__
 
-    return _build.build()
+    return __graft_entry__._builder().build()
 
 
 def declared_functions():
