@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+    "rmat20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat14": dict(scale=14, ef=16, desc="R-MAT scale 14, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
 }
 METRIC = "input edges/s compressed (TR + CSR rebuild)"
@@ -133,7 +134,10 @@ def run_ours(args, rank, world):
     wl = WORKLOADS[args.workload]
     seed = 1 + rank  # independent replica per GPU; rank 0 is the named workload
     g = gg.rmat(wl["scale"], wl["ef"], seed=seed, device="cuda")
-    ctx = sg.Context(local)
+    torch.cuda.synchronize()
+    # the library runs on this stream; every timing event is recorded on it
+    stream = torch.cuda.Stream(local)
+    ctx = sg.Context(local, stream=stream)
     G = sg.Graph.from_csr(ctx, g, copy=True)
     n, m = G.n, G.m
     work = sg.tr_work(G)
@@ -157,7 +161,6 @@ def run_ours(args, rank, world):
     ctx.stats(reset=True)
     ctx.reset_profile()
     ctx.set_profiling(True)
-    stream = ctx.torch_stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     time.sleep(0.3)

@@ -130,6 +130,13 @@ sg_status sg_ctx_stats(sg_ctx *ctx, sg_stats *out, int reset);
 sg_status sg_ctx_set_profiling(sg_ctx *ctx, int on);
 sg_status sg_ctx_kernel_time(sg_ctx *ctx, const char *prefix, double *ms, int64_t *launches);
 sg_status sg_ctx_reset_profile(sg_ctx *ctx);
+/* Memory bound of the Edge-Once kernels.  They keep the live selected
+ * triangles in a device list (32 bytes per triangle) once it fits, so that
+ * later reservation rounds need no new enumeration.  records > 0 caps the list
+ * at that many triangles, 0 (default) sizes it at a quarter of free device
+ * memory, -1 disables it (every round then enumerates the triangles again).
+ * The result is the same in every setting; only time and memory change. */
+sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records);
 
 /* ----------------------------------------------------------------- graphs */
 

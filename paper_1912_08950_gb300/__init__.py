@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -64,6 +64,7 @@ _SIGS = {
     "sg_ctx_set_profiling": [_vp, _int],
     "sg_ctx_kernel_time": [_vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "sg_ctx_reset_profile": [_vp],
+    "sg_ctx_set_eo_list_capacity": [_vp, _i64],
     "sg_graph_from_device": [_vp, C.POINTER(CsrView), _int, _int, _PP],
     "sg_graph_from_host": [_vp, _i64, _i64, _vp, _vp, _vp, _PP],
     "sg_graph_view": [_vp, C.POINTER(CsrView)],
@@ -115,14 +116,18 @@ class Context:
 
         self.device = device
         if stream is None:
-            stream = torch.cuda.current_stream(device)
+            stream = torch.cuda.Stream(device)
         self.torch_stream = stream
         h = C.c_void_p()
         _check(_lib.sg_ctx_create(device, C.c_void_p(stream.cuda_stream), C.byref(h)))
         self.handle = h
+        self._graphs = weakref.WeakSet()
 
     def close(self):
+        """Free every graph still alive on this context, then the context."""
         if getattr(self, "handle", None):
+            for g in list(self._graphs):
+                g.free()
             _lib.sg_ctx_destroy(self.handle)
             self.handle = None
 
@@ -151,6 +156,10 @@ class Context:
     def reset_profile(self):
         _check(_lib.sg_ctx_reset_profile(self.handle))
 
+    def set_eo_list_capacity(self, records: int):
+        """0: automatic, -1: no triangle list, > 0: at most that many triangles."""
+        _check(_lib.sg_ctx_set_eo_list_capacity(self.handle, int(records)))
+
 
 class Graph:
     """A device-resident symmetric CSR owned (or borrowed) by the library."""
@@ -159,6 +168,7 @@ class Graph:
         self.ctx = ctx
         self.handle = handle
         self._keep = keepalive
+        ctx._graphs.add(self)
         v = CsrView()
         _check(_lib.sg_graph_view(self.handle, C.byref(v)))
         self.n, self.nnz = v.n, v.nnz
@@ -180,6 +190,10 @@ class Graph:
     @classmethod
     def from_tensors(cls, ctx: Context, n: int, off, col, w=None, copy: bool = False, validate: bool = False):
         """Wrap (copy=False) or copy CUDA tensors: off int64[n+1], col int32/uint32[nnz], w float32[nnz]."""
+        import torch
+
+        # the tensors may still be in flight on the producer's stream
+        ctx.torch_stream.wait_stream(torch.cuda.current_stream(ctx.device))
         v = CsrView(n, col.numel(), off.data_ptr(), col.data_ptr(), None if w is None else w.data_ptr())
         h = C.c_void_p()
         _check(_lib.sg_graph_from_device(ctx.handle, C.byref(v), int(copy), int(validate), C.byref(h)))
@@ -206,6 +220,7 @@ class Graph:
         if getattr(self, "handle", None):
             _lib.sg_graph_free(self.handle)
             self.handle = None
+            self._keep = None
 
     def __del__(self):
         try:
@@ -240,6 +255,9 @@ def pagerank(g: Graph, damping: float = 0.85, iters: int = 50):
 
 
 def kl_divergence(ctx: Context, P, Q) -> float:
+    import torch
+
+    ctx.torch_stream.wait_stream(torch.cuda.current_stream(ctx.device))
     out = C.c_double()
     _check(_lib.sg_kl_divergence(ctx.handle, P.numel(), P.data_ptr(), Q.data_ptr(), C.byref(out)))
     return out.value

@@ -2,14 +2,26 @@
 // launch accounting and the dispatch of compress / divergence to the kernels.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_set>
 
 #include "sg_internal.cuh"
 
 namespace sg {
 
 static thread_local std::string g_last_error;
+
+// Contexts that are alive: a graph freed after its context was destroyed
+// must not touch the context's (freed) stream.
+static std::mutex g_ctx_mutex;
+static std::unordered_set<const Ctx *> g_live_ctx;
+
+static bool ctx_alive(const Ctx *c) {
+    std::lock_guard<std::mutex> lock(g_ctx_mutex);
+    return g_live_ctx.count(c) != 0;
+}
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -162,6 +174,10 @@ sg_status sg_ctx_create(int device, void *cuda_stream, sg_ctx **out) {
         sg_ctx_destroy(c);
         return st;
     }
+    {
+        std::lock_guard<std::mutex> lock(g_ctx_mutex);
+        g_live_ctx.insert(c);
+    }
     *out = c;
     return SG_OK;
 }
@@ -169,6 +185,10 @@ sg_status sg_ctx_create(int device, void *cuda_stream, sg_ctx **out) {
 void sg_ctx_destroy(sg_ctx *ctx) {
     if (!ctx) return;
     Ctx *c = C_(ctx);
+    {
+        std::lock_guard<std::mutex> lock(g_ctx_mutex);
+        g_live_ctx.erase(c);
+    }
     (void)cudaSetDevice(c->device);
     if (c->stream) (void)cudaStreamSynchronize(c->stream);
     for (auto &r : c->prof) {
@@ -218,6 +238,12 @@ sg_status sg_ctx_set_profiling(sg_ctx *ctx, int on) {
     return SG_OK;
 }
 
+sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records) {
+    if (!ctx || records < -1) return fail(SG_ERR_INVALID_ARG, "bad argument");
+    C_(ctx)->eo_list_cap = records;
+    return SG_OK;
+}
+
 sg_status sg_ctx_kernel_time(sg_ctx *ctx, const char *prefix, double *ms, int64_t *launches) {
     if (!ctx || !prefix || !ms || !launches) return fail(SG_ERR_INVALID_ARG, "NULL argument");
     Ctx *c = C_(ctx);
@@ -262,6 +288,7 @@ sg_status sg_graph_from_device(sg_ctx *ctx, const sg_csr_view *in, int copy, int
     sg_graph *g = new (std::nothrow) sg_graph;
     if (!g) return fail(SG_ERR_OOM, "host allocation failed");
     g->ctx = c;
+    g->device = c->device;
     g->n = in->n;
     g->nnz = in->nnz;
     if (!copy) {
@@ -307,6 +334,7 @@ sg_status sg_graph_from_host(sg_ctx *ctx, int64_t n, int64_t nnz, const int64_t 
     sg_graph *g = new (std::nothrow) sg_graph;
     if (!g) return fail(SG_ERR_OOM, "host allocation failed");
     g->ctx = c;
+    g->device = c->device;
     g->n = n;
     g->nnz = nnz;
     g->owned = true;
@@ -358,10 +386,17 @@ void sg_graph_free(sg_graph *g) {
     if (!g) return;
     if (g->owned && g->ctx) {
         Ctx *c = g->ctx;
-        (void)cudaSetDevice(c->device);
-        dfree(c, g->off);
-        dfree(c, g->col);
-        dfree(c, g->w);
+        if (ctx_alive(c)) {
+            (void)cudaSetDevice(c->device);
+            dfree(c, g->off);
+            dfree(c, g->col);
+            dfree(c, g->w);
+        } else {
+            // the context is gone: free synchronously, without its stream
+            (void)cudaSetDevice(g->device);
+            for (void *p : {(void *)g->off, (void *)g->col, (void *)g->w})
+                if (p) (void)cudaFree(p);
+        }
     }
     delete g;
 }

@@ -433,6 +433,7 @@ static sg_status read_i64(Ctx *c, const int64_t *dptr, int64_t *out) {
 static sg_status new_graph(Ctx *c, int64_t n, int64_t nnz_cap, bool weighted, Graph **out) {
     Graph *h = new Graph;
     h->ctx = c;
+    h->device = c->device;
     h->n = n;
     h->owned = true;
     sg_status st = dalloc(c, (void **)&h->off, sizeof(int64_t) * (size_t)(n + 1));

@@ -44,6 +44,7 @@ struct Ctx {
     int64_t *h_pinned = nullptr;           // pinned host scratch (small reads)
     uint64_t launches = 0;
     uint64_t eo_rounds = 0;
+    int64_t eo_list_cap = 0;               // 0 auto, -1 off, > 0 records
     bool profiling = false;
     std::vector<ProfRec> prof;             // events of launches since reset
     std::vector<cudaEvent_t> event_pool;   // recycled events
@@ -54,6 +55,7 @@ enum CtrIdx { kCtrProbes = 0, kCtrTriangles = 1, kCtrLive = 2, kCtrHeavy = 3, kC
 
 struct Graph {
     Ctx *ctx = nullptr;
+    int device = 0;
     int64_t n = 0, nnz = 0;
     int64_t *off = nullptr;
     uint32_t *col = nullptr;

@@ -53,7 +53,56 @@ struct TriArgs {
     const uint32_t *heavy;
     int64_t n_heavy;
     int heavy_log_slots;
+    // edge-once: optional list of the live selected triangles
+    struct TriRec *list;
+    unsigned long long *list_ctr;  // slots handed out (chunks of kChunk)
+    int64_t list_cap;
+    int *list_overflow;
 };
+
+// One live selected triangle: sorted original ids x0 < x1 < x2, its draws
+// r1 (edge choice) and r2 (edge-once order), and the oriented arcs joining
+// (x0,x1), (x0,x2), (x1,x2).  x0 == kSentinel marks an unused slot.
+struct __align__(16) TriRec {
+    uint32_t x0, x1, x2, r1;
+    uint32_t r2, e01, e02, e12;
+};
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;
+constexpr int kChunk = 1024;  // list slots a warp claims at a time
+
+// Per-warp list writer: claims chunks of kChunk slots, fills them in order and
+// seals the unused tail of a chunk with sentinels.
+struct Emitter {
+    unsigned long long cur = 0, end = 0;
+    bool dead = false;
+};
+
+__device__ __forceinline__ void emit_seal(const TriArgs &a, Emitter &em) {
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long i = em.cur + lane; i < em.end; i += 32) a.list[i].x0 = kSentinel;
+    em.cur = em.end;
+}
+
+__device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool want, const TriRec &rec) {
+    const unsigned bm = __ballot_sync(kFull, want);
+    if (!bm || em.dead) return;
+    const int cnt = __popc(bm);
+    if (em.end - em.cur < (unsigned long long)cnt) {
+        emit_seal(a, em);
+        unsigned long long base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(a.list_ctr, (unsigned long long)kChunk);
+        base = __shfl_sync(kFull, base, 0);
+        if (base + kChunk > (unsigned long long)a.list_cap) {
+            if ((threadIdx.x & 31) == 0) atomicExch(a.list_overflow, 1);
+            em.dead = true;
+            return;
+        }
+        em.cur = base;
+        em.end = base + kChunk;
+    }
+    if (want) a.list[em.cur + __popc(bm & lanemask_lt())] = rec;
+    em.cur += cnt;
+}
 
 struct HitQueue {
     uint32_t u[kQ], v[kQ], w[kQ];
@@ -74,39 +123,52 @@ __device__ __forceinline__ void swap2(T &a, T &b) {
 }
 
 // One triangle (u, v, w) with its three oriented arcs: selection and action.
+// Warp-collective (the edge-once list writer uses ballots); lanes without a
+// triangle pass valid = false.
 template <Mode M>
-__device__ __forceinline__ void decide(const TriArgs &a, uint32_t u, uint32_t v, uint32_t w, int64_t iuv,
-                                       int64_t iuw, int64_t ivw, unsigned &live) {
+__device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u, uint32_t v, uint32_t w,
+                                       int64_t iuv, int64_t iuw, int64_t ivw, unsigned &live, Emitter &em) {
     if constexpr (M == Mode::Count) {
         return;
     } else {
-        // sort the vertices, keeping e_ij = the arc joining x_i and x_j
-        uint32_t x0 = u, x1 = v, x2 = w;
-        int64_t e01 = iuv, e02 = iuw, e12 = ivw;
-        if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
-        if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
-        if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
-        const uint4 r = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), a.k0, a.k1);
-        if ((unsigned long long)r.x >= a.tp) return;  // triangle not selected
-        if constexpr (M == Mode::UnionRandom) {
-            const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
-            a.del[k == 0 ? e01 : (k == 1 ? e02 : e12)] = 1;
-        } else if constexpr (M == Mode::UnionMaxw) {
-            // heaviest edge under (weight, lo, hi)
-            const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
-            int64_t best = e01;
-            float bw = w01;
-            uint32_t bl = x0, bh = x1;
-            if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
-            if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
-            a.del[best] = 1;
-        } else {  // EoReserve
-            if (a.considered[e01] | a.considered[e02] | a.considered[e12]) return;
-            const unsigned long long hi = (unsigned long long)r.z << 32;
-            atomicMin(a.resv + e01, hi | x2);
-            atomicMin(a.resv + e02, hi | x1);
-            atomicMin(a.resv + e12, hi | x0);
-            ++live;
+        bool emit = false;
+        TriRec rec;
+        if (valid) {
+            // sort the vertices, keeping e_ij = the arc joining x_i and x_j
+            uint32_t x0 = u, x1 = v, x2 = w;
+            int64_t e01 = iuv, e02 = iuw, e12 = ivw;
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            const uint4 r = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), a.k0, a.k1);
+            if ((unsigned long long)r.x < a.tp) {  // the triangle is selected
+                if constexpr (M == Mode::UnionRandom) {
+                    const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
+                    a.del[k == 0 ? e01 : (k == 1 ? e02 : e12)] = 1;
+                } else if constexpr (M == Mode::UnionMaxw) {
+                    // heaviest edge under (weight, lo, hi)
+                    const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
+                    int64_t best = e01;
+                    float bw = w01;
+                    uint32_t bl = x0, bh = x1;
+                    if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
+                    if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
+                    a.del[best] = 1;
+                } else {  // EoReserve
+                    if (!(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
+                        const unsigned long long hi = (unsigned long long)r.z << 32;
+                        atomicMin(a.resv + e01, hi | x2);
+                        atomicMin(a.resv + e02, hi | x1);
+                        atomicMin(a.resv + e12, hi | x0);
+                        ++live;
+                        emit = true;
+                        rec = TriRec{x0, x1, x2, r.y, r.z, (uint32_t)e01, (uint32_t)e02, (uint32_t)e12};
+                    }
+                }
+            }
+        }
+        if constexpr (M == Mode::EoReserve) {
+            if (a.list != nullptr) emit_push(a, em, emit, rec);
         }
     }
 }
@@ -115,7 +177,7 @@ __device__ __forceinline__ void decide(const TriArgs &a, uint32_t u, uint32_t v,
 template <Mode M>
 __device__ __forceinline__ void push_hits(const TriArgs &a, HitQueue &q, int &qn, bool hit, uint32_t u, uint32_t v,
                                           uint32_t w, int64_t iuv, int64_t iuw, int64_t ivw, unsigned &live,
-                                          unsigned long long &tris) {
+                                          unsigned long long &tris, Emitter &em) {
     const unsigned hm = __ballot_sync(kFull, hit);
     if (!hm) return;
     const int lane = threadIdx.x & 31;
@@ -128,7 +190,7 @@ __device__ __forceinline__ void push_hits(const TriArgs &a, HitQueue &q, int &qn
     tris += hit ? 1 : 0;
     __syncwarp();
     if (qn >= 32) {
-        decide<M>(a, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live);
+        decide<M>(a, true, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live, em);
         __syncwarp();
         const int rest = qn - 32;
         if (lane < rest) {
@@ -141,9 +203,11 @@ __device__ __forceinline__ void push_hits(const TriArgs &a, HitQueue &q, int &qn
 }
 
 template <Mode M>
-__device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn, unsigned &live) {
+__device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn, unsigned &live, Emitter &em) {
     const int lane = threadIdx.x & 31;
-    if (lane < qn) decide<M>(a, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live);
+    const bool valid = lane < qn;
+    decide<M>(a, valid, valid ? q.u[lane] : 0u, valid ? q.v[lane] : 0u, valid ? q.w[lane] : 0u,
+              valid ? q.iuv[lane] : 0, valid ? q.iuw[lane] : 0, valid ? q.ivw[lane] : 0, live, em);
     __syncwarp();
 }
 
@@ -151,7 +215,8 @@ __device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn
 template <Mode M>
 __device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key, const uint16_t *idx, int log_slots,
                                            uint32_t u, int64_t ou, int i, uint32_t v, HitQueue &q, int &qn,
-                                           unsigned &live, unsigned long long &probes, unsigned long long &tris) {
+                                           unsigned &live, unsigned long long &probes, unsigned long long &tris,
+                                           Emitter &em) {
     const int lane = threadIdx.x & 31;
     const uint32_t mask = (1u << log_slots) - 1u;
     const int64_t ov = __ldg(a.offp + v);
@@ -171,7 +236,7 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key
                 s = (s + 1) & mask;
             }
         }
-        push_hits<M>(a, q, qn, hit, u, v, w, ou + i, ou + t, ov + j, live, tris);
+        push_hits<M>(a, q, qn, hit, u, v, w, ou + i, ou + t, ov + j, live, tris, em);
     }
 }
 
@@ -187,8 +252,11 @@ __device__ __forceinline__ void table_insert(uint32_t *key, uint16_t *idx, int l
 
 template <Mode M>
 __device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, unsigned live,
-                                       unsigned long long probes, unsigned long long tris) {
-    flush_hits<M>(a, q, qn, live);
+                                       unsigned long long probes, unsigned long long tris, Emitter &em) {
+    flush_hits<M>(a, q, qn, live, em);
+    if constexpr (M == Mode::EoReserve) {
+        if (a.list != nullptr && !em.dead) emit_seal(a, em);
+    }
     const unsigned long long P = warp_sum(probes), T = warp_sum(tris);
     const unsigned L = warp_sum(live);
     if ((threadIdx.x & 31) == 0) {
@@ -211,6 +279,7 @@ __global__ void __launch_bounds__(kTW * 32) tri_light_kernel(TriArgs a) {
     int qn = 0;
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
+    Emitter em;
     const int64_t nw = (int64_t)gridDim.x * kTW;
     for (int64_t u = (int64_t)blockIdx.x * kTW + warp; u < a.n; u += nw) {
         const int64_t ou = __ldg(a.offp + u);
@@ -228,11 +297,11 @@ __global__ void __launch_bounds__(kTW * 32) tri_light_kernel(TriArgs a) {
         for (int i = 0; i < d; ++i) {
             const uint32_t v = __shfl_sync(kFull, i < 32 ? n0 : n1, i & 31);
             if (M == Mode::EoReserve && a.considered[ou + i]) continue;
-            probe_list<M>(a, key, idx, log_slots, (uint32_t)u, ou, i, v, q, qn, live, probes, tris);
+            probe_list<M>(a, key, idx, log_slots, (uint32_t)u, ou, i, v, q, qn, live, probes, tris, em);
         }
         __syncwarp();
     }
-    finish<M>(a, q, qn, live, probes, tris);
+    finish<M>(a, q, qn, live, probes, tris, em);
 }
 
 // CTA per heavy vertex (d+(u) > kLightMax); the table lives in dynamic smem
@@ -247,6 +316,7 @@ __global__ void __launch_bounds__(kTW * 32) tri_heavy_kernel(TriArgs a) {
     int qn = 0;
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
+    Emitter em;
     for (int64_t h = blockIdx.x; h < a.n_heavy; h += gridDim.x) {
         const uint32_t u = __ldg(a.heavy + h);
         const int64_t ou = __ldg(a.offp + u);
@@ -263,10 +333,10 @@ __global__ void __launch_bounds__(kTW * 32) tri_heavy_kernel(TriArgs a) {
         for (int i = warp; i < d; i += kTW) {
             if (M == Mode::EoReserve && a.considered[ou + i]) continue;
             const uint32_t v = __ldg(a.colp + ou + i);
-            probe_list<M>(a, key, idx, log_slots, u, ou, i, v, q, qn, live, probes, tris);
+            probe_list<M>(a, key, idx, log_slots, u, ou, i, v, q, qn, live, probes, tris, em);
         }
     }
-    finish<M>(a, q, qn, live, probes, tris);
+    finish<M>(a, q, qn, live, probes, tris, em);
 }
 
 // heavy-vertex list and the maximum out-degree
@@ -354,6 +424,82 @@ __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uin
     }
 }
 
+// Edge-once rounds over the list of live selected triangles.
+// Accept: a triangle holding the reservations of all three of its edges is
+// accepted; accepted triangles are edge-disjoint, so their stores never race.
+template <bool MAXW>
+__global__ void eo_list_accept_kernel(const TriRec *__restrict__ L, int64_t len,
+                                      const unsigned long long *__restrict__ resv, uint8_t *considered,
+                                      uint8_t *del, const float *__restrict__ wp) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const TriRec r = L[i];
+        if (r.x0 == kSentinel) continue;
+        const unsigned long long hi = (unsigned long long)r.r2 << 32;
+        if (resv[r.e01] != (hi | r.x2) || resv[r.e02] != (hi | r.x1) || resv[r.e12] != (hi | r.x0)) continue;
+        considered[r.e01] = 1;
+        considered[r.e02] = 1;
+        considered[r.e12] = 1;
+        uint32_t chosen;
+        if constexpr (MAXW) {
+            const float w01 = __ldg(wp + r.e01), w02 = __ldg(wp + r.e02), w12 = __ldg(wp + r.e12);
+            chosen = r.e01;
+            float bw = w01;
+            uint32_t bl = r.x0, bh = r.x1;
+            if (w02 > bw || (w02 == bw && (r.x0 > bl || (r.x0 == bl && r.x2 > bh)))) { chosen = r.e02; bw = w02; bl = r.x0; bh = r.x2; }
+            if (w12 > bw || (w12 == bw && (r.x1 > bl || (r.x1 == bl && r.x2 > bh)))) { chosen = r.e12; }
+        } else {
+            const int k = (int)(((unsigned long long)r.r1 * 3ull) >> 32);
+            chosen = k == 0 ? r.e01 : (k == 1 ? r.e02 : r.e12);
+        }
+        del[chosen] = 1;
+    }
+}
+
+// Reserve: drop every triangle that lost an edge to an accepted one, reserve
+// the edges of the survivors (64-bit atomicMin of (r2, third vertex)) and
+// compact the survivors into `out` (block-aggregated appends).
+__global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__restrict__ L, int64_t len,
+                                                              TriRec *__restrict__ out,
+                                                              unsigned long long *out_len,
+                                                              unsigned long long *resv,
+                                                              const uint8_t *__restrict__ considered) {
+    __shared__ int s_cnt[8];
+    __shared__ unsigned long long s_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        TriRec r{kSentinel, 0, 0, 0, 0, 0, 0, 0};
+        if (i < len) {
+            r = L[i];
+            if (r.x0 != kSentinel && !(considered[r.e01] | considered[r.e02] | considered[r.e12])) {
+                keep = true;
+                const unsigned long long hi = (unsigned long long)r.r2 << 32;
+                atomicMin(resv + r.e01, hi | r.x2);
+                atomicMin(resv + r.e02, hi | r.x1);
+                atomicMin(resv + r.e12, hi | r.x0);
+            }
+        }
+        const unsigned bm = __ballot_sync(kFull, keep);
+        if (lane == 0) s_cnt[warp] = __popc(bm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int c = s_cnt[k];
+                s_cnt[k] = tot;
+                tot += c;
+            }
+            s_base = tot ? atomicAdd(out_len, (unsigned long long)tot) : 0ull;
+        }
+        __syncthreads();
+        if (keep) out[s_base + s_cnt[warp] + __popc(bm & lanemask_lt())] = r;
+        __syncthreads();
+    }
+}
+
 // -------------------------------------------------------------------- host
 struct Plan {
     uint32_t *heavy = nullptr;
@@ -438,6 +584,122 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
     return a;
 }
 
+// Edge-once rounds.  While no list is held, a round enumerates the triangles
+// (reserving the edges of every live selected triangle) and also writes those
+// triangles to a list if it fits the memory budget; rounds then continue on the
+// shrinking list alone.  A round whose list overflowed accepts through the
+// edge pass and the next round enumerates again.
+static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
+    const size_t m = (size_t)std::max<int64_t>(o.m, 1);
+    const bool maxw = (k == SG_TR_EO_MAXW);
+    uint8_t *considered = nullptr;
+    unsigned long long *resv = nullptr, *lctr = nullptr;
+    int *lovf = nullptr;
+    TriRec *LA = nullptr, *LB = nullptr;
+    int64_t capA = 0, lenA = 0;
+    bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
+    sg_status st = dalloc(c, (void **)&considered, m);
+    if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
+    if (st == SG_OK) st = dalloc(c, (void **)&lctr, 2 * sizeof(unsigned long long) + sizeof(int));
+    if (st == SG_OK) {
+        lovf = reinterpret_cast<int *>(lctr + 2);
+        if (cudaMemsetAsync(considered, 0, m, c->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+    }
+    a.considered = considered;
+    a.resv = resv;
+    const int64_t acc_blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
+    for (int round = 0; st == SG_OK; ++round) {
+        if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
+        if (cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "memset");
+            break;
+        }
+        unsigned long long live = 0;
+        if (LA == nullptr) {
+            // enumeration round, writing the list when it fits
+            a.list = nullptr;
+            if (use_list) {
+                size_t fr = 0, tot = 0;
+                if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+                capA = (int64_t)(fr / 4 / sizeof(TriRec));
+                if (c->eo_list_cap > 0) capA = std::min<int64_t>(capA, c->eo_list_cap);
+                if (capA >= 4 * kChunk && dalloc(c, (void **)&LA, (size_t)capA * sizeof(TriRec)) == SG_OK) {
+                    a.list = LA;
+                    a.list_ctr = lctr;
+                    a.list_cap = capA;
+                    a.list_overflow = lovf;
+                    SG_CUDA(cudaMemsetAsync(lctr, 0, 2 * sizeof(unsigned long long) + sizeof(int), c->stream));
+                } else {
+                    LA = nullptr;
+                    set_error("");
+                }
+            }
+            SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+            st = launch_enum<Mode::EoReserve>(c, a, pl);
+            if (st != SG_OK) break;
+            st = read_ctr(c, kCtrLive, 1, &live);
+            if (st != SG_OK || live == 0) break;
+            if (a.list != nullptr) {
+                unsigned long long used = 0;
+                int ovf = 0;
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned + 1, lovf, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaStreamSynchronize(c->stream));
+                std::memcpy(&used, c->h_pinned, sizeof(used));
+                std::memcpy(&ovf, c->h_pinned + 1, sizeof(int));
+                if (ovf) {
+                    dfree(c, LA);
+                    LA = nullptr;
+                } else {
+                    lenA = (int64_t)std::min<unsigned long long>(used, (unsigned long long)capA);
+                }
+            }
+            a.list = nullptr;
+        } else {
+            // list round: drop dead triangles, reserve, compact into LB
+            if (LB == nullptr) {
+                st = dalloc(c, (void **)&LB, (size_t)std::max<int64_t>(lenA, 1) * sizeof(TriRec));
+                if (st != SG_OK) break;
+            }
+            SG_CUDA(cudaMemsetAsync(lctr, 0, sizeof(unsigned long long), c->stream));
+            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
+            if (blocks > 0) {
+                SG_LAUNCH(c, "tri_eo_list_reserve");
+                eo_list_reserve_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, LB, lctr, resv, considered);
+            }
+            SG_CUDA(cudaGetLastError());
+            SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+            SG_CUDA(cudaStreamSynchronize(c->stream));
+            std::memcpy(&live, c->h_pinned, sizeof(live));
+            if (live == 0) break;
+            std::swap(LA, LB);
+            lenA = (int64_t)live;
+        }
+        ++c->eo_rounds;
+        if (LA != nullptr) {
+            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
+            SG_LAUNCH(c, "tri_eo_list_accept");
+            if (maxw)
+                eo_list_accept_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered, a.del, a.wp);
+            else
+                eo_list_accept_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered, a.del, a.wp);
+        } else {
+            SG_LAUNCH(c, "tri_eo_accept");
+            if (maxw)
+                eo_accept_kernel<true><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            else
+                eo_accept_kernel<false><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+        }
+        SG_CUDA(cudaGetLastError());
+    }
+    dfree(c, LA);
+    dfree(c, LB);
+    dfree(c, lctr);
+    dfree(c, considered);
+    dfree(c, resv);
+    return st;
+}
+
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed, uint8_t *del) {
     Plan pl;
     sg_status st = make_plan(c, o, &pl);
@@ -446,42 +708,11 @@ sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double
     a.k1 = (uint32_t)(seed >> 32);
     a.tp = prob_threshold(p);
     a.del = del;
-    uint8_t *considered = nullptr;
-    unsigned long long *resv = nullptr;
     if (st == SG_OK && (k == SG_TR_RANDOM || k == SG_TR_MAXW)) {
         st = (k == SG_TR_RANDOM) ? launch_enum<Mode::UnionRandom>(c, a, pl) : launch_enum<Mode::UnionMaxw>(c, a, pl);
     } else if (st == SG_OK) {
-        const size_t m = (size_t)std::max<int64_t>(o.m, 1);
-        st = dalloc(c, (void **)&considered, m);
-        if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
-        if (st == SG_OK) {
-            SG_CUDA(cudaMemsetAsync(considered, 0, m, c->stream));
-            a.considered = considered;
-            a.resv = resv;
-        }
-        for (int round = 0; st == SG_OK; ++round) {
-            SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
-            SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
-            st = launch_enum<Mode::EoReserve>(c, a, pl);
-            if (st != SG_OK) break;
-            unsigned long long live = 0;
-            st = read_ctr(c, kCtrLive, 1, &live);
-            if (st != SG_OK || live == 0) break;
-            ++c->eo_rounds;
-            const int64_t blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
-            {
-                SG_LAUNCH(c, "tri_eo_accept");
-                if (k == SG_TR_EO_MAXW)
-                    eo_accept_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a, g->off, considered);
-                else
-                    eo_accept_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(a, g->off, considered);
-            }
-            SG_CUDA(cudaGetLastError());
-            if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
-        }
+        st = eo_rounds(c, g, o, k, pl, a);
     }
-    dfree(c, considered);
-    dfree(c, resv);
     dfree(c, pl.heavy);
     return st;
 }

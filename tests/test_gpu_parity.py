@@ -131,6 +131,19 @@ def test_triangle_count(sg, ctx, rmat14):
         G.free()
 
 
+@pytest.mark.parametrize("cap", [-1, 4096, 60000, 0])
+@pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw"])
+def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
+    # -1: enumerate every round; small caps overflow and fall back to the edge
+    # pass, then retry the list in a later round; 0: automatic
+    g = gg.attach_weights(gg.rmat(13, 16, seed=8), seed=8)
+    ctx.set_eo_list_capacity(cap)
+    try:
+        _same(sg, ctx, g, kern, 0.7, 4)
+    finally:
+        ctx.set_eo_list_capacity(0)
+
+
 def test_deterministic_repeats(sg, ctx, rmat14):
     G = sg.Graph.from_csr(ctx, rmat14)
     ref = None
