@@ -197,6 +197,30 @@ sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out);
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out,
                      int64_t *max_out_degree, int64_t *triangles_out);
 
+/* ------------------------------------------------- no-allocation variant */
+
+/* Uniform edge sampling (SG_UNIFORM) that allocates no device memory.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc -- for example a host framework whose own allocator owns the
+ * whole GPU memory budget and must account for every byte, or a caller that
+ * reserved device memory up front and cannot let a library grow it.  Such a
+ * caller passes device buffers for the input CSR (off[n+1], col[nnz]) and for
+ * the output (off_out[n+1], col_out with room for nnz arcs, since the output
+ * is a subset of the input); the result equals sg_compress(G, SG_UNIFORM, p,
+ * seed) bit for bit and *nnz_out (host) receives its arc count.
+ * Scratch lives in one fixed device array inside the library (about 3 MB per
+ * GPU that loads it, held until the process exits), which caps the input at
+ * nnz <= 134217728 arcs; larger inputs return SG_ERR_UNSUPPORTED.
+ * The first call on a device looks up that array's device address; make the
+ * first call before any stream capture.  The call synchronises cuda_stream.
+ * All calls share the one array: calls that overlap on the GPU (different
+ * streams, threads or processes sharing the library) race and must be
+ * serialised by the caller.  No context is needed; errors are reported as by
+ * every other entry point (sg_last_error). */
+sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz, const int64_t *off,
+                                      const uint32_t *col, double p, uint64_t seed, int64_t *off_out,
+                                      uint32_t *col_out, int64_t *nnz_out);
+
 /* Message describing the last non-OK status returned on this thread. */
 const char *sg_last_error(void);
 

@@ -75,6 +75,7 @@ _SIGS = {
     "sg_kl_divergence": [_vp, _i64, _vp, _vp, C.POINTER(C.c_double)],
     "sg_cc_count": [_vp, _vp, C.POINTER(C.c_int64), _vp],
     "sg_triangle_count": [_vp, _vp, C.POINTER(C.c_int64)],
+    "sg_compress_uniform_noalloc": [_int, _vp, _i64, _i64, _vp, _vp, _dbl, _u64, _vp, _vp, C.POINTER(C.c_int64)],
     "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                    C.POINTER(C.c_int64)],
 }

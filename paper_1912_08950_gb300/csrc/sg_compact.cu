@@ -19,6 +19,8 @@
 // atomic ticket, so a CTA only ever waits on tiles already owned by running
 // CTAs; every wait is bounded and reports a device error instead of hanging.
 #include <climits>
+#include <mutex>
+#include <string>
 
 #include "sg_internal.cuh"
 
@@ -550,3 +552,119 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
 }
 
 }  // namespace sg
+
+// ------------------------------------------------ no-allocation entry point
+// Uniform edge sampling for callers that must not allocate device memory:
+// the scratch (row maps, tile status words, the tile ticket and an error
+// word) lives in one fixed file-scope device array instead of the stream-
+// ordered pool.  Every process that loads this library reserves the array on
+// each GPU it touches, for as long as the library stays loaded.
+namespace sg {
+namespace {
+
+constexpr int64_t kNaMaxArcs = int64_t(1) << 27;
+constexpr int64_t kNaMaxChunks = kNaMaxArcs / kWarpSpan;
+constexpr int64_t kNaMaxTiles = kNaMaxArcs / kTile;
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNaChunkOff = 0;
+constexpr size_t kNaTileOff = na_align(kNaChunkOff + sizeof(uint32_t) * (kNaMaxChunks + 1));
+constexpr size_t kNaStatusOff = na_align(kNaTileOff + sizeof(int64_t) * (kNaMaxTiles + 1));
+constexpr size_t kNaErrOff = na_align(kNaStatusOff + sizeof(unsigned long long) * (kNaMaxTiles + 1));
+constexpr size_t kNaBytes = na_align(kNaErrOff + sizeof(int));
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+// Looked up once per device and cached.
+cudaError_t na_scratch(int device, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_na_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz,
+                                                 const int64_t *off, const uint32_t *col, double p, uint64_t seed,
+                                                 int64_t *off_out, uint32_t *col_out, int64_t *nnz_out) {
+    using namespace sg;
+    if (!off || !off_out || !nnz_out || (nnz > 0 && (!col || !col_out)))
+        return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || nnz < 0) return fail(SG_ERR_INVALID_ARG, "negative size");
+    if (!(p >= 0.0 && p <= 1.0)) return fail(SG_ERR_INVALID_ARG, "p must lie in [0, 1]");
+    if (n >= (int64_t)4294967295ll) return fail(SG_ERR_UNSUPPORTED, "n >= 2^32 - 1: ids are uint32");
+    if (nnz > kNaMaxArcs)
+        return fail(SG_ERR_UNSUPPORTED, "nnz = " + std::to_string(nnz) +
+                                            " exceeds the 134217728-arc limit of the fixed scratch array; "
+                                            "use sg_compress instead");
+    int ndev = 0;
+    SG_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev || device >= kNaMaxDevices) return fail(SG_ERR_INVALID_ARG, "no such device");
+    SG_CUDA(cudaSetDevice(device));
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    unsigned char *base = nullptr;
+    SG_CUDA(na_scratch(device, &base));
+    int *err = reinterpret_cast<int *>(base + kNaErrOff);
+    SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), stream));
+    *nnz_out = 0;
+    if (nnz == 0) {
+        SG_CUDA(cudaMemsetAsync(off_out, 0, sizeof(int64_t) * (size_t)(n + 1), stream));
+        SG_CUDA(cudaStreamSynchronize(stream));
+        return SG_OK;
+    }
+    int num_sms = 0;
+    SG_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+    const int64_t num_tiles = (nnz + kTile - 1) / kTile;
+    const int64_t num_chunks = (nnz + kWarpSpan - 1) / kWarpSpan;
+    uint32_t *chunk_row = reinterpret_cast<uint32_t *>(base + kNaChunkOff);
+    int64_t *tile_vlo = reinterpret_cast<int64_t *>(base + kNaTileOff);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(base + kNaStatusOff);
+    // the status words and the ticket must start at zero on every call
+    SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(num_tiles + 1), stream));
+    const int64_t rb = std::min<int64_t>((n + 1 + 255) / 256, (int64_t)num_sms * 16);
+    row_maps_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, stream>>>(off, n, chunk_row, num_chunks, tile_vlo,
+                                                                           num_tiles);
+    SG_CUDA(cudaGetLastError());
+    CompactArgs a;
+    a.off = off;
+    a.col = col;
+    a.w = nullptr;
+    a.n = n;
+    a.nnz = nnz;
+    a.num_tiles = num_tiles;
+    a.chunk_row = chunk_row;
+    a.tile_vlo = tile_vlo;
+    a.off_out = off_out;
+    a.col_out = col_out;
+    a.w_out = nullptr;
+    a.status = status;
+    a.ticket = reinterpret_cast<unsigned int *>(status + num_tiles);
+    a.err = err;
+    a.keep_bits = nullptr;
+    UniformPol pol{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), prob_threshold(p)};
+    int per_sm = 0;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<UniformPol>, CW * 32, 0));
+    const int64_t grid = std::min<int64_t>(num_tiles, (int64_t)num_sms * std::max(per_sm, 1));
+    compact_kernel<UniformPol><<<(unsigned)grid, CW * 32, 0, stream>>>(a, pol);
+    SG_CUDA(cudaGetLastError());
+    int64_t count = 0;
+    int code = 0;
+    SG_CUDA(cudaMemcpyAsync(&count, off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    SG_CUDA(cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SG_CUDA(cudaStreamSynchronize(stream));
+    if (code != kDevOk) return fail(SG_ERR_TIMEOUT, "a device-side wait of the prefix scan gave up; outputs are invalid");
+    *nnz_out = count;
+    return SG_OK;
+}
+
