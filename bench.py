@@ -175,11 +175,11 @@ def run_ours(args, rank, world):
     ms = ev0.elapsed_time(ev1) / args.steps
     st = ctx.stats()
     kt = {}
-    for name in ("tri_light", "tri_heavy", "tri_eo_accept", "tri_classify", "compact_orient", "compact_trmask",
-                 "row_maps"):
+    for name in ("tri_enum", "tri_eo_list_reserve", "tri_eo_list_accept", "tri_eo_accept", "tri_classify",
+                 "compact_orient", "compact_trmask", "row_maps"):
         kt[name] = ctx.kernel_time(name)
-    enum_ms = kt["tri_light"][0] + kt["tri_heavy"][0]
-    enum_launches = max(kt["tri_light"][1], 1)  # one enumeration pass = light + heavy launch
+    enum_ms = kt["tri_enum"][0]
+    enum_launches = max(kt["tri_enum"][1], 1)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -297,6 +297,147 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def _digest(graphs, sync_stream):
+    """Order-sensitive digest of many device CSRs, computed on the GPU."""
+    import torch
+
+    torch.cuda.current_stream().wait_stream(sync_stream)
+    acc = torch.zeros((), dtype=torch.int64, device="cuda")
+    for i, g in enumerate(graphs):
+        off, col, _ = g.tensors()
+        c = col.to(torch.int64)
+        idx = torch.arange(c.numel(), device="cuda", dtype=torch.int64)
+        acc = acc * 1000003 + (c * (idx * 2654435761 % 1000000007 + 1)).sum() + off.sum() * 31 + i
+        acc = acc % (1 << 61)
+    return int(acc.item())
+
+
+def run_batch(args):
+    """Batched compression of many R-MAT graphs vs the plain one-call-per-graph loop."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_1912_08950_gb300 as sg
+
+    torch.cuda.set_device(0)
+    G = args.batch_graphs
+    rng = np.random.default_rng(7)
+    scales = [int(round(8 + 8 * u)) for u in rng.random(G)]
+    efs = [int(e) for e in rng.integers(8, 33, size=G)]
+    seeds = [i + 1 for i in range(G)]
+    ps = [float(x) for x in rng.choice([0.2, 0.5, 0.8], size=G)]
+    kernels = [("uniform", "spectral_avgdeg", "tr_random")[i % 3] for i in range(G)]
+    t0 = time.perf_counter()
+    u, vbase, _ = gg.rmat_batch(scales, efs, seeds, device="cuda")
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    ctx = sg.Context(0, stream=stream)
+    graphs = [sg.Graph.from_csr(ctx, gg.batch_member(u, vbase, i, 1 << scales[i]), copy=True) for i in range(G)]
+    del u
+    m_total = sum(g.m for g in graphs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def plain():
+        return [sg.compress(graphs[i], kernels[i], ps[i], seeds[i]) for i in range(G)]
+
+    for _ in range(max(1, args.warmup // 2)):
+        for h in plain():
+            h.free()
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ev[0].record(stream)
+    reps = max(1, args.steps // 2)
+    for _ in range(reps):
+        outs = plain()
+        if _ < reps - 1:
+            for h in outs:
+                h.free()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1]) / reps
+    plain_launches = ctx.stats(reset=True)["kernel_launches"] / reps
+    d_plain = _digest(outs, stream)
+    for h in outs:
+        h.free()
+    B = sg.Batch(ctx, graphs)
+    t0 = time.perf_counter()
+    outs_b = B.compress(kernels, ps, seeds)  # first call: autotune + capture
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        outs_b = B.compress(kernels, ps, seeds)
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ev[2].record(stream)
+    for _ in range(args.steps):
+        outs_b = B.compress(kernels, ps, seeds)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    batch_ms = ev[2].elapsed_time(ev[3]) / args.steps
+    batch_launches = ctx.stats(reset=True)["kernel_launches"] / args.steps
+    d_batch = _digest(outs_b, stream)
+    info = B.info()
+    print(json.dumps({
+        "mode": "batch", "metric": METRIC + ", batched vs plain", "unit": "edges/s",
+        "value": m_total / (batch_ms / 1e3), "plain_value": m_total / (plain_ms / 1e3),
+        "speedup": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
+        "identical_outputs": d_plain == d_batch, "graphs": G, "m_total": m_total,
+        "gpu_launches_per_call": {"batch": batch_launches, "plain": plain_launches},
+        "autotune": info, "autotune_s": tune_s, "generation_s": gen_s, "steps": args.steps,
+        "config": {"workload": f"{G} R-MAT graphs, scale round(8+8u) u~U[0,1), ef~U{{8..32}}, seed i+1, "
+                               "p~U{0.2,0.5,0.8}, kernel round-robin uniform/spectral_avgdeg/tr_random"},
+    }), flush=True)
+    B.free()
+    ctx.close()
+
+
+def run_serve(args):
+    """Continuous-batching serving of compress + divergence jobs with Poisson arrivals."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    from paper_1912_08950_gb300.serve import GpuExecutor, Job, Server, poisson_arrivals, replay
+
+    rng = np.random.default_rng(5)
+    pool = {}
+    for s in range(args.serve_min_scale, args.serve_max_scale + 1):
+        g = gg.rmat(s, 16, seed=s, device="cuda")
+        off, col, _ = g.numpy()
+        pool[s] = (g.n, np.ascontiguousarray(off), np.ascontiguousarray(col))
+    kern = ["uniform", "spectral_avgdeg", "tr_random", "tr_eo"]
+
+    def make_jobs(count, seed):
+        r = np.random.default_rng(seed)
+        jobs = []
+        for i in range(count):
+            s = int(r.integers(args.serve_min_scale, args.serve_max_scale + 1))
+            n, off, col = pool[s]
+            jobs.append(Job(n=n, off=off, col=col, kernel=kern[int(r.integers(0, 4))],
+                            p=float(r.choice([0.2, 0.5, 0.8])), seed=i + 1))
+        return jobs
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.6)
+    slots = args.serve_slots
+    res = {}
+    for label, rate in (("offered", args.serve_rate), ("capacity70", None)):
+        if rate is None:
+            rate = 0.7 * res["offered"]["jobs_per_s"]
+        srv = Server(lambda i: GpuExecutor(0), slots=slots, memory_budget=budget)
+        jobs = make_jobs(args.serve_jobs, 11)
+        out = replay(srv, jobs, poisson_arrivals(rate, len(jobs), seed=3))
+        srv.close()
+        out.pop("results")
+        out["rate"] = rate
+        res[label] = out
+    print(json.dumps({"mode": "serve", "slots": slots, "memory_budget": budget, **res,
+                      "config": {"workload": f"Poisson arrivals; jobs = compress + KL/CC on R-MAT scale "
+                                             f"U{{{args.serve_min_scale}..{args.serve_max_scale}}} ef 16; "
+                                             "kernels uniform/spectral_avgdeg/tr_random/tr_eo, p~U{0.2,0.5,0.8}"}}),
+          flush=True)
+
+
 def _oracle_sample(kernel, p):
     """One bounded oracle run: the same generator at scale 16 (a 64x smaller sample)."""
     import graphgen as gg
@@ -350,7 +491,18 @@ def main():
     ap.add_argument("--kernel", default="tr_eo")
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--mode", choices=["compress", "batch", "serve"], default="compress")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-jobs", type=int, default=300)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-min-scale", type=int, default=10)
+    ap.add_argument("--serve-max-scale", type=int, default=22)
     args = ap.parse_args()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", 0))

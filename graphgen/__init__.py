@@ -85,10 +85,14 @@ def _mix32(x: torch.Tensor) -> torch.Tensor:
     return x
 
 
-def draw32(seed: int, stream: int, ctr: torch.Tensor, sub: int = 0) -> torch.Tensor:
-    """Uniform 32-bit values (int64 tensor) for counters ``ctr`` (int64, >= 0)."""
-    s = _mix32(torch.full((), ((seed & M32) ^ (seed >> 32) * 0x5851F42D) & M32,
-                          dtype=torch.int64, device=ctr.device))
+def draw32(seed, stream: int, ctr: torch.Tensor, sub: int = 0) -> torch.Tensor:
+    """Uniform 32-bit values (int64 tensor) for counters ``ctr`` (int64, >= 0).
+    ``seed`` is an int or an int64 tensor broadcastable against ``ctr``."""
+    if isinstance(seed, torch.Tensor):
+        s = _mix32(((seed & M32) ^ ((seed >> 32) * 0x5851F42D)) & M32)
+    else:
+        s = _mix32(torch.full((), ((seed & M32) ^ (seed >> 32) * 0x5851F42D) & M32,
+                              dtype=torch.int64, device=ctr.device))
     s = _mix32((s + stream) & M32)
     h = _mix32((s + (ctr & M32)) & M32)
     h = _mix32((h + ((ctr >> 32) & M32) + 0x3C6EF372) & M32)
@@ -159,6 +163,64 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
         perm = _permutation(n, seed, device)
         src, dst = perm[src], perm[dst]
     return csr_from_edges(n, src, dst)
+
+
+def rmat_batch(scales, efs, seeds, a: float = 0.57, b: float = 0.19, c: float = 0.19, device="cpu"):
+    """Many R-MAT graphs at once, as one disjoint union CSR.
+
+    Graph i equals rmat(scales[i], efs[i], seed=seeds[i]) exactly; its vertices
+    occupy [vbase[i], vbase[i] + 2**scales[i]) of the union.  Returns
+    (union CSR, vbase, abase) with abase[i] = offset of graph i's first arc."""
+    G = len(scales)
+    sc = torch.tensor(scales, dtype=torch.int64, device=device)
+    ef = torch.tensor(efs, dtype=torch.int64, device=device)
+    sd = torch.tensor(seeds, dtype=torch.int64, device=device)
+    nv = torch.ones_like(sc) << sc
+    vbase = torch.zeros(G, dtype=torch.int64, device=device)
+    vbase[1:] = torch.cumsum(nv, 0)[:-1]
+    n_total = int(nv.sum().item())
+    counts = ef * nv
+    gi = torch.repeat_interleave(torch.arange(G, device=device), counts)
+    start = torch.cumsum(counts, 0) - counts
+    ei = torch.arange(gi.numel(), dtype=torch.int64, device=device) - start[gi]
+    ta = int(math.floor(a * 2**32))
+    tab = int(math.floor((a + b) * 2**32))
+    tabc = int(math.floor((a + b + c) * 2**32))
+    es, eg, ek = sc[gi], sd[gi], ei
+    src = torch.zeros_like(ei)
+    dst = torch.zeros_like(ei)
+    for lvl in range(int(sc.max().item())):
+        live = lvl < es
+        r = draw32(eg, _S_RMAT, ek, lvl)
+        sb = (r >= tab).to(torch.int64)
+        db = (((r >= ta) & (r < tab)) | (r >= tabc)).to(torch.int64)
+        src = torch.where(live, src * 2 + sb, src)
+        dst = torch.where(live, dst * 2 + db, dst)
+    # per-graph seeded permutation: rank of (hash, id) inside each graph
+    vg = torch.repeat_interleave(torch.arange(G, device=device), nv)
+    vl = torch.arange(n_total, dtype=torch.int64, device=device) - vbase[vg]
+    h = draw32(sd[vg], _S_PERM, vl)
+    if int(sc.max().item()) > 20:
+        raise ValueError("rmat_batch supports scales up to 20")
+    # lexicographic (graph, hash, id) by two stable sorts (the packed key would overflow)
+    o1 = torch.argsort(h * (1 << 20) + vl, stable=True)
+    order = o1[torch.argsort(vg[o1], stable=True)]
+    perm = torch.empty_like(order)
+    perm[order] = torch.arange(n_total, dtype=torch.int64, device=device)
+    # perm maps union id -> union position; positions within a graph are contiguous
+    src = perm[vbase[gi] + src]
+    dst = perm[vbase[gi] + dst]
+    g = csr_from_edges(n_total, src, dst)
+    abase = g.off[vbase]
+    return g, vbase.cpu().tolist(), abase.cpu().tolist()
+
+
+def batch_member(union: CSR, vbase, i: int, n_i: int) -> CSR:
+    """Graph i of a disjoint union as a standalone CSR (local ids)."""
+    lo, hi = vbase[i], vbase[i] + n_i
+    off = union.off[lo:hi + 1] - union.off[lo]
+    col = union.col[int(union.off[lo]):int(union.off[hi])] - lo
+    return CSR(n_i, off.clone(), col.clone(), None)
 
 
 # ---------------------------------------------------------------------------
@@ -251,14 +313,16 @@ def attach_weights(g: CSR, seed: int = 1) -> CSR:
     """Weights k * 2**-24 with k uniform in {1..2**24}, keyed by the canonical
     endpoint pair, so both arcs of an edge carry the same value and sums are exact."""
     dev = g.col.device
-    rows = torch.repeat_interleave(torch.arange(g.n, dtype=torch.int64, device=dev),
+    rows = torch.repeat_interleave(torch.arange(g.n, dtype=torch.int32 if g.n < 2**31 else torch.int64, device=dev),
                                    g.off[1:] - g.off[:-1])
-    cols = g.col.to(torch.int64)
-    lo = torch.minimum(rows, cols)
-    hi = torch.maximum(rows, cols)
-    k = (draw32(seed, _S_WGT, lo * g.n + hi) & 0xFFFFFF) + 1
-    w = k.to(torch.float64) * 2.0**-24
-    return CSR(g.n, g.off, g.col, w.to(torch.float32))
+    w = torch.empty(g.nnz, dtype=torch.float32, device=dev)
+    chunk = 1 << 27  # bounds the int64 temporaries on very large graphs
+    for s0 in range(0, g.nnz, chunk):
+        r = rows[s0:s0 + chunk].to(torch.int64)
+        c = g.col[s0:s0 + chunk].to(torch.int64)
+        k = (draw32(seed, _S_WGT, torch.minimum(r, c) * g.n + torch.maximum(r, c)) & 0xFFFFFF) + 1
+        w[s0:s0 + chunk] = (k.to(torch.float64) * 2.0**-24).to(torch.float32)
+    return CSR(g.n, g.off, g.col, w)
 
 
 # ---------------------------------------------------------------------------

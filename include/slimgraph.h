@@ -169,6 +169,34 @@ void sg_graph_free(sg_graph *g);
 sg_status sg_compress(sg_ctx *ctx, const sg_graph *g, sg_kernel kernel, double p, uint64_t seed,
                       int want_weights, sg_graph **out);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent graphs compressed together (the paper runs one graph per
+ * pass; batching is this library's addition).  A batch packs `count` graphs
+ * (copied, so the inputs may be freed afterwards) into one device-resident
+ * disjoint union; all graphs must be weighted or all unweighted; count is at
+ * most 65535 and the union must have fewer than 2^32 vertices.
+ * Errors: SG_ERR_INVALID_ARG, SG_ERR_UNSUPPORTED, SG_ERR_OOM, SG_ERR_CUDA. */
+typedef struct sg_batch sg_batch;
+sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs, sg_batch **out);
+void sg_batch_free(sg_batch *b);
+/* Compress graph i of the batch with kernels[i], ps[i], seeds[i] -- the same
+ * result, bit for bit, as sg_compress on that graph alone.  Every step runs
+ * once over the whole union and the sequence is replayed as one CUDA graph;
+ * the first call times a few work-partition settings on this batch (CTAs per
+ * SM of the compaction and enumeration kernels, the warp-per-vertex out-degree
+ * limit) and keeps the fastest.  outs[i] receives a handle whose arrays live
+ * inside the batch: they stay valid until the next sg_compress_batch on this
+ * batch or sg_batch_free; release each handle with sg_graph_free.  Edge-once
+ * kernels need host-driven rounds and return SG_ERR_UNSUPPORTED here. */
+sg_status sg_compress_batch(sg_ctx *ctx, sg_batch *b, const sg_kernel *kernels, const double *ps,
+                            const uint64_t *seeds, int want_weights, sg_graph **outs);
+/* Size of the union and the work-partition setting the autotuner chose
+ * (light_max: largest out-degree given one warp; *_per_sm: CTAs per SM, 0 =
+ * occupancy limit; tuned_ms: the winner's replay time).  Any pointer may be NULL. */
+sg_status sg_batch_info(const sg_batch *b, int64_t *vertices, int64_t *arcs, int *light_max, int *compact_per_sm,
+                        int *enum_per_sm, double *tuned_ms);
+
 /* ------------------------------------------------------------- analytics */
 
 /* divergence(G, H): PageRank of both graphs (damping, iters; FP32 values,

@@ -76,6 +76,11 @@ _SIGS = {
     "sg_cc_count": [_vp, _vp, C.POINTER(C.c_int64), _vp],
     "sg_triangle_count": [_vp, _vp, C.POINTER(C.c_int64)],
     "sg_compress_uniform_noalloc": [_int, _vp, _i64, _i64, _vp, _vp, _dbl, _u64, _vp, _vp, C.POINTER(C.c_int64)],
+    "sg_batch_create": [_vp, _int, C.POINTER(C.c_void_p), _PP],
+    "sg_compress_batch": [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_uint64), _int,
+                          C.POINTER(C.c_void_p)],
+    "sg_batch_info": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                      C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                    C.POINTER(C.c_int64)],
 }
@@ -85,6 +90,8 @@ for _name, _args in _SIGS.items():
     _f.restype = _int
 _lib.sg_ctx_destroy.argtypes = [_vp]
 _lib.sg_ctx_destroy.restype = None
+_lib.sg_batch_free.argtypes = [_vp]
+_lib.sg_batch_free.restype = None
 _lib.sg_graph_free.argtypes = [_vp]
 _lib.sg_graph_free.restype = None
 _lib.sg_last_error.argtypes = []
@@ -210,6 +217,25 @@ class Graph:
         w = None if g.w is None else g.w.to(dev).contiguous()
         return cls.from_tensors(ctx, g.n, off, col, w, copy=copy, validate=validate)
 
+    def tensors(self):
+        """Zero-copy CUDA tensors (off int64, col int32, w float32 or None) over the
+        graph's device arrays; valid only while this graph is alive."""
+        import torch
+
+        v = CsrView()
+        _check(_lib.sg_graph_view(self.handle, C.byref(v)))
+
+        class _Arr:
+            def __init__(self, ptr, n, typestr):
+                self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                                 "version": 3, "strides": None}
+
+        dev = torch.device("cuda", self.ctx.device)
+        off = torch.as_tensor(_Arr(v.off, v.n + 1, "<i8"), device=dev)
+        col = torch.as_tensor(_Arr(v.col, v.nnz, "<i4"), device=dev) if v.nnz else torch.zeros(0, dtype=torch.int32, device=dev)
+        w = torch.as_tensor(_Arr(v.w, v.nnz, "<f4"), device=dev) if (v.w and v.nnz) else None
+        return off, col, w
+
     def download(self):
         off = np.zeros(self.n + 1, dtype=np.int64)
         col = np.zeros(max(self.nnz, 1), dtype=np.uint32)
@@ -283,3 +309,58 @@ def tr_work(g: Graph) -> dict:
     m, w, md, t = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
     _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t)))
     return {"m": m.value, "probes": w.value, "max_out_degree": md.value, "triangles": t.value}
+
+
+class Batch:
+    """Many graphs packed into one device-resident union (sg_batch_create)."""
+
+    def __init__(self, ctx: Context, graphs):
+        self.ctx = ctx
+        self.count = len(graphs)
+        arr = (C.c_void_p * self.count)(*[g.handle.value if hasattr(g.handle, "value") else g.handle
+                                          for g in graphs])
+        h = C.c_void_p()
+        _check(_lib.sg_batch_create(ctx.handle, self.count, arr, C.byref(h)))
+        self.handle = h
+        self._outs = []
+
+    def compress(self, kernels, ps, seeds, want_weights: bool = False):
+        """Compress every graph with its own kernel, p and seed (one CUDA-graph replay).
+        The returned graphs are views valid until the next call or free()."""
+        import torch
+
+        self._release()
+        self.ctx.torch_stream.wait_stream(torch.cuda.current_stream(self.ctx.device))
+        ks = (C.c_int * self.count)(*[KERNELS[k] if isinstance(k, str) else int(k) for k in kernels])
+        pv = (C.c_double * self.count)(*[float(p) for p in ps])
+        sv = (C.c_uint64 * self.count)(*[int(x) & (2**64 - 1) for x in seeds])
+        outs = (C.c_void_p * self.count)()
+        _check(_lib.sg_compress_batch(self.ctx.handle, self.handle, ks, pv, sv, int(want_weights), outs))
+        self._outs = [Graph(self.ctx, C.c_void_p(outs[i])) for i in range(self.count)]
+        return list(self._outs)
+
+    def info(self) -> dict:
+        v, a = C.c_int64(), C.c_int64()
+        lm, cp, ep = C.c_int(), C.c_int(), C.c_int()
+        ms = C.c_double()
+        _check(_lib.sg_batch_info(self.handle, C.byref(v), C.byref(a), C.byref(lm), C.byref(cp), C.byref(ep),
+                                  C.byref(ms)))
+        return {"vertices": v.value, "arcs": a.value, "light_max": lm.value, "compact_per_sm": cp.value,
+                "enum_per_sm": ep.value, "tuned_ms": ms.value}
+
+    def _release(self):
+        for g in self._outs:
+            g.free()
+        self._outs = []
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self._release()
+            _lib.sg_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -64,6 +64,18 @@ __global__ void row_maps_kernel(const int64_t *__restrict__ off, int64_t n, uint
     if (blockIdx.x == 0 && threadIdx.x == 0) tile_vlo[num_tiles] = n + 1;
 }
 
+sg_status fill_row_maps(Ctx *c, const Graph *g, const RowMaps &rm) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((g->n + 1 + threads - 1) / threads, (int64_t)c->num_sms * 16);
+    {
+        SG_LAUNCH(c, "row_maps");
+        row_maps_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, c->stream>>>(
+            g->off, g->n, rm.chunk_row, rm.num_chunks, rm.tile_vlo, rm.num_tiles);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
 sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm) {
     rm->num_tiles = (g->nnz + kTile - 1) / kTile;
     rm->num_chunks = (g->nnz + kWarpSpan - 1) / kWarpSpan;
@@ -71,15 +83,7 @@ sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm) {
     if (st != SG_OK) return st;
     st = dalloc(c, (void **)&rm->tile_vlo, sizeof(int64_t) * (size_t)(rm->num_tiles + 1));
     if (st != SG_OK) return st;
-    const int threads = 256;
-    const int64_t blocks = std::min<int64_t>((g->n + 1 + threads - 1) / threads, (int64_t)c->num_sms * 16);
-    {
-        SG_LAUNCH(c, "row_maps");
-        row_maps_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, c->stream>>>(
-            g->off, g->n, rm->chunk_row, rm->num_chunks, rm->tile_vlo, rm->num_tiles);
-    }
-    SG_CUDA(cudaGetLastError());
-    return SG_OK;
+    return fill_row_maps(c, g, *rm);
 }
 
 void free_row_maps(Ctx *c, RowMaps *rm) {
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
                 }
                 const bool keep = valid && pol.keep(x, y, p, sc, wv);
                 masks[k] = __ballot_sync(kFull, keep);
-                ys[k] = y;
+                if constexpr (Pol::kMapCol) ys[k] = pol.map_col(x, y); else ys[k] = y;
                 ws[k] = wv;
                 wcnt += __popc(masks[k]);
                 if (a.keep_bits != nullptr && lane == 0) a.keep_bits[sbase >> 5] = masks[k];
@@ -307,6 +311,7 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
 // ---------------------------------------------------------------- policies
 struct UniformPol {
     static constexpr bool kOrPrefix = false;
+    static constexpr bool kMapCol = false;
     uint32_t k0, k1;
     unsigned long long tp;
     // random_uniform(E e): the edge stays iff its draw is below floor(p 2^32)
@@ -319,6 +324,7 @@ struct UniformPol {
 
 struct SpectralPol {
     static constexpr bool kOrPrefix = false;
+    static constexpr bool kMapCol = false;
     const int64_t *off;
     uint32_t k0, k1;
     unsigned long long ty;  // floor(Y 2^32)
@@ -339,6 +345,7 @@ struct SpectralPol {
 
 struct OrientPol {
     static constexpr bool kOrPrefix = false;
+    static constexpr bool kMapCol = false;
     const int64_t *off;
     // x precedes y in the degree order (d_x, x) < (d_y, y)
     __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
@@ -350,6 +357,7 @@ struct OrientPol {
 
 struct MaskPol {
     static constexpr bool kOrPrefix = true;
+    static constexpr bool kMapCol = false;
     const uint32_t *fwd_bits;
     const unsigned long long *or_status;
     const int64_t *offp;
@@ -393,7 +401,7 @@ static int blocks_per_sm() {
 template <class Pol>
 static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Pol &pol, const float *w_in,
                              int64_t *off_out, uint32_t *col_out, float *w_out, uint32_t *keep_bits,
-                             unsigned long long *status, const char *name) {
+                             unsigned long long *status, const char *name, int grid_per_sm = 0) {
     if (g->nnz == 0) {
         SG_CUDA(cudaMemsetAsync(off_out, 0, sizeof(int64_t) * (size_t)(g->n + 1), c->stream));
         return SG_OK;
@@ -416,7 +424,8 @@ static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Po
     a.ticket = reinterpret_cast<unsigned int *>(status + rm.num_tiles);
     a.err = c->d_err;
     a.keep_bits = keep_bits;
-    const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * blocks_per_sm<Pol>());
+    const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, blocks_per_sm<Pol>()) : blocks_per_sm<Pol>();
+    const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * per_sm);
     {
         SG_LAUNCH(c, name);
         compact_kernel<Pol><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
@@ -549,6 +558,66 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
     }
     *out = h;
     return SG_OK;
+}
+
+// ------------------------------------------------------- batched variants
+// A batch is a disjoint union of graphs; each union vertex knows its graph and
+// every graph carries its own kernel, p, seed and vertex base.  Random keys use
+// the graph's local ids, so every graph's output equals its solo compression.
+struct BatchOrientPol {
+    static constexpr bool kOrPrefix = false;
+    static constexpr bool kMapCol = false;
+    const int64_t *off;
+    BatchDev b;
+    // only graphs compressed by a triangle kernel need E+
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
+        const int kern = __ldg(&b.params[__ldg(b.vgid + x)].kernel);
+        if (kern < (int)SG_TR_RANDOM) return false;
+        const int64_t dx = __ldg(off + x + 1) - __ldg(off + x);
+        const int64_t dy = __ldg(off + y + 1) - __ldg(off + y);
+        return dx < dy || (dx == dy && (uint32_t)x < y);
+    }
+};
+
+struct BatchFinalPol {
+    static constexpr bool kOrPrefix = true;
+    static constexpr bool kMapCol = true;
+    const int64_t *off;
+    BatchDev b;
+    MaskPol mask;
+    const uint32_t *fwd_bits;  // = mask.fwd_bits (read directly by the tile prologue)
+    __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const { return mask.tile_or_excl(tile); }
+    __device__ __forceinline__ uint32_t map_col(int64_t x, uint32_t y) const {
+        return y - (uint32_t)__ldg(&b.params[__ldg(b.vgid + x)].vbase);
+    }
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t p, const SlabCtx &s, float &w) const {
+        const BatchParam &P = b.params[__ldg(b.vgid + x)];
+        const int kern = P.kernel;
+        if (kern >= (int)SG_TR_RANDOM) return mask.keep(x, y, p, s, w);
+        const uint32_t lx = (uint32_t)(x - P.vbase), ly = (uint32_t)(y - P.vbase);
+        const uint4 r = philox4x32_10(make_uint4(min(lx, ly), max(lx, ly), 0u, kTagEdge), P.k0, P.k1);
+        if (kern == (int)SG_UNIFORM) return (unsigned long long)r.x < P.tp;
+        const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
+        const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
+        const uint64_t dmin = dx < dy ? dx : dy;
+        if (P.reweight) w = (dmin * 4294967296ull <= P.ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), P.yf);
+        return (unsigned long long)r.x * dmin < P.ty;
+    }
+};
+
+sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev &b, bool weights, Oriented *o,
+                       unsigned long long *status, int grid_per_sm) {
+    BatchOrientPol pol{u->off, b};
+    return run_compact(c, u, rm, pol, weights ? u->w : nullptr, o->off, o->col, weights ? o->w : nullptr,
+                       o->fwd_bits, status, "compact_orient", grid_per_sm);
+}
+
+sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
+                      const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
+                      unsigned long long *status, int grid_per_sm) {
+    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, o.off, o.col, del, c->d_err}, o.fwd_bits};
+    return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, nullptr, status, "compact_final",
+                       grid_per_sm);
 }
 
 }  // namespace sg

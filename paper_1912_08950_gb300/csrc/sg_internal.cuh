@@ -147,6 +147,18 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t lo
 
 #endif  // __CUDACC__
 
+// batched compression: per-graph parameters in the disjoint union
+struct BatchParam {
+    int64_t vbase;              // first vertex of the graph in the union
+    unsigned long long tp;      // floor(p 2^32): uniform and triangle kernels
+    unsigned long long ty;      // floor(Y 2^32): spectral kernels
+    uint32_t k0, k1;            // Philox key (seed low, high word)
+    float yf;                   // Y rounded to float (spectral weights)
+    int kernel;                 // sg_kernel
+    int reweight;               // spectral: emit 1/p_uv weights
+    int64_t n;                  // vertices of the graph
+};
+
 // ---------------------------------------------------------- internal entry
 // compaction / edge kernels (sg_compact.cu)
 struct RowMaps {
@@ -155,6 +167,7 @@ struct RowMaps {
     int64_t num_tiles = 0, num_chunks = 0;
 };
 sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm);
+sg_status fill_row_maps(Ctx *c, const Graph *g, const RowMaps &rm);  // into allocated maps
 void free_row_maps(Ctx *c, RowMaps *rm);
 
 sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t seed, int want_weights,
@@ -175,10 +188,34 @@ void free_oriented(Ctx *c, Oriented *o);
 sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
                        Graph **out);
 
+// batched variants over a disjoint union (sg_compact.cu)
+struct BatchDev {
+    const BatchParam *params;   // [count]
+    const uint32_t *vgid;       // graph of every union vertex
+};
+sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev &b, bool weights, Oriented *o,
+                       unsigned long long *status, int grid_per_sm);
+sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
+                      const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
+                      unsigned long long *status, int grid_per_sm);
+
 // triangles (sg_triangles.cu)
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed,
                   uint8_t *del);
 sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg);
+// batched union TR, with no host synchronisation (capturable in a CUDA graph)
+struct BatchTri {
+    uint32_t *heavy = nullptr;
+    unsigned long long *buckets = nullptr;  // counts, fills, total
+    int log_slots = 3;
+    size_t smem = 0;
+    int max_deg = 1;      // largest out-degree (sizes the heavy vertex arrays)
+    int light_max = 64;
+    int grid_per_sm = 0;  // 0: occupancy limit
+};
+sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt);
+sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const BatchTri &bt, uint8_t *del);
+void batch_tr_free(Ctx *c, BatchTri *bt);
 
 // analytics (sg_analytics.cu)
 sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_out, double *resid);

@@ -35,9 +35,9 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kLightMax = 64;     // largest out-degree processed by one warp
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
-constexpr int kQ = 64;            // per-warp hit queue entries
+constexpr int kQ = 96;            // per-warp hit queue entries (31 left over + 2 slabs of hits)
 
-enum class Mode { Count, UnionRandom, UnionMaxw, EoReserve };
+enum class Mode { Count, UnionRandom, UnionMaxw, EoReserve, BatchUnion };
 
 struct TriArgs {
     const int64_t *offp;
@@ -53,6 +53,13 @@ struct TriArgs {
     const uint32_t *heavy;
     int64_t n_heavy;
     int heavy_log_slots;
+    int heavy_max_deg;           // capacity of the per-vertex list arrays of phase 1
+    int light_max;               // out-degrees up to this go to the warp-per-vertex phase
+    unsigned long long *work;    // [0] next heavy vertex, [1] next light vertex block
+    const unsigned long long *n_heavy_dev;  // if set, the heavy count is read on the device
+    // batched union: per-graph parameters and the graph of every vertex
+    const BatchParam *bparams;
+    const uint32_t *vgid;
     // edge-once: optional list of the live selected triangles
     struct TriRec *list;
     unsigned long long *list_ctr;  // slots handed out (chunks of kChunk)
@@ -104,9 +111,10 @@ __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool wa
     em.cur += cnt;
 }
 
+// Oriented arcs are addressed with 32-bit indices (E+ holds fewer than 2^32 arcs).
 struct HitQueue {
     uint32_t u[kQ], v[kQ], w[kQ];
-    long long iuv[kQ], iuw[kQ], ivw[kQ];
+    uint32_t iuv[kQ], iuw[kQ], ivw[kQ];
 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t key, int log_slots) {
@@ -127,16 +135,45 @@ __device__ __forceinline__ void swap2(T &a, T &b) {
 // triangle pass valid = false.
 template <Mode M>
 __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u, uint32_t v, uint32_t w,
-                                       int64_t iuv, int64_t iuw, int64_t ivw, unsigned &live, Emitter &em) {
+                                       uint32_t iuv, uint32_t iuw, uint32_t ivw, unsigned &live, Emitter &em) {
     if constexpr (M == Mode::Count) {
         return;
     } else {
         bool emit = false;
         TriRec rec;
+        if constexpr (M == Mode::BatchUnion) {
+            if (valid) {
+                // the triangle's graph: its own seed, p and kernel, local ids as keys
+                const BatchParam &P = a.bparams[__ldg(a.vgid + u)];
+                const uint32_t base = (uint32_t)P.vbase;
+                uint32_t x0 = u - base, x1 = v - base, x2 = w - base;
+                uint32_t e01 = iuv, e02 = iuw, e12 = ivw;
+                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+                if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+                const uint4 r = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), P.k0, P.k1);
+                if ((unsigned long long)r.x < P.tp) {
+                    uint32_t best;
+                    if (P.kernel == (int)SG_TR_MAXW) {
+                        const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
+                        best = e01;
+                        float bw = w01;
+                        uint32_t bl = x0, bh = x1;
+                        if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
+                        if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
+                    } else {
+                        const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
+                        best = k == 0 ? e01 : (k == 1 ? e02 : e12);
+                    }
+                    a.del[best] = 1;
+                }
+            }
+            return;
+        }
         if (valid) {
             // sort the vertices, keeping e_ij = the arc joining x_i and x_j
             uint32_t x0 = u, x1 = v, x2 = w;
-            int64_t e01 = iuv, e02 = iuw, e12 = ivw;
+            uint32_t e01 = iuv, e02 = iuw, e12 = ivw;
             if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
             if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
             if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
@@ -148,7 +185,7 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                 } else if constexpr (M == Mode::UnionMaxw) {
                     // heaviest edge under (weight, lo, hi)
                     const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
-                    int64_t best = e01;
+                    uint32_t best = e01;
                     float bw = w01;
                     uint32_t bl = x0, bh = x1;
                     if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
@@ -162,7 +199,7 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                         atomicMin(a.resv + e12, hi | x0);
                         ++live;
                         emit = true;
-                        rec = TriRec{x0, x1, x2, r.y, r.z, (uint32_t)e01, (uint32_t)e02, (uint32_t)e12};
+                        rec = TriRec{x0, x1, x2, r.y, r.z, e01, e02, e12};
                     }
                 }
             }
@@ -173,71 +210,31 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
     }
 }
 
-// Queue one hit per lane flag; decide 32 queued triangles whenever full.
+// Decide the 32 oldest queued triangles with all lanes and shift the rest down.
+// Kept out of line so that the probe loop's register budget stays small.
 template <Mode M>
-__device__ __forceinline__ void push_hits(const TriArgs &a, HitQueue &q, int &qn, bool hit, uint32_t u, uint32_t v,
-                                          uint32_t w, int64_t iuv, int64_t iuw, int64_t ivw, unsigned &live,
-                                          unsigned long long &tris, Emitter &em) {
-    const unsigned hm = __ballot_sync(kFull, hit);
-    if (!hm) return;
+__device__ __noinline__ int drain32(const TriArgs &a, HitQueue &q, int qn, unsigned &live, Emitter &em) {
     const int lane = threadIdx.x & 31;
-    if (hit) {
-        const int s = qn + __popc(hm & lanemask_lt());
-        q.u[s] = u; q.v[s] = v; q.w[s] = w;
-        q.iuv[s] = iuv; q.iuw[s] = iuw; q.ivw[s] = ivw;
-    }
-    qn += __popc(hm);
-    tris += hit ? 1 : 0;
+    decide<M>(a, true, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live, em);
     __syncwarp();
-    if (qn >= 32) {
-        decide<M>(a, true, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live, em);
-        __syncwarp();
-        const int rest = qn - 32;
-        if (lane < rest) {
-            q.u[lane] = q.u[lane + 32]; q.v[lane] = q.v[lane + 32]; q.w[lane] = q.w[lane + 32];
-            q.iuv[lane] = q.iuv[lane + 32]; q.iuw[lane] = q.iuw[lane + 32]; q.ivw[lane] = q.ivw[lane + 32];
-        }
-        qn = rest;
-        __syncwarp();
+    const int rest = qn - 32;
+    for (int k = lane; k < rest; k += 32) {
+        q.u[k] = q.u[k + 32]; q.v[k] = q.v[k + 32]; q.w[k] = q.w[k + 32];
+        q.iuv[k] = q.iuv[k + 32]; q.iuw[k] = q.iuw[k + 32]; q.ivw[k] = q.ivw[k + 32];
+        __syncwarp(__activemask());
     }
+    __syncwarp();
+    return rest;
 }
 
 template <Mode M>
 __device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn, unsigned &live, Emitter &em) {
     const int lane = threadIdx.x & 31;
+    while (qn >= 32) qn = drain32<M>(a, q, qn, live, em);
     const bool valid = lane < qn;
     decide<M>(a, valid, valid ? q.u[lane] : 0u, valid ? q.v[lane] : 0u, valid ? q.w[lane] : 0u,
-              valid ? q.iuv[lane] : 0, valid ? q.iuw[lane] : 0, valid ? q.ivw[lane] : 0, live, em);
+              valid ? q.iuv[lane] : 0u, valid ? q.iuw[lane] : 0u, valid ? q.ivw[lane] : 0u, live, em);
     __syncwarp();
-}
-
-// Stream N+(v) for v = N+(u)[i] through the table of N+(u).
-template <Mode M>
-__device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key, const uint16_t *idx, int log_slots,
-                                           uint32_t u, int64_t ou, int i, uint32_t v, HitQueue &q, int &qn,
-                                           unsigned &live, unsigned long long &probes, unsigned long long &tris,
-                                           Emitter &em) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t mask = (1u << log_slots) - 1u;
-    const int64_t ov = __ldg(a.offp + v);
-    const int64_t dv = __ldg(a.offp + v + 1) - ov;
-    for (int64_t j0 = 0; j0 < dv; j0 += 32) {
-        const int64_t j = j0 + lane;
-        bool hit = false;
-        uint32_t w = 0, t = 0;
-        if (j < dv) {
-            w = __ldg(a.colp + ov + j);
-            ++probes;
-            uint32_t s = slot_of(w, log_slots);
-            for (;;) {
-                const uint32_t k = key[s];
-                if (k == w) { hit = true; t = idx[s]; break; }
-                if (k == kEmpty) break;
-                s = (s + 1) & mask;
-            }
-        }
-        push_hits<M>(a, q, qn, hit, u, v, w, ou + i, ou + t, ov + j, live, tris, em);
-    }
 }
 
 __device__ __forceinline__ void table_insert(uint32_t *key, uint16_t *idx, int log_slots, uint32_t w, int i) {
@@ -247,6 +244,57 @@ __device__ __forceinline__ void table_insert(uint32_t *key, uint16_t *idx, int l
         const uint32_t old = atomicCAS(key + s, kEmpty, w);
         if (old == kEmpty) { idx[s] = (uint16_t)i; return; }
         s = (s + 1) & mask;
+    }
+}
+
+// Probe one element w (a lane's share of N+(v)) against the table of N+(u).
+// The first slot is read inline; collisions (load <= 1/4) take the loop.
+__device__ __forceinline__ bool probe_one(const uint32_t *key, int sh, uint32_t mask, uint32_t w, uint32_t &s) {
+    s = (w * 0x9E3779B1u) >> sh;
+    uint32_t k = key[s];
+    while (k != w && k != kEmpty) {
+        s = (s + 1) & mask;
+        k = key[s];
+    }
+    return k == w;
+}
+
+// Stream N+(v) = colp[ov, ov + dv) through the table of N+(u): two 32-element
+// slabs per iteration (two loads in flight per lane); hits go to the queue.
+template <Mode M>
+__device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key, const uint16_t *idx, int log_slots,
+                                           uint32_t u, uint32_t iuv, uint32_t ou, uint32_t v, uint32_t ov, int dv,
+                                           HitQueue &q, int &qn, unsigned &live, unsigned long long &tris,
+                                           Emitter &em) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t *lst = a.colp + ov;
+    const int sh = 32 - log_slots;
+    const uint32_t mask = (1u << log_slots) - 1u;
+    for (int j0 = 0; j0 < dv; j0 += 64) {
+        const int ja = j0 + lane, jb = ja + 32;
+        uint32_t wa = 0, wb = 0, sa = 0, sb = 0;
+        if (ja < dv) wa = __ldg(lst + ja);
+        if (jb < dv) wb = __ldg(lst + jb);
+        const bool ha = ja < dv && probe_one(key, sh, mask, wa, sa);
+        const bool hb = jb < dv && probe_one(key, sh, mask, wb, sb);
+        const unsigned ma = __ballot_sync(kFull, ha), mb = __ballot_sync(kFull, hb);
+        if (ma | mb) {
+            int s0 = qn + __popc(ma & lt);
+            if (ha) {
+                q.u[s0] = u; q.v[s0] = v; q.w[s0] = wa;
+                q.iuv[s0] = iuv; q.iuw[s0] = ou + idx[sa]; q.ivw[s0] = ov + (uint32_t)ja;
+            }
+            s0 = qn + __popc(ma) + __popc(mb & lt);
+            if (hb) {
+                q.u[s0] = u; q.v[s0] = v; q.w[s0] = wb;
+                q.iuv[s0] = iuv; q.iuw[s0] = ou + idx[sb]; q.ivw[s0] = ov + (uint32_t)jb;
+            }
+            qn += __popc(ma) + __popc(mb);
+            if (lane == 0) tris += (unsigned)(__popc(ma) + __popc(mb));
+            __syncwarp();
+            while (qn >= 32) qn = drain32<M>(a, q, qn, live, em);
+        }
     }
 }
 
@@ -266,105 +314,201 @@ __device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, un
     }
 }
 
-// warp per vertex u with 2 <= d+(u) <= kLightMax
+// One persistent launch per enumeration pass.
+// Phase 1: heavy vertices (d+(u) > light_max), largest out-degree first; a CTA
+// stages N+(u) in a shared-memory table (plus every v's list bounds) and its
+// warps claim the lists N+(v) one at a time.  Phase 2: light vertices, a warp
+// per vertex with its own small table; warps claim 32 vertex ids at a time.
+// Probe and triangle totals are counted per list and per found triangle.
 template <Mode M>
-__global__ void __launch_bounds__(kTW * 32) tri_light_kernel(TriArgs a) {
-    __shared__ uint32_t s_key[kTW][kLightSlots];
-    __shared__ uint16_t s_idx[kTW][kLightSlots];
-    __shared__ HitQueue s_q[kTW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *key = s_key[warp];
-    uint16_t *idx = s_idx[warp];
-    HitQueue &q = s_q[warp];
-    int qn = 0;
-    unsigned live = 0;
-    unsigned long long probes = 0, tris = 0;
-    Emitter em;
-    const int64_t nw = (int64_t)gridDim.x * kTW;
-    for (int64_t u = (int64_t)blockIdx.x * kTW + warp; u < a.n; u += nw) {
-        const int64_t ou = __ldg(a.offp + u);
-        const int d = (int)(__ldg(a.offp + u + 1) - ou);
-        if (d < 2 || d > kLightMax) continue;
-        const int log_slots = max(3, ceil_log2(4 * d));
-        for (int s = lane; s < (1 << log_slots); s += 32) key[s] = kEmpty;
-        __syncwarp();
-        const uint32_t n0 = lane < d ? __ldg(a.colp + ou + lane) : 0u;
-        const uint32_t n1 = lane + 32 < d ? __ldg(a.colp + ou + lane + 32) : 0u;
-        if (lane < d && (M != Mode::EoReserve || !a.considered[ou + lane])) table_insert(key, idx, log_slots, n0, lane);
-        if (lane + 32 < d && (M != Mode::EoReserve || !a.considered[ou + lane + 32]))
-            table_insert(key, idx, log_slots, n1, lane + 32);
-        __syncwarp();
-        for (int i = 0; i < d; ++i) {
-            const uint32_t v = __shfl_sync(kFull, i < 32 ? n0 : n1, i & 31);
-            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
-            probe_list<M>(a, key, idx, log_slots, (uint32_t)u, ou, i, v, q, qn, live, probes, tris, em);
-        }
-        __syncwarp();
-    }
-    finish<M>(a, q, qn, live, probes, tris, em);
-}
-
-// CTA per heavy vertex (d+(u) > kLightMax); the table lives in dynamic smem
-template <Mode M>
-__global__ void __launch_bounds__(kTW * 32) tri_heavy_kernel(TriArgs a) {
+__global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_next;
+    __shared__ long long s_h;
     HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
-    uint32_t *key = reinterpret_cast<uint32_t *>(smem + sizeof(HitQueue) * kTW);
-    uint16_t *idx = reinterpret_cast<uint16_t *>(key + (1 << a.heavy_log_slots));
-    const int warp = threadIdx.x >> 5;
+    unsigned char *tbl = smem + sizeof(HitQueue) * kTW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     HitQueue &q = qs[warp];
     int qn = 0;
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
     Emitter em;
-    for (int64_t h = blockIdx.x; h < a.n_heavy; h += gridDim.x) {
-        const uint32_t u = __ldg(a.heavy + h);
-        const int64_t ou = __ldg(a.offp + u);
-        const int d = (int)(__ldg(a.offp + u + 1) - ou);
-        const int log_slots = min(a.heavy_log_slots, ceil_log2(4 * d));
-        __syncthreads();  // previous vertex finished with the table
-        for (int s = threadIdx.x; s < (1 << log_slots); s += blockDim.x) key[s] = kEmpty;
-        __syncthreads();
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
-            table_insert(key, idx, log_slots, __ldg(a.colp + ou + i), i);
+    const int64_t n_heavy = a.n_heavy_dev ? (int64_t)*a.n_heavy_dev : a.n_heavy;
+
+    // ---- phase 1: heavy vertices
+    {
+        const int slots = 1 << a.heavy_log_slots;
+        uint32_t *key = reinterpret_cast<uint32_t *>(tbl);
+        uint16_t *idx = reinterpret_cast<uint16_t *>(key + slots);
+        uint32_t *vv = reinterpret_cast<uint32_t *>(idx + slots);  // v, off+(v), d+(v) of N+(u)
+        uint32_t *vo = vv + max(a.heavy_max_deg, 1);
+        int *vd = reinterpret_cast<int *>(vo + max(a.heavy_max_deg, 1));
+        for (;;) {
+            if (threadIdx.x == 0) {
+                s_h = (long long)atomicAdd(a.work, 1ull);
+                s_next = 0;
+            }
+            __syncthreads();
+            const int64_t h = s_h;
+            if (h >= n_heavy) break;
+            const uint32_t u = __ldg(a.heavy + h);
+            const uint32_t ou = (uint32_t)__ldg(a.offp + u);
+            const int d = (int)(__ldg(a.offp + u + 1) - (int64_t)ou);
+            const int log_slots = min(a.heavy_log_slots, ceil_log2(4 * d));
+            for (int s2 = threadIdx.x; s2 < (1 << log_slots); s2 += blockDim.x) key[s2] = kEmpty;
+            __syncthreads();
+            const bool staged = a.heavy_max_deg > 0;  // list bounds of N+(u) kept in shared memory
+            for (int i = threadIdx.x; i < d; i += blockDim.x) {
+                const uint32_t v = __ldg(a.colp + ou + i);
+                const bool dead = M == Mode::EoReserve && a.considered[ou + i];
+                if (staged) {
+                    const int64_t ov = __ldg(a.offp + v);
+                    vv[i] = v;
+                    vo[i] = (uint32_t)ov;
+                    // a considered arc u->v closes no live triangle
+                    vd[i] = dead ? 0 : (int)(__ldg(a.offp + v + 1) - ov);
+                }
+                if (!dead) table_insert(key, idx, log_slots, v, i);
+            }
+            __syncthreads();
+            for (;;) {
+                int i = 0;
+                if (lane == 0) i = atomicAdd(&s_next, 1);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= d) break;
+                uint32_t v, ov;
+                int dv;
+                if (staged) {
+                    v = vv[i];
+                    ov = vo[i];
+                    dv = vd[i];
+                } else {
+                    v = __ldg(a.colp + ou + i);
+                    const int64_t o64 = __ldg(a.offp + v);
+                    ov = (uint32_t)o64;
+                    dv = (M == Mode::EoReserve && a.considered[ou + i]) ? 0 : (int)(__ldg(a.offp + v + 1) - o64);
+                }
+                if (lane == 0) probes += (unsigned)dv;
+                probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris, em);
+            }
+            __syncthreads();  // the table is rebuilt for the next vertex
         }
-        __syncthreads();
-        for (int i = warp; i < d; i += kTW) {
-            if (M == Mode::EoReserve && a.considered[ou + i]) continue;
-            const uint32_t v = __ldg(a.colp + ou + i);
-            probe_list<M>(a, key, idx, log_slots, u, ou, i, v, q, qn, live, probes, tris, em);
+    }
+
+    // ---- phase 2: light vertices
+    {
+        uint32_t *key = reinterpret_cast<uint32_t *>(tbl) + warp * kLightSlots;
+        uint16_t *idx = reinterpret_cast<uint16_t *>(tbl + sizeof(uint32_t) * kLightSlots * kTW) + warp * kLightSlots;
+        for (;;) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.work + 1, 32ull);
+            base = __shfl_sync(kFull, base, 0);
+            if ((int64_t)base >= a.n) break;
+            const int64_t ul = (int64_t)base + lane;
+            uint32_t oul = 0;
+            int dl = 0;
+            if (ul < a.n) {
+                const int64_t o0 = __ldg(a.offp + ul);
+                oul = (uint32_t)o0;
+                dl = (int)(__ldg(a.offp + ul + 1) - o0);
+            }
+            unsigned lm = __ballot_sync(kFull, dl >= 2 && dl <= a.light_max);
+            while (lm) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const uint32_t u = (uint32_t)(base + src);
+                const uint32_t ou = __shfl_sync(kFull, oul, src);
+                const int d = __shfl_sync(kFull, dl, src);
+                const int log_slots = max(3, ceil_log2(4 * d));
+                for (int s2 = lane; s2 < (1 << log_slots); s2 += 32) key[s2] = kEmpty;
+                __syncwarp();
+                // lane k holds N+(u)[k] and N+(u)[k + 32] with their list bounds
+                uint32_t n0 = 0, n1 = 0, o0 = 0, o1 = 0;
+                int d0 = 0, d1 = 0;
+                if (lane < d) {
+                    n0 = __ldg(a.colp + ou + lane);
+                    const int64_t b0 = __ldg(a.offp + n0);
+                    o0 = (uint32_t)b0;
+                    d0 = (int)(__ldg(a.offp + n0 + 1) - b0);
+                    if (M != Mode::EoReserve || !a.considered[ou + lane]) table_insert(key, idx, log_slots, n0, lane);
+                    else d0 = 0;
+                }
+                if (lane + 32 < d) {
+                    n1 = __ldg(a.colp + ou + lane + 32);
+                    const int64_t b1 = __ldg(a.offp + n1);
+                    o1 = (uint32_t)b1;
+                    d1 = (int)(__ldg(a.offp + n1 + 1) - b1);
+                    if (M != Mode::EoReserve || !a.considered[ou + lane + 32])
+                        table_insert(key, idx, log_slots, n1, lane + 32);
+                    else d1 = 0;
+                }
+                __syncwarp();
+                for (int i = 0; i < d; ++i) {
+                    const bool lo = i < 32;
+                    const uint32_t v = __shfl_sync(kFull, lo ? n0 : n1, i & 31);
+                    const uint32_t ov = __shfl_sync(kFull, lo ? o0 : o1, i & 31);
+                    const int dv = __shfl_sync(kFull, lo ? d0 : d1, i & 31);
+                    if (lane == 0) probes += (unsigned)dv;
+                    probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris, em);
+                }
+                __syncwarp();
+            }
         }
     }
     finish<M>(a, q, qn, live, probes, tris, em);
 }
 
-// heavy-vertex list and the maximum out-degree
-__global__ void classify_kernel(const int64_t *__restrict__ offp, int64_t n, uint32_t *heavy,
-                                unsigned long long *ctr) {
-    const int lane = threadIdx.x & 31;
+// Heavy vertices in decreasing out-degree order, by log2 buckets: pass 1
+// counts the vertices of each bucket (and the maximum out-degree), pass 2
+// scatters them so that larger buckets come first.
+constexpr int kBuckets = 17;  // floor(log2(d+)) for d+ < 2^17
+
+__device__ __forceinline__ int bucket_of(int64_t d) { return 63 - __clzll((unsigned long long)d); }
+
+__global__ void classify_count_kernel(const int64_t *__restrict__ offp, int64_t n, int light_max,
+                                      unsigned long long *bucket_cnt, unsigned long long *ctr) {
+    __shared__ unsigned int s_cnt[kBuckets];
+    if (threadIdx.x < kBuckets) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
     unsigned long long dmax = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t u = base + threadIdx.x;
-        int64_t d = 0;
-        if (u < n) d = offp[u + 1] - offp[u];
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int64_t d = offp[u + 1] - offp[u];
         dmax = d > (int64_t)dmax ? (unsigned long long)d : dmax;
-        const bool hv = d > kLightMax;
-        const unsigned hm = __ballot_sync(kFull, hv);
-        if (hm) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(ctr + kCtrHeavy, (unsigned long long)__popc(hm));
-            pos = __shfl_sync(kFull, pos, 0);
-            if (hv) heavy[pos + __popc(hm & lanemask_lt())] = (uint32_t)u;
-        }
+        if (d > light_max) atomicAdd(&s_cnt[min(bucket_of(d), kBuckets - 1)], 1u);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long t = __shfl_xor_sync(kFull, dmax, o);
         dmax = t > dmax ? t : dmax;
     }
-    if (lane == 0) atomicMax(ctr + kCtrMaxDeg, dmax);
+    if ((threadIdx.x & 31) == 0) atomicMax(ctr + kCtrMaxDeg, dmax);
+    __syncthreads();
+    if (threadIdx.x < kBuckets && s_cnt[threadIdx.x]) atomicAdd(bucket_cnt + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+__global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, int64_t n, int light_max,
+                                        const unsigned long long *__restrict__ bucket_cnt,
+                                        unsigned long long *bucket_fill, uint32_t *heavy,
+                                        unsigned long long *total_out) {
+    __shared__ unsigned long long s_off[kBuckets];
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int b = kBuckets - 1; b >= 0; --b) {
+            s_off[b] = run;
+            run += bucket_cnt[b];
+        }
+        if (blockIdx.x == 0 && total_out) *total_out = run;
+    }
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int64_t d = offp[u + 1] - offp[u];
+        if (d > light_max) {
+            const int b = min(bucket_of(d), kBuckets - 1);
+            heavy[s_off[b] + atomicAdd(bucket_fill + b, 1ull)] = (uint32_t)u;
+        }
+    }
 }
 
 // Edge-Once acceptance: an oriented arc e = u->y holding reservation
@@ -500,12 +644,28 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
     }
 }
 
+// Clear the reservations of the listed triangles' edges (cheaper than a full
+// reset once the list is short): every reserved edge belongs to a listed triangle.
+__global__ void eo_list_reset_kernel(const TriRec *__restrict__ L, int64_t len, unsigned long long *resv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const TriRec r = L[i];
+        if (r.x0 == kSentinel) continue;
+        resv[r.e01] = ~0ull;
+        resv[r.e02] = ~0ull;
+        resv[r.e12] = ~0ull;
+    }
+}
+
 // -------------------------------------------------------------------- host
 struct Plan {
     uint32_t *heavy = nullptr;
+    unsigned long long *buckets = nullptr;  // counts [kBuckets], fills [kBuckets]
     int64_t n_heavy = 0, max_deg = 0;
+    int light_max = kLightMax;
     int log_slots = 3;
-    size_t heavy_smem = 0;
+    size_t smem = 0;
+    bool staged = true;  // heavy vertices' list bounds fit in shared memory
 };
 
 static sg_status read_ctr(Ctx *c, int first, int count, unsigned long long *out) {
@@ -516,25 +676,49 @@ static sg_status read_ctr(Ctx *c, int first, int count, unsigned long long *out)
     return SG_OK;
 }
 
+static void free_plan(Ctx *c, Plan *pl) {
+    dfree(c, pl->heavy);
+    dfree(c, pl->buckets);
+    pl->heavy = nullptr;
+    pl->buckets = nullptr;
+}
+
 static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
+    if (o.m >= (int64_t)0xFFFFFFFFll)
+        return fail(SG_ERR_UNSUPPORTED, "triangle kernels address oriented arcs with 32 bits: m must be < 2^32");
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kBuckets);
     if (st != SG_OK) return st;
-    // per-call counters only: the probe and triangle totals accumulate
-    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrHeavy, 0, sizeof(unsigned long long) * 2, c->stream));
+    SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, c->stream));
+    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     if (o.n > 0) {
-        const int64_t blocks = std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8);
         SG_LAUNCH(c, "tri_classify");
-        classify_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->heavy, c->d_ctr);
+        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->light_max, pl->buckets,
+                                                                       c->d_ctr);
     }
     SG_CUDA(cudaGetLastError());
-    unsigned long long v[kCtrCount];
-    st = read_ctr(c, 0, kCtrCount, v);
-    if (st != SG_OK) return st;
-    pl->n_heavy = (int64_t)v[kCtrHeavy];
-    pl->max_deg = (int64_t)v[kCtrMaxDeg];
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, pl->buckets, sizeof(unsigned long long) * kBuckets, cudaMemcpyDeviceToHost,
+                            c->stream));
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned + kBuckets, c->d_ctr + kCtrMaxDeg, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long cnt[kBuckets + 1];
+    std::memcpy(cnt, c->h_pinned, sizeof(cnt));
+    pl->n_heavy = 0;
+    for (int b = 0; b < kBuckets; ++b) pl->n_heavy += (int64_t)cnt[b];
+    pl->max_deg = (int64_t)cnt[kBuckets];
     if (pl->max_deg > 65535)
         return fail(SG_ERR_UNSUPPORTED, "an oriented out-degree above 65535 is not supported");
+    if (pl->n_heavy > 0) {
+        SG_LAUNCH(c, "tri_classify");
+        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->light_max, pl->buckets,
+                                                                         pl->buckets + kBuckets, pl->heavy, nullptr);
+    }
+    SG_CUDA(cudaGetLastError());
+    // shared memory: hit queues + the larger of the heavy table and the light tables
     const size_t queue_bytes = sizeof(HitQueue) * kTW;
+    const size_t light_bytes = (size_t)kTW * kLightSlots * 6;
     int ls = 3;
     while ((1ll << ls) < 4 * std::max<int64_t>(pl->max_deg, 2)) ++ls;
     const size_t limit = 220 * 1024;
@@ -542,33 +726,49 @@ static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
     if (queue_bytes + (size_t)(1ll << ls) * 6 > limit)
         return fail(SG_ERR_UNSUPPORTED, "oriented out-degree too large for the shared-memory table");
     pl->log_slots = ls;
-    pl->heavy_smem = queue_bytes + (size_t)(1ll << ls) * 6;
+    // the list bounds of N+(u) are staged in shared memory when they fit
+    size_t heavy_bytes = (size_t)(1ll << ls) * 6 + (size_t)std::max<int64_t>(pl->max_deg, 1) * 12;
+    pl->staged = queue_bytes + heavy_bytes <= limit;
+    if (!pl->staged) heavy_bytes = (size_t)(1ll << ls) * 6 + 12;
+    pl->smem = queue_bytes + std::max(light_bytes, heavy_bytes);
+    return SG_OK;
+}
+
+template <Mode M>
+static sg_status launch_enum_raw(Ctx *c, TriArgs a, size_t smem, int grid_per_sm) {
+    SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
+    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M>, kTW * 32, smem));
+    per_sm = std::max(per_sm, 1);
+    if (grid_per_sm > 0) per_sm = std::min(per_sm, grid_per_sm);
+    const int64_t grid = (int64_t)c->num_sms * per_sm;
+    {
+        SG_LAUNCH(c, "tri_enum");
+        tri_enum_kernel<M><<<(unsigned)grid, kTW * 32, smem, c->stream>>>(a);
+    }
+    SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
 
 template <Mode M>
 static sg_status launch_enum(Ctx *c, const TriArgs &base, const Plan &pl) {
+    if (base.n == 0) return SG_OK;
     TriArgs a = base;
     a.heavy = pl.heavy;
     a.n_heavy = pl.n_heavy;
     a.heavy_log_slots = pl.log_slots;
-    if (pl.n_heavy > 0) {
-        SG_CUDA(cudaFuncSetAttribute(tri_heavy_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)pl.heavy_smem));
-        int per_sm = 0;
-        SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_heavy_kernel<M>, kTW * 32,
-                                                              pl.heavy_smem));
-        const int64_t grid = std::min<int64_t>(pl.n_heavy, (int64_t)c->num_sms * std::max(per_sm, 1));
-        SG_LAUNCH(c, "tri_heavy");
-        tri_heavy_kernel<M><<<(unsigned)grid, kTW * 32, pl.heavy_smem, c->stream>>>(a);
-    }
-    SG_CUDA(cudaGetLastError());
-    if (a.n > 0) {
-        int per_sm = 0;
-        SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_light_kernel<M>, kTW * 32, 0));
-        const int64_t grid = std::min<int64_t>((a.n + kTW - 1) / kTW, (int64_t)c->num_sms * std::max(per_sm, 1));
-        SG_LAUNCH(c, "tri_light");
-        tri_light_kernel<M><<<(unsigned)grid, kTW * 32, 0, c->stream>>>(a);
+    a.heavy_max_deg = pl.staged ? (int)std::max<int64_t>(pl.max_deg, 1) : 0;
+    a.light_max = pl.light_max;
+    a.work = c->d_ctr + kCtrAux;
+    SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
+    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    int per_sm = 0;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M>, kTW * 32, pl.smem));
+    const int64_t grid = (int64_t)c->num_sms * std::max(per_sm, 1);
+    {
+        SG_LAUNCH(c, "tri_enum");
+        tri_enum_kernel<M><<<(unsigned)grid, kTW * 32, pl.smem, c->stream>>>(a);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -608,12 +808,11 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     a.considered = considered;
     a.resv = resv;
     const int64_t acc_blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
+    if (st == SG_OK && cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "memset");
     for (int round = 0; st == SG_OK; ++round) {
         if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
-        if (cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess) {
-            st = cuda_fail(cudaGetLastError(), "memset");
-            break;
-        }
+        // ---- reserve: every live selected triangle bids for its three edges
         unsigned long long live = 0;
         if (LA == nullptr) {
             // enumeration round, writing the list when it fits
@@ -676,7 +875,10 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             lenA = (int64_t)live;
         }
         ++c->eo_rounds;
-        if (LA != nullptr) {
+        // ---- accept: triangles holding all three reservations.  A long list is
+        // cheaper to judge from the edges' side (one pass over m reservations).
+        const bool small_list = LA != nullptr && (double)lenA * sizeof(TriRec) <= 8.0 * (double)m;
+        if (small_list) {
             const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
             SG_LAUNCH(c, "tri_eo_list_accept");
             if (maxw)
@@ -689,6 +891,15 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                 eo_accept_kernel<true><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
             else
                 eo_accept_kernel<false><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+        }
+        SG_CUDA(cudaGetLastError());
+        // ---- reset the reservations for the next round
+        if (small_list) {
+            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
+            SG_LAUNCH(c, "tri_eo_list_reset");
+            eo_list_reset_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv);
+        } else {
+            SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
         }
         SG_CUDA(cudaGetLastError());
     }
@@ -713,7 +924,7 @@ sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double
     } else if (st == SG_OK) {
         st = eo_rounds(c, g, o, k, pl, a);
     }
-    dfree(c, pl.heavy);
+    free_plan(c, &pl);
     return st;
 }
 
@@ -728,8 +939,64 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
     if (count) *count = (int64_t)(v1[kCtrTriangles] - v0[kCtrTriangles]);
     if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
     if (maxdeg) *maxdeg = pl.max_deg;
-    dfree(c, pl.heavy);
+    free_plan(c, &pl);
     return st;
+}
+
+// ---------------------------------------------------------- batched union
+sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt) {
+    Plan pl;
+    pl.light_max = bt->light_max;
+    sg_status st = make_plan(c, o, &pl);
+    if (st == SG_OK) {
+        bt->log_slots = pl.log_slots;
+        bt->smem = pl.smem;
+        bt->max_deg = pl.staged ? (int)std::max<int64_t>(pl.max_deg, 1) : 0;
+    }
+    free_plan(c, &pl);
+    if (st != SG_OK) return st;
+    if (!bt->heavy) st = dalloc(c, (void **)&bt->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    if (st == SG_OK && !bt->buckets)
+        st = dalloc(c, (void **)&bt->buckets, sizeof(unsigned long long) * (2 * kBuckets + 1));
+    return st;
+}
+
+void batch_tr_free(Ctx *c, BatchTri *bt) {
+    dfree(c, bt->heavy);
+    dfree(c, bt->buckets);
+    bt->heavy = nullptr;
+    bt->buckets = nullptr;
+}
+
+// No host synchronisation: the heavy-vertex count stays on the device.
+sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const BatchTri &bt, uint8_t *del) {
+    if (o.n == 0) return SG_OK;
+    SG_CUDA(cudaMemsetAsync(bt.buckets, 0, sizeof(unsigned long long) * (2 * kBuckets + 1), c->stream));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
+    {
+        SG_LAUNCH(c, "tri_classify");
+        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, bt.light_max, bt.buckets,
+                                                                       c->d_ctr);
+    }
+    {
+        SG_LAUNCH(c, "tri_classify");
+        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, bt.light_max, bt.buckets,
+                                                                         bt.buckets + kBuckets, bt.heavy,
+                                                                         bt.buckets + 2 * kBuckets);
+    }
+    SG_CUDA(cudaGetLastError());
+    TriArgs a = base_args(c, o);
+    a.del = del;
+    a.heavy = bt.heavy;
+    a.n_heavy = 0;
+    a.n_heavy_dev = bt.buckets + 2 * kBuckets;
+    a.heavy_log_slots = bt.log_slots;
+    a.heavy_max_deg = bt.max_deg;
+    a.light_max = bt.light_max;
+    a.work = c->d_ctr + kCtrAux;
+    a.bparams = b.params;
+    a.vgid = b.vgid;
+    return launch_enum_raw<Mode::BatchUnion>(c, a, bt.smem, bt.grid_per_sm);
 }
 
 }  // namespace sg

@@ -1,0 +1,229 @@
+"""Continuous-batching serving loop for compression + divergence jobs.
+
+A job is one request of the form "compress this graph with (kernel, p, seed),
+then judge the result with divergence(G, H)" -- the two calls of the library
+(Listing 1 kernels; Sec. 5 metrics).  The server admits jobs while others are
+still running on the GPU, as soon as an execution slot and enough device
+memory are free, so their work overlaps on the device (every slot owns its own
+context and CUDA stream).  Jobs keep their graphs device-resident from upload
+to the last analytic.  Latency is measured from arrival to completion.
+
+The scheduling logic is independent of the GPU: an executor object does the
+work, so the admission policy can be tested with a fake executor on the CPU.
+"""
+from __future__ import annotations
+
+import heapq
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+
+@dataclass
+class Job:
+    """One request: a host CSR plus the compression parameters."""
+
+    n: int
+    off: object  # int64[n+1] (numpy or torch CPU tensor, ideally pinned)
+    col: object  # int32/uint32[nnz]
+    kernel: str
+    p: float
+    seed: int
+    w: object = None
+    arrival: float = 0.0
+    job_id: int = 0
+
+    @property
+    def nnz(self) -> int:
+        return int(len(self.col))
+
+    def device_bytes(self) -> int:
+        """Peak device memory the job needs: input and output CSR, the
+        orientation, per-arc flags and reservations, and the triangle list
+        budget of the edge-once kernels (kept small by the server)."""
+        base = 8 * (self.n + 1) + 4 * self.nnz
+        if self.w is not None:
+            base += 4 * self.nnz
+        per_arc = 4 + 1 + 1 + 8 + 4  # E+ column, del, considered, reservation, output
+        return 3 * base + per_arc * self.nnz + 64 * (self.n + 1) + (64 << 20)
+
+
+@dataclass(order=True)
+class _Pending:
+    arrival: float
+    job_id: int
+    job: Job = field(compare=False)
+    fut: Future = field(compare=False)
+
+
+class Server:
+    """Admit jobs by free device memory and free slots; run them concurrently.
+
+    executor_factory(slot) returns an object with run(job) -> dict and an
+    optional close(); one executor per slot, each on its own stream.
+    memory_budget: bytes of device memory the server may hand out at once.
+    """
+
+    def __init__(self, executor_factory: Callable[[int], object], slots: int, memory_budget: int):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.slots = slots
+        self.budget = int(memory_budget)
+        self.reserved = 0
+        self._cv = threading.Condition()
+        self._pending: List[_Pending] = []
+        self._free_slots = list(range(slots))
+        self._stop = False
+        self._executors = [executor_factory(i) for i in range(slots)]
+        self._records = []
+        self._active = 0
+        self.max_active = 0
+        self._next_id = 0
+        self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self._dispatcher.start()
+
+    # ---------------------------------------------------------------- public
+    def submit(self, job: Job) -> Future:
+        fut: Future = Future()
+        if job.device_bytes() > self.budget:
+            fut.set_exception(MemoryError(f"job needs {job.device_bytes()} bytes, budget is {self.budget}"))
+            return fut
+        with self._cv:
+            if self._stop:
+                raise RuntimeError("server is closed")
+            job.arrival = job.arrival or time.perf_counter()
+            job.job_id = self._next_id
+            self._next_id += 1
+            heapq.heappush(self._pending, _Pending(job.arrival, job.job_id, job, fut))
+            self._cv.notify_all()
+        return fut
+
+    def close(self, wait: bool = True):
+        with self._cv:
+            self._stop = True
+            self._cv.notify_all()
+        if wait:
+            self._dispatcher.join()
+        for ex in self._executors:
+            if hasattr(ex, "close"):
+                ex.close()
+
+    def records(self):
+        with self._cv:
+            return list(self._records)
+
+    # -------------------------------------------------------------- internal
+    def _admissible(self) -> Optional[_Pending]:
+        # first come, first served: the oldest job waits until it fits, which
+        # keeps large jobs from starving behind a stream of small ones
+        if not self._pending or not self._free_slots:
+            return None
+        head = self._pending[0]
+        if self.reserved + head.job.device_bytes() > self.budget:
+            return None
+        return heapq.heappop(self._pending)
+
+    def _dispatch(self):
+        while True:
+            with self._cv:
+                item = None
+                while item is None:
+                    if self._stop and not self._pending:
+                        # wait for running jobs to finish
+                        while self._active:
+                            self._cv.wait()
+                        return
+                    item = self._admissible()
+                    if item is None:
+                        self._cv.wait()
+                slot = self._free_slots.pop()
+                self.reserved += item.job.device_bytes()
+                self._active += 1
+                self.max_active = max(self.max_active, self._active)
+            t = threading.Thread(target=self._run, args=(slot, item), daemon=True)
+            t.start()
+
+    def _run(self, slot: int, item: _Pending):
+        start = time.perf_counter()
+        try:
+            res = self._executors[slot].run(item.job)
+            err = None
+        except Exception as e:  # reported through the future
+            res, err = None, e
+        end = time.perf_counter()
+        with self._cv:
+            self.reserved -= item.job.device_bytes()
+            self._free_slots.append(slot)
+            self._active -= 1
+            self._records.append({"job": item.job.job_id, "arrival": item.job.arrival, "start": start, "end": end,
+                                  "latency": end - item.job.arrival, "m": item.job.nnz // 2, "ok": err is None})
+            self._cv.notify_all()
+        if err is None:
+            item.fut.set_result(res)
+        else:
+            item.fut.set_exception(err)
+
+
+class GpuExecutor:
+    """Runs one job on its own context/stream: upload, compress, divergence."""
+
+    def __init__(self, device: int = 0, eo_list_cap: int = 1 << 22):
+        import paper_1912_08950_gb300 as sg
+
+        self.sg = sg
+        self.ctx = sg.Context(device)
+        # a bounded triangle list keeps each job's footprint predictable
+        self.ctx.set_eo_list_capacity(eo_list_cap)
+
+    def run(self, job: Job) -> dict:
+        sg = self.sg
+        import numpy as np
+
+        off = np.ascontiguousarray(job.off, dtype=np.int64)
+        col = np.ascontiguousarray(job.col).view(np.uint32)
+        G = sg.Graph.from_host(self.ctx, job.n, off, col, job.w)
+        try:
+            H = sg.compress(G, job.kernel, job.p, job.seed)
+            try:
+                d = sg.divergence(G, H)
+                d["nnz_out"] = H.nnz
+            finally:
+                H.free()
+        finally:
+            G.free()
+        return d
+
+    def close(self):
+        self.ctx.close()
+
+
+def poisson_arrivals(rate: float, count: int, seed: int = 1):
+    """Arrival times (seconds from 0) of a Poisson process with the given rate."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def replay(server: Server, jobs: List[Job], arrivals) -> dict:
+    """Submit jobs at their arrival times; return latency percentiles and throughput."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    futs = []
+    for job, at in zip(jobs, arrivals):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        job.arrival = time.perf_counter()
+        futs.append(server.submit(job))
+    results = [f.result() for f in futs]
+    t1 = time.perf_counter()
+    recs = server.records()
+    lat = np.array([r["latency"] for r in recs])
+    edges = sum(r["m"] for r in recs)
+    return {"jobs": len(recs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": t1 - t0, "edges_per_s": edges / (t1 - t0),
+            "jobs_per_s": len(recs) / (t1 - t0), "max_concurrent": server.max_active, "results": results}

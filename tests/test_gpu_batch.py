@@ -1,0 +1,98 @@
+"""Batched compression: every graph of the batch must come out bit for bit as
+it does from sg_compress alone (and as the oracle computes it)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+EDGE_TR = ["uniform", "spectral_logn", "spectral_avgdeg", "tr_random"]
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import paper_1912_08950_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sg):
+    c = sg.Context(0)
+    yield c
+    c.close()
+
+
+def _graphs(count, weighted, seed0):
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i in range(count):
+        s = int(rng.integers(3, 12))
+        ef = int(rng.integers(2, 20))
+        g = gg.rmat(s, ef, seed=seed0 + i)
+        out.append(gg.attach_weights(g, seed=i + 1) if weighted else g)
+    out.insert(count // 2, gg.from_edge_list(0, []) if not weighted else gg.attach_weights(gg.complete(4)))
+    out.insert(count // 3, gg.attach_weights(gg.from_edge_list(6, [])) if weighted else gg.from_edge_list(6, []))
+    return out
+
+
+def _check_batch(sg, ctx, graphs, kernels, ps, seeds, want_weights=False):
+    G = [sg.Graph.from_csr(ctx, g) for g in graphs]
+    B = sg.Batch(ctx, G)
+    outs = B.compress(kernels, ps, seeds, want_weights)
+    for i, (g, h) in enumerate(zip(graphs, outs)):
+        off, col, w = h.download()
+        solo = sg.compress(G[i], kernels[i], ps[i], seeds[i], want_weights)
+        s_off, s_col, s_w = solo.download()
+        solo.free()
+        assert np.array_equal(off, s_off), (i, kernels[i])
+        assert np.array_equal(col, s_col), (i, kernels[i])
+        if s_w is not None and w is not None:
+            assert np.array_equal(w.view(np.uint32), s_w.view(np.uint32)), (i, kernels[i])
+        if i % 5 == 0:
+            o_off, o_col, _ = oracle.compress(g, kernels[i], ps[i], seeds[i], want_weights)
+            assert np.array_equal(off, o_off) and np.array_equal(col, o_col)
+    info = B.info()
+    assert info["vertices"] == sum(g.n for g in graphs)
+    return B, G
+
+
+def test_batch_matches_solo_unweighted(sg, ctx):
+    graphs = _graphs(40, False, 100)
+    n = len(graphs)
+    kernels = [EDGE_TR[i % 4] for i in range(n)]
+    ps = [(0.2, 0.5, 0.8)[i % 3] for i in range(n)]
+    seeds = [i + 1 for i in range(n)]
+    B, G = _check_batch(sg, ctx, graphs, kernels, ps, seeds, want_weights=True)
+    # a second call with new parameters reuses the tuned CUDA graph
+    kernels2 = kernels[::-1]
+    seeds2 = [s * 7 + 3 for s in seeds]
+    outs = B.compress(kernels2, ps, seeds2)
+    for i in range(n):
+        off, col, _ = outs[i].download()
+        solo = sg.compress(G[i], kernels2[i], ps[i], seeds2[i])
+        s_off, s_col, _ = solo.download()
+        solo.free()
+        assert np.array_equal(off, s_off) and np.array_equal(col, s_col)
+    B.free()
+
+
+def test_batch_matches_solo_weighted_maxw(sg, ctx):
+    graphs = _graphs(24, True, 300)
+    n = len(graphs)
+    kernels = [("tr_maxw", "tr_random", "uniform", "spectral_avgdeg")[i % 4] for i in range(n)]
+    ps = [1.0 if k == "tr_maxw" else 0.5 for k in kernels]
+    seeds = [11 * i + 5 for i in range(n)]
+    B, _ = _check_batch(sg, ctx, graphs, kernels, ps, seeds)
+    B.free()
+
+
+def test_batch_rejects_edge_once(sg, ctx):
+    G = [sg.Graph.from_csr(ctx, gg.complete(5))]
+    B = sg.Batch(ctx, G)
+    with pytest.raises(sg.SgError) as e:
+        B.compress(["tr_eo"], [0.5], [1])
+    assert e.value.status == sg.SG_ERR_UNSUPPORTED
+    B.free()

@@ -63,3 +63,14 @@ def test_weights_symmetric_in_range():
     assert np.all(w > 0) and np.all(w <= 1)
     k = w.astype(np.float64) * 2**24
     assert np.all(k == np.round(k))
+
+
+def test_rmat_batch_equals_individual_graphs():
+    scales, efs, seeds = [5, 8, 3, 7, 8], [4, 16, 8, 2, 32], [11, 12, 13, 14, 15]
+    u, vbase, abase = gg.rmat_batch(scales, efs, seeds)
+    _check_csr(u)
+    for i, (s, e, sd) in enumerate(zip(scales, efs, seeds)):
+        one = gg.rmat(s, e, seed=sd)
+        mem = gg.batch_member(u, vbase, i, 1 << s)
+        assert torch.equal(mem.off, one.off) and torch.equal(mem.col, one.col), i
+        assert abase[i] == int(u.off[vbase[i]])

@@ -1,0 +1,147 @@
+"""Serving loop: admission by memory and slots, continuous batching, and
+(on the GPU) identical results alone and in a concurrent mix."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+
+def _job(n=100, nnz=400, kernel="uniform", p=0.5, seed=1, size_hint=None):
+    from paper_1912_08950_gb300.serve import Job
+
+    return Job(n=n, off=np.zeros(n + 1, np.int64), col=np.zeros(nnz, np.uint32), kernel=kernel, p=p, seed=seed)
+
+
+class FakeExecutor:
+    """Sleeps for a job-dependent time and records concurrency."""
+
+    lock = threading.Lock()
+    active = 0
+    peak = 0
+    reserved_seen = []
+
+    def __init__(self, slot, server_ref, delay=0.05):
+        self.slot = slot
+        self.server_ref = server_ref
+        self.delay = delay
+
+    def run(self, job):
+        with FakeExecutor.lock:
+            FakeExecutor.active += 1
+            FakeExecutor.peak = max(FakeExecutor.peak, FakeExecutor.active)
+            srv = self.server_ref[0]
+            FakeExecutor.reserved_seen.append((srv.reserved, srv.budget))
+        time.sleep(self.delay)
+        with FakeExecutor.lock:
+            FakeExecutor.active -= 1
+        if job.kernel == "boom":
+            raise ValueError("executor failure")
+        return {"job": job.seed}
+
+
+def _server(slots, budget, delay=0.05):
+    from paper_1912_08950_gb300.serve import Server
+
+    FakeExecutor.active = FakeExecutor.peak = 0
+    FakeExecutor.reserved_seen = []
+    ref = [None]
+    srv = Server(lambda i: FakeExecutor(i, ref, delay), slots=slots, memory_budget=budget)
+    ref[0] = srv
+    return srv
+
+
+def test_all_jobs_complete_with_their_own_results():
+    srv = _server(4, 1 << 40)
+    futs = [srv.submit(_job(seed=i)) for i in range(20)]
+    assert [f.result()["job"] for f in futs] == list(range(20))
+    srv.close()
+
+
+def test_continuous_batching_overlaps_jobs():
+    srv = _server(4, 1 << 40, delay=0.1)
+    futs = []
+    for i in range(12):  # arrivals while others run
+        futs.append(srv.submit(_job(seed=i)))
+        time.sleep(0.01)
+    for f in futs:
+        f.result()
+    srv.close()
+    assert FakeExecutor.peak == 4 and srv.max_active == 4
+
+
+def test_memory_budget_is_never_exceeded():
+    one = _job().device_bytes()
+    srv = _server(8, int(2.5 * one))  # room for two jobs at a time
+    futs = [srv.submit(_job(seed=i)) for i in range(10)]
+    for f in futs:
+        f.result()
+    srv.close()
+    assert FakeExecutor.peak <= 2
+    assert all(r <= b for r, b in FakeExecutor.reserved_seen)
+
+
+def test_oversized_job_rejected():
+    srv = _server(2, 1000)
+    f = srv.submit(_job())
+    with pytest.raises(MemoryError):
+        f.result()
+    srv.close()
+
+
+def test_failures_reach_the_future():
+    srv = _server(2, 1 << 40)
+    f = srv.submit(_job(kernel="boom"))
+    with pytest.raises(ValueError):
+        f.result()
+    g = srv.submit(_job(seed=5))
+    assert g.result()["job"] == 5
+    srv.close()
+
+
+def test_first_come_first_served_start_order():
+    srv = _server(1, 1 << 40, delay=0.02)
+    futs = [srv.submit(_job(seed=i)) for i in range(6)]
+    for f in futs:
+        f.result()
+    recs = sorted(srv.records(), key=lambda r: r["start"])
+    srv.close()
+    assert [r["job"] for r in recs] == list(range(6))
+
+
+def test_poisson_arrivals_rate():
+    from paper_1912_08950_gb300.serve import poisson_arrivals
+
+    a = poisson_arrivals(2000.0, 20000, seed=3)
+    assert np.all(np.diff(a) > 0)
+    assert abs(len(a) / a[-1] - 2000.0) / 2000.0 < 0.03
+
+
+@pytest.mark.gpu
+def test_results_same_alone_and_in_the_mix():
+    from paper_1912_08950_gb300.serve import GpuExecutor, Job, Server, replay
+
+    specs = [(11, "uniform", 0.5), (12, "tr_eo", 0.5), (10, "tr_random", 0.8), (13, "spectral_avgdeg", 0.5),
+             (12, "tr_eo", 0.2), (11, "tr_random", 0.5), (14, "uniform", 0.3), (10, "tr_eo", 0.8)]
+    graphs = [gg.rmat(s, 16, seed=s) for s, _, _ in specs]
+
+    def jobs():
+        out = []
+        for (s, k, p), g in zip(specs, graphs):
+            off, col, _ = g.numpy()
+            out.append(Job(n=g.n, off=off, col=col, kernel=k, p=p, seed=s))
+        return out
+
+    alone = []
+    srv = Server(lambda i: GpuExecutor(0), slots=1, memory_budget=8 << 30)
+    for j in jobs():
+        alone.append(srv.submit(j).result())
+    srv.close()
+    srv = Server(lambda i: GpuExecutor(0), slots=4, memory_budget=8 << 30)
+    mixed = replay(srv, jobs(), np.zeros(len(specs)))
+    srv.close()
+    assert mixed["max_concurrent"] > 1
+    for a, b in zip(alone, mixed["results"]):
+        assert a["nnz_out"] == b["nnz_out"] and a["cc_h"] == b["cc_h"] and a["kl_bits"] == b["kl_bits"]
