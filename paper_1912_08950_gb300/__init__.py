@@ -130,10 +130,13 @@ class Context:
         _check(_lib.sg_ctx_create(device, C.c_void_p(stream.cuda_stream), C.byref(h)))
         self.handle = h
         self._graphs = weakref.WeakSet()
+        self._batches = weakref.WeakSet()
 
     def close(self):
-        """Free every graph still alive on this context, then the context."""
+        """Free every graph and batch still alive on this context, then the context."""
         if getattr(self, "handle", None):
+            for b in list(self._batches):
+                b.free()
             for g in list(self._graphs):
                 g.free()
             _lib.sg_ctx_destroy(self.handle)
@@ -323,6 +326,7 @@ class Batch:
         _check(_lib.sg_batch_create(ctx.handle, self.count, arr, C.byref(h)))
         self.handle = h
         self._outs = []
+        ctx._batches.add(self)
 
     def compress(self, kernels, ps, seeds, want_weights: bool = False):
         """Compress every graph with its own kernel, p and seed (one CUDA-graph replay).

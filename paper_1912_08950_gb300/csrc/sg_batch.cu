@@ -373,6 +373,21 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
 void sg_batch_free(sg_batch *b) {
     if (!b) return;
     Ctx *c = b->c;
+    if (!ctx_alive(c)) {
+        // the context is gone: release synchronously, without its stream
+        (void)cudaSetDevice(b->u.device);
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        for (void *p : {(void *)b->u.off, (void *)b->u.col, (void *)b->u.w, (void *)b->vgid, (void *)b->d_params,
+                        (void *)b->rm.chunk_row, (void *)b->rm.tile_vlo, (void *)b->o.off, (void *)b->o.col,
+                        (void *)b->o.w, (void *)b->o.fwd_bits, (void *)b->o.status, (void *)b->st_final,
+                        (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->off_c,
+                        (void *)b->out_off, (void *)b->out_col, (void *)b->out_w, (void *)b->d_info})
+            if (p) (void)cudaFree(p);
+        if (b->h_params) cudaFreeHost(b->h_params);
+        if (b->h_info) cudaFreeHost(b->h_info);
+        delete b;
+        return;
+    }
     (void)cudaSetDevice(c->device);
     (void)cudaStreamSynchronize(c->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -409,7 +424,8 @@ sg_status sg_compress_batch(sg_ctx *ctx, sg_batch *b, const sg_kernel *kernels, 
         if (k < (int)SG_UNIFORM || k > (int)SG_TR_EO_MAXW) return fail(SG_ERR_INVALID_ARG, "unknown kernel");
         if (k == (int)SG_TR_EO || k == (int)SG_TR_EO_MAXW)
             return fail(SG_ERR_UNSUPPORTED, "edge-once kernels need host-driven rounds; use sg_compress");
-        if (k == (int)SG_TR_MAXW && !b->u.w) return fail(SG_ERR_NEEDS_WEIGHTS, "the max-weight kernel needs weights");
+        if (k == (int)SG_TR_MAXW && !b->u.w && b->nnz[i] > 0)
+            return fail(SG_ERR_NEEDS_WEIGHTS, "the max-weight kernel needs weights");
     }
     SG_CUDA(cudaStreamSynchronize(c->stream));  // the pinned parameters may still be read by a replay
     for (int i = 0; i < b->count; ++i) {

@@ -18,7 +18,7 @@ static thread_local std::string g_last_error;
 static std::mutex g_ctx_mutex;
 static std::unordered_set<const Ctx *> g_live_ctx;
 
-static bool ctx_alive(const Ctx *c) {
+bool ctx_alive(const Ctx *c) {
     std::lock_guard<std::mutex> lock(g_ctx_mutex);
     return g_live_ctx.count(c) != 0;
 }
@@ -408,7 +408,7 @@ sg_status sg_compress(sg_ctx *ctx, const sg_graph *g, sg_kernel kernel, double p
     if (!(p >= 0.0 && p <= 1.0)) return fail(SG_ERR_INVALID_ARG, "p must lie in [0, 1]");
     if ((int)kernel < (int)SG_UNIFORM || (int)kernel > (int)SG_TR_EO_MAXW)
         return fail(SG_ERR_INVALID_ARG, "unknown kernel");
-    if ((kernel == SG_TR_MAXW || kernel == SG_TR_EO_MAXW) && !g->w)
+    if ((kernel == SG_TR_MAXW || kernel == SG_TR_EO_MAXW) && !g->w && g->nnz > 0)
         return fail(SG_ERR_NEEDS_WEIGHTS, "the max-weight kernels need edge weights");
     Ctx *c = C_(ctx);
     sg_status st = set_device(c);

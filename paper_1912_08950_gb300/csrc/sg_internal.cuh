@@ -74,6 +74,9 @@ sg_status cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::sg::cuda_fail(_e, #call);       \
     } while (0)
 
+// whether a context is still alive (objects may outlive their context)
+bool ctx_alive(const Ctx *c);
+
 // stream-ordered device allocation on the context stream
 sg_status dalloc(Ctx *c, void **p, size_t bytes);
 void dfree(Ctx *c, void *p);
