@@ -139,6 +139,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(local)
     ctx = sg.Context(local, stream=stream)
     G = sg.Graph.from_csr(ctx, g, copy=True)
+    ctx.set_eo_list_capacity(args.eo_list_cap)
     n, m = G.n, G.m
     work = sg.tr_work(G)
 
@@ -211,6 +212,13 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         rows[kern] = {"ms": e0.elapsed_time(e1) / 3, "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
+    # the enumeration alone (triangle counting, no decisions) for comparison
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    sg.tr_work(G)
+    ctx.set_profiling(False)
+    rows["enum_count_only"] = {"ms": ctx.kernel_time("tri_enum")[0], "probes": work["probes"],
+                               "triangles": work["triangles"]}
     H = sg.compress(G, args.kernel, args.p, 1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -271,6 +279,7 @@ def run_ours(args, rank, world):
         "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "n": n, "m": m,
+                   "eo_list_capacity": args.eo_list_cap,
                    "arcs": 2 * m, "triangles": work["triangles"], "probes_per_pass": work["probes"],
                    "max_out_degree": work["max_out_degree"], "kept_arcs": int(A_out),
                    "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
@@ -491,6 +500,8 @@ def main():
     ap.add_argument("--kernel", default="tr_eo")
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--eo-list-cap", type=int, default=0,
+                    help="edge-once triangle list capacity in records (0: automatic, -1: none)")
     ap.add_argument("--mode", choices=["compress", "batch", "serve"], default="compress")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=2000.0)

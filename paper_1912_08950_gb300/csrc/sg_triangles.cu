@@ -35,6 +35,7 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kLightMax = 64;     // largest out-degree processed by one warp
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
+constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
 constexpr int kQ = 96;            // per-warp hit queue entries (31 left over + 2 slabs of hits)
 
 enum class Mode { Count, UnionRandom, UnionMaxw, EoReserve, BatchUnion };
@@ -53,7 +54,7 @@ struct TriArgs {
     const uint32_t *heavy;
     int64_t n_heavy;
     int heavy_log_slots;
-    int heavy_max_deg;           // capacity of the per-vertex list arrays of phase 1
+    int heavy_cap;               // entries of the phase-1 table; larger N+(u) go in chunks
     int light_max;               // out-degrees up to this go to the warp-per-vertex phase
     unsigned long long *work;    // [0] next heavy vertex, [1] next light vertex block
     const unsigned long long *n_heavy_dev;  // if set, the heavy count is read on the device
@@ -122,6 +123,11 @@ __device__ __forceinline__ uint32_t slot_of(uint32_t key, int log_slots) {
 }
 
 __device__ __forceinline__ int ceil_log2(int x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
+static int ceil_log2_host(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
 
 template <typename T>
 __device__ __forceinline__ void swap2(T &a, T &b) {
@@ -337,61 +343,67 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
 
     // ---- phase 1: heavy vertices
     {
-        const int slots = 1 << a.heavy_log_slots;
+        const int cap = a.heavy_cap;  // table capacity: larger N+(u) is processed in chunks
+        const int slots = 4 * cap;
         uint32_t *key = reinterpret_cast<uint32_t *>(tbl);
         uint16_t *idx = reinterpret_cast<uint16_t *>(key + slots);
         uint32_t *vv = reinterpret_cast<uint32_t *>(idx + slots);  // v, off+(v), d+(v) of N+(u)
-        uint32_t *vo = vv + max(a.heavy_max_deg, 1);
-        int *vd = reinterpret_cast<int *>(vo + max(a.heavy_max_deg, 1));
+        uint32_t *vo = vv + cap;
+        int *vd = reinterpret_cast<int *>(vo + cap);
         for (;;) {
-            if (threadIdx.x == 0) {
-                s_h = (long long)atomicAdd(a.work, 1ull);
-                s_next = 0;
-            }
+            if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.work, 1ull);
             __syncthreads();
             const int64_t h = s_h;
             if (h >= n_heavy) break;
             const uint32_t u = __ldg(a.heavy + h);
             const uint32_t ou = (uint32_t)__ldg(a.offp + u);
             const int d = (int)(__ldg(a.offp + u + 1) - (int64_t)ou);
-            const int log_slots = min(a.heavy_log_slots, ceil_log2(4 * d));
-            for (int s2 = threadIdx.x; s2 < (1 << log_slots); s2 += blockDim.x) key[s2] = kEmpty;
-            __syncthreads();
-            const bool staged = a.heavy_max_deg > 0;  // list bounds of N+(u) kept in shared memory
-            for (int i = threadIdx.x; i < d; i += blockDim.x) {
-                const uint32_t v = __ldg(a.colp + ou + i);
-                const bool dead = M == Mode::EoReserve && a.considered[ou + i];
-                if (staged) {
-                    const int64_t ov = __ldg(a.offp + v);
-                    vv[i] = v;
-                    vo[i] = (uint32_t)ov;
-                    // a considered arc u->v closes no live triangle
-                    vd[i] = dead ? 0 : (int)(__ldg(a.offp + v + 1) - ov);
+            const bool staged = d <= cap;  // list bounds of N+(u) kept in shared memory
+            for (int c0 = 0; c0 < d; c0 += cap) {
+                const int cn = min(cap, d - c0);
+                const int log_slots = ceil_log2(4 * cn) < 3 ? 3 : ceil_log2(4 * cn);
+                for (int s2 = threadIdx.x; s2 < (1 << log_slots); s2 += blockDim.x) key[s2] = kEmpty;
+                if (threadIdx.x == 0) s_next = 0;
+                __syncthreads();
+                for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+                    const int i = c0 + k;
+                    const uint32_t v = __ldg(a.colp + ou + i);
+                    const bool dead = M == Mode::EoReserve && a.considered[ou + i];
+                    if (staged) {
+                        const int64_t ov = __ldg(a.offp + v);
+                        vv[i] = v;
+                        vo[i] = (uint32_t)ov;
+                        // a considered arc u->v closes no live triangle
+                        vd[i] = dead ? 0 : (int)(__ldg(a.offp + v + 1) - ov);
+                    }
+                    if (!dead) table_insert(key, idx, log_slots, v, k);
                 }
-                if (!dead) table_insert(key, idx, log_slots, v, i);
-            }
-            __syncthreads();
-            for (;;) {
-                int i = 0;
-                if (lane == 0) i = atomicAdd(&s_next, 1);
-                i = __shfl_sync(kFull, i, 0);
-                if (i >= d) break;
-                uint32_t v, ov;
-                int dv;
-                if (staged) {
-                    v = vv[i];
-                    ov = vo[i];
-                    dv = vd[i];
-                } else {
-                    v = __ldg(a.colp + ou + i);
-                    const int64_t o64 = __ldg(a.offp + v);
-                    ov = (uint32_t)o64;
-                    dv = (M == Mode::EoReserve && a.considered[ou + i]) ? 0 : (int)(__ldg(a.offp + v + 1) - o64);
+                __syncthreads();
+                for (;;) {
+                    int i = 0;
+                    if (lane == 0) i = atomicAdd(&s_next, 1);
+                    i = __shfl_sync(kFull, i, 0);
+                    if (i >= d) break;
+                    uint32_t v, ov;
+                    int dv;
+                    if (staged) {
+                        v = vv[i];
+                        ov = vo[i];
+                        dv = vd[i];
+                    } else {
+                        v = __ldg(a.colp + ou + i);
+                        const int64_t o64 = __ldg(a.offp + v);
+                        ov = (uint32_t)o64;
+                        dv = (M == Mode::EoReserve && a.considered[ou + i]) ? 0
+                                                                            : (int)(__ldg(a.offp + v + 1) - o64);
+                    }
+                    // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
+                    if (lane == 0 && c0 == 0) probes += (unsigned)dv;
+                    probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou + (uint32_t)c0, v, ov, dv, q, qn,
+                                  live, tris, em);
                 }
-                if (lane == 0) probes += (unsigned)dv;
-                probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris, em);
+                __syncthreads();  // the table is rebuilt for the next chunk or vertex
             }
-            __syncthreads();  // the table is rebuilt for the next vertex
         }
     }
 
@@ -665,7 +677,7 @@ struct Plan {
     int light_max = kLightMax;
     int log_slots = 3;
     size_t smem = 0;
-    bool staged = true;  // heavy vertices' list bounds fit in shared memory
+    int heavy_cap = 8;  // phase-1 table entries
 };
 
 static sg_status read_ctr(Ctx *c, int first, int count, unsigned long long *out) {
@@ -708,28 +720,21 @@ static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
     pl->n_heavy = 0;
     for (int b = 0; b < kBuckets; ++b) pl->n_heavy += (int64_t)cnt[b];
     pl->max_deg = (int64_t)cnt[kBuckets];
-    if (pl->max_deg > 65535)
-        return fail(SG_ERR_UNSUPPORTED, "an oriented out-degree above 65535 is not supported");
     if (pl->n_heavy > 0) {
         SG_LAUNCH(c, "tri_classify");
         classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->light_max, pl->buckets,
                                                                          pl->buckets + kBuckets, pl->heavy, nullptr);
     }
     SG_CUDA(cudaGetLastError());
-    // shared memory: hit queues + the larger of the heavy table and the light tables
+    // shared memory: hit queues + the larger of the heavy table (4 slots per
+    // entry, load <= 1/4, with the list bounds of N+(u)) and the light tables
     const size_t queue_bytes = sizeof(HitQueue) * kTW;
     const size_t light_bytes = (size_t)kTW * kLightSlots * 6;
-    int ls = 3;
-    while ((1ll << ls) < 4 * std::max<int64_t>(pl->max_deg, 2)) ++ls;
-    const size_t limit = 220 * 1024;
-    while (ls > 3 && queue_bytes + (size_t)(1ll << ls) * 6 > limit && (1ll << (ls - 1)) >= 2 * pl->max_deg) --ls;
-    if (queue_bytes + (size_t)(1ll << ls) * 6 > limit)
-        return fail(SG_ERR_UNSUPPORTED, "oriented out-degree too large for the shared-memory table");
-    pl->log_slots = ls;
-    // the list bounds of N+(u) are staged in shared memory when they fit
-    size_t heavy_bytes = (size_t)(1ll << ls) * 6 + (size_t)std::max<int64_t>(pl->max_deg, 1) * 12;
-    pl->staged = queue_bytes + heavy_bytes <= limit;
-    if (!pl->staged) heavy_bytes = (size_t)(1ll << ls) * 6 + 12;
+    int cap = 8;
+    while (cap < pl->max_deg && cap < kHeavyCap) cap *= 2;
+    pl->heavy_cap = cap;
+    pl->log_slots = ceil_log2_host(4 * cap);
+    const size_t heavy_bytes = (size_t)cap * (4 * 6 + 12);
     pl->smem = queue_bytes + std::max(light_bytes, heavy_bytes);
     return SG_OK;
 }
@@ -758,7 +763,7 @@ static sg_status launch_enum(Ctx *c, const TriArgs &base, const Plan &pl) {
     a.heavy = pl.heavy;
     a.n_heavy = pl.n_heavy;
     a.heavy_log_slots = pl.log_slots;
-    a.heavy_max_deg = pl.staged ? (int)std::max<int64_t>(pl.max_deg, 1) : 0;
+    a.heavy_cap = pl.heavy_cap;
     a.light_max = pl.light_max;
     a.work = c->d_ctr + kCtrAux;
     SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
@@ -951,7 +956,7 @@ sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt) {
     if (st == SG_OK) {
         bt->log_slots = pl.log_slots;
         bt->smem = pl.smem;
-        bt->max_deg = pl.staged ? (int)std::max<int64_t>(pl.max_deg, 1) : 0;
+        bt->max_deg = pl.heavy_cap;
     }
     free_plan(c, &pl);
     if (st != SG_OK) return st;
@@ -991,7 +996,7 @@ sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const Batc
     a.n_heavy = 0;
     a.n_heavy_dev = bt.buckets + 2 * kBuckets;
     a.heavy_log_slots = bt.log_slots;
-    a.heavy_max_deg = bt.max_deg;
+    a.heavy_cap = bt.max_deg;
     a.light_max = bt.light_max;
     a.work = c->d_ctr + kCtrAux;
     a.bparams = b.params;

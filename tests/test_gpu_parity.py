@@ -247,3 +247,14 @@ def test_errors(sg, ctx):
     G = sg.Graph.from_csr(ctx, g, validate=True)
     _ = sg.compress(G, "uniform", 0.5, 1)
     G.free()
+
+
+@pytest.mark.parametrize("kern,p", [("tr_random", 0.3), ("tr_eo", 0.5), ("tr_eo", 1.0)])
+def test_chunked_heavy_tables(sg, ctx, kern, p):
+    # K600 has out-degrees up to 599: the largest vertices' N+(u) exceeds one
+    # shared-memory table and is processed in chunks
+    g = gg.complete(600)
+    _same(sg, ctx, g, kern, p, 12)
+    G = sg.Graph.from_csr(ctx, g)
+    assert sg.triangle_count(G) == 600 * 599 * 598 // 6
+    G.free()
