@@ -23,10 +23,12 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-UNIFORM, SPECTRAL_LOGN, SPECTRAL_AVGDEG, TR_RANDOM, TR_MAXW, TR_EO, TR_EO_MAXW = range(7)
+UNIFORM, SPECTRAL_LOGN, SPECTRAL_AVGDEG, TR_RANDOM, TR_MAXW, TR_EO, TR_EO_MAXW, TR_P2, TR_MINCOUNT, \
+    TR_EO_MINCOUNT = range(10)
 KERNELS = {
     "uniform": UNIFORM, "spectral_logn": SPECTRAL_LOGN, "spectral_avgdeg": SPECTRAL_AVGDEG,
     "tr_random": TR_RANDOM, "tr_maxw": TR_MAXW, "tr_eo": TR_EO, "tr_eo_maxw": TR_EO_MAXW,
+    "tr_p2": TR_P2, "tr_mincount": TR_MINCOUNT, "tr_eo_mincount": TR_EO_MINCOUNT,
 }
 
 

@@ -36,6 +36,11 @@
  *    (r2, a, b, c); a triangle is accepted iff none of its edges was already
  *    considered; an accepted triangle marks its three edges considered and
  *    deletes its chosen edge;
+ *  - Triangle p-2-Reduction (Sec. 4.3, x = 2) deletes two edges of each
+ *    selected triangle chosen u.a.r., i.e. keeps the edge the draw r1 picks;
+ *  - Min-Count TR (the technical-report variant behind "CT", Sec. 7) deletes
+ *    the edge lying in the fewest triangles of the input, ties broken by the
+ *    smaller endpoint pair; CT is Edge-Once with that choice;
  *  - PageRank (Table 1; output "P", a distribution) uses damping d, uniform
  *    teleport and uniform redistribution of dangling mass; KL divergence is
  *    sum_i P(i) log2(P(i)/Q(i)) (Sec. 5.2.3).
@@ -55,7 +60,10 @@ enum {
     ORC_TR_RANDOM = 3,
     ORC_TR_MAXW = 4,
     ORC_TR_EO = 5,
-    ORC_TR_EO_MAXW = 6
+    ORC_TR_EO_MAXW = 6,
+    ORC_TR_P2 = 7,          /* Triangle p-2-Reduction: two edges of each selected triangle go */
+    ORC_TR_MINCOUNT = 8,    /* Min-Count p-1-TR: the edge in the fewest triangles of G goes */
+    ORC_TR_EO_MINCOUNT = 9  /* "CT": Edge-Once with the min-count choice */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -232,10 +240,38 @@ static int maxw_choice(const float *w, const int64_t e[3], const uint32_t lo[3],
     return best;
 }
 
+/* the edge in the fewest triangles under the order (count, lo, hi) */
+static int mincount_choice(const int64_t *tcount, const int64_t e[3], const uint32_t lo[3], const uint32_t hi[3])
+{
+    int best = 0;
+    for (int k = 1; k < 3; ++k) {
+        int64_t ck = tcount[e[k]], cb = tcount[e[best]];
+        int smaller = (ck < cb) || (ck == cb && (lo[k] < lo[best] || (lo[k] == lo[best] && hi[k] < hi[best])));
+        if (smaller) best = k;
+    }
+    return best;
+}
+
+static void tcount_cb(uint32_t a, uint32_t b, uint32_t c, int64_t eab, int64_t eac, int64_t ebc, void *ctx)
+{
+    (void)a; (void)b; (void)c;
+    int64_t *t = (int64_t *)ctx;
+    ++t[eab]; ++t[eac]; ++t[ebc];
+}
+
+/* number of triangles of G through every edge, indexed by canonical edge id */
+static int64_t *edge_triangle_counts(int64_t n, int64_t nnz, const int64_t *off, const uint32_t *col)
+{
+    int64_t *t = (int64_t *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(int64_t));
+    if (t) for_each_triangle(n, off, col, tcount_cb, t);
+    return t;
+}
+
 typedef struct {
     uint64_t seed, tp;
-    int maxw;
+    int mode;  /* 0 random, 1 max-weight, 2 two edges, 3 min-count */
     const float *w;
+    const int64_t *tcount;
     uint8_t *del;
 } union_ctx;
 
@@ -247,7 +283,14 @@ static void union_cb(uint32_t a, uint32_t b, uint32_t c, int64_t eab, int64_t ea
     if ((uint64_t)r[0] >= U->tp) return; /* triangle not selected */
     int64_t e[3] = {eab, eac, ebc};
     uint32_t lo[3] = {a, a, b}, hi[3] = {b, c, c};
-    int k = U->maxw ? maxw_choice(U->w, e, lo, hi) : random_choice(r[1]);
+    if (U->mode == 2) { /* x = 2: all but the edge the draw picks */
+        int keep = random_choice(r[1]);
+        for (int k = 0; k < 3; ++k) if (k != keep) U->del[e[k]] = 1;
+        return;
+    }
+    int k = U->mode == 1 ? maxw_choice(U->w, e, lo, hi)
+          : U->mode == 3 ? mincount_choice(U->tcount, e, lo, hi)
+                         : random_choice(r[1]);
     U->del[e[k]] = 1; /* SG.del is idempotent */
 }
 
@@ -307,7 +350,7 @@ int64_t orc_compress(int64_t n, int64_t nnz, const int64_t *off, const uint32_t 
 {
     if (!(p >= 0.0 && p <= 1.0)) return -1;
     if ((kernel == ORC_TR_MAXW || kernel == ORC_TR_EO_MAXW) && !w) return -2;
-    if (kernel < ORC_UNIFORM || kernel > ORC_TR_EO_MAXW) return -1;
+    if (kernel < ORC_UNIFORM || kernel > ORC_TR_EO_MINCOUNT) return -1;
     uint8_t *del = (uint8_t *)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
     if (!del) return -3;
     float *wnew = NULL;
@@ -355,24 +398,37 @@ int64_t orc_compress(int64_t n, int64_t nnz, const int64_t *off, const uint32_t 
                 }
             }
         wsrc = wnew;
-    } else if (kernel == ORC_TR_RANDOM || kernel == ORC_TR_MAXW) {
-        union_ctx U = {seed, orc_threshold(p), kernel == ORC_TR_MAXW, w, del};
+    } else if (kernel == ORC_TR_RANDOM || kernel == ORC_TR_MAXW || kernel == ORC_TR_P2 ||
+               kernel == ORC_TR_MINCOUNT) {
+        int64_t *tc = NULL;
+        if (kernel == ORC_TR_MINCOUNT) {
+            tc = edge_triangle_counts(n, nnz, off, col);
+            if (!tc) { free(del); return -3; }
+        }
+        union_ctx U = {seed, orc_threshold(p),
+                       kernel == ORC_TR_MAXW ? 1 : kernel == ORC_TR_P2 ? 2 : kernel == ORC_TR_MINCOUNT ? 3 : 0,
+                       w, tc, del};
         for_each_triangle(n, off, col, union_cb, &U);
-    } else { /* ORC_TR_EO, ORC_TR_EO_MAXW */
+        free(tc);
+    } else { /* ORC_TR_EO, ORC_TR_EO_MAXW, ORC_TR_EO_MINCOUNT */
         eo_ctx E = {seed, orc_threshold(p), NULL, 0, 0, 0};
         for_each_triangle(n, off, col, eo_collect_cb, &E);
         if (E.oom) { free(E.v); free(del); return -3; }
         qsort(E.v, (size_t)E.k, sizeof(sel_tri), sel_cmp);
         uint8_t *considered = (uint8_t *)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
-        if (!considered) { free(E.v); free(del); return -3; }
+        int64_t *tc = kernel == ORC_TR_EO_MINCOUNT ? edge_triangle_counts(n, nnz, off, col) : NULL;
+        if (!considered || (kernel == ORC_TR_EO_MINCOUNT && !tc)) { free(tc); free(considered); free(E.v); free(del); return -3; }
         for (int64_t s = 0; s < E.k; ++s) {
             sel_tri *t = &E.v[s];
             if (considered[t->e[0]] || considered[t->e[1]] || considered[t->e[2]]) continue;
             considered[t->e[0]] = considered[t->e[1]] = considered[t->e[2]] = 1;
             uint32_t lo[3] = {t->a, t->a, t->b}, hi[3] = {t->b, t->c, t->c};
-            int k = (kernel == ORC_TR_EO_MAXW) ? maxw_choice(w, t->e, lo, hi) : random_choice(t->r1);
+            int k = (kernel == ORC_TR_EO_MAXW) ? maxw_choice(w, t->e, lo, hi)
+                  : (kernel == ORC_TR_EO_MINCOUNT) ? mincount_choice(tc, t->e, lo, hi)
+                                                   : random_choice(t->r1);
             del[t->e[k]] = 1;
         }
+        free(tc);
         if (accepted_out) {
             for (int64_t x = 0; x < n; ++x)
                 for (int64_t i = off[x]; i < off[x + 1]; ++i)
@@ -385,6 +441,18 @@ int64_t orc_compress(int64_t n, int64_t nnz, const int64_t *off, const uint32_t 
     int64_t k = build_output(n, off, col, wsrc, del, off_out, col_out, w_out);
     free(wnew);
     free(del);
+    return k;
+}
+
+/* |N(x) ∩ N(y)| by a merge of the two sorted lists */
+static int64_t common_count(const int64_t *off, const uint32_t *col, uint32_t x, uint32_t y)
+{
+    int64_t i = off[x], j = off[y], k = 0;
+    while (i < off[x + 1] && j < off[y + 1]) {
+        if (col[i] < col[j]) ++i;
+        else if (col[j] < col[i]) ++j;
+        else { ++k; ++i; ++j; }
+    }
     return k;
 }
 
@@ -411,15 +479,25 @@ int orc_tr_union_edge_deleted(int64_t n, const int64_t *off, const uint32_t *col
         draw(seed, a, b, c, ORC_TAG_TRI, r);
         if ((uint64_t)r[0] >= tp) continue;
         int k;
+        uint32_t l3[3] = {a, a, b}, h3[3] = {b, c, c};
         if (kernel == ORC_TR_MAXW) {
             int64_t e[3] = {edge_id(off, col, a, b), edge_id(off, col, a, c), edge_id(off, col, b, c)};
-            uint32_t l3[3] = {a, a, b}, h3[3] = {b, c, c};
             k = maxw_choice(w, e, l3, h3);
+        } else if (kernel == ORC_TR_MINCOUNT) {
+            /* triangle counts of the three edges: |N(x) ∩ N(y)| each */
+            int64_t cnt[3] = {common_count(off, col, a, b), common_count(off, col, a, c),
+                              common_count(off, col, b, c)};
+            int64_t e[3] = {0, 1, 2};
+            k = mincount_choice(cnt, e, l3, h3);
         } else {
             k = random_choice(r[1]);
         }
         uint32_t dl = (k == 2) ? b : a, dh = (k == 0) ? b : c;
-        if (dl == lo && dh == hi) return 1;
+        if (kernel == ORC_TR_P2) {
+            if (!(dl == lo && dh == hi)) return 1; /* only the drawn edge stays */
+        } else if (dl == lo && dh == hi) {
+            return 1;
+        }
     }
     return 0;
 }

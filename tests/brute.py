@@ -94,3 +94,53 @@ def tr_eo(n, E, p, seed, W=None):
         k = ((r1 * 3) >> 32) if W is None else max(range(3), key=lambda i: (W[es[i]], es[i]))
         D.add(es[k])
     return E - D, accepted
+
+
+def edge_triangle_counts(n, E):
+    cnt = {e: 0 for e in E}
+    for a, b, c in triangles(n, E):
+        for e in ((a, b), (a, c), (b, c)):
+            cnt[e] += 1
+    return cnt
+
+
+def tr_p2(n, E, p, seed):
+    """Each selected triangle keeps only the edge its draw r1 names."""
+    D = set()
+    for a, b, c in triangles(n, E):
+        r = draw(seed, a, b, c, TAG_TRI)
+        if int(r[0]) >= thr(p):
+            continue
+        es = [(a, b), (a, c), (b, c)]
+        keep = (int(r[1]) * 3) >> 32
+        D.update(e for i, e in enumerate(es) if i != keep)
+    return E - D
+
+
+def tr_mincount(n, E, p, seed):
+    cnt = edge_triangle_counts(n, E)
+    D = set()
+    for a, b, c in triangles(n, E):
+        r = draw(seed, a, b, c, TAG_TRI)
+        if int(r[0]) < thr(p):
+            es = [(a, b), (a, c), (b, c)]
+            D.add(min(es, key=lambda e: (cnt[e], e)))
+    return E - D
+
+
+def tr_eo_mincount(n, E, p, seed):
+    cnt = edge_triangle_counts(n, E)
+    sel = []
+    for a, b, c in triangles(n, E):
+        r = draw(seed, a, b, c, TAG_TRI)
+        if int(r[0]) < thr(p):
+            sel.append((int(r[2]), a, b, c))
+    sel.sort()
+    considered, D = set(), set()
+    for r2, a, b, c in sel:
+        es = [(a, b), (a, c), (b, c)]
+        if any(e in considered for e in es):
+            continue
+        considered.update(es)
+        D.add(min(es, key=lambda e: (cnt[e], e)))
+    return E - D

@@ -372,7 +372,7 @@ def test_eo_removes_no_more_than_union():
 # --------------------------------------------------------------------------
 # per-edge union query agrees with the whole-graph kernels
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("kern", ["tr_random", "tr_maxw"])
+@pytest.mark.parametrize("kern", ["tr_random", "tr_maxw", "tr_p2", "tr_mincount"])
 def test_union_edge_query(kern):
     g = gg.attach_weights(gg.rmat(9, 16, seed=2))
     E = brute.edge_set(g)
@@ -472,3 +472,65 @@ def test_divergence_of_identity_is_zero():
     g = gg.rmat(10, 8, seed=1)
     d = oracle.divergence(g, g)
     assert d["kl_bits"] == 0.0 and d["cc_g"] == d["cc_h"]
+
+
+
+# --------------------------------------------------------------------------
+# Triangle p-2-Reduction and Min-Count TR (Sec. 4.3 x = 2; "CT", Sec. 7)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,q,seed", [(16, 0.5, 1), (30, 0.35, 2), (48, 0.2, 3)])
+@pytest.mark.parametrize("p", [0.4, 1.0])
+def test_new_tr_kernels_match_brute_force(n, q, seed, p):
+    g = gg.gnp(n, q, seed)
+    E = brute.edge_set(g)
+    assert _edges_of(n, oracle.compress(g, "tr_p2", p, seed)) == brute.tr_p2(n, E, p, seed)
+    assert _edges_of(n, oracle.compress(g, "tr_mincount", p, seed)) == brute.tr_mincount(n, E, p, seed)
+    assert _edges_of(n, oracle.compress(g, "tr_eo_mincount", p, seed)) == brute.tr_eo_mincount(n, E, p, seed)
+
+
+def test_p2_single_triangle_keeps_one_edge():
+    g = gg.complete(3)
+    for s in range(1, 20):
+        off, col, _ = oracle.compress(g, "tr_p2", 1.0, s)
+        assert col.size == 2
+        r = brute.draw(s, 0, 1, 2, brute.TAG_TRI)
+        assert _edges_of(3, (off, col, None)) == {[(0, 1), (0, 2), (1, 2)][(int(r[1]) * 3) >> 32]}
+
+
+def test_p2_on_disjoint_triangles():
+    k = 500
+    g = gg.disjoint_union(*[gg.complete(3)] * k)
+    off, col, _ = oracle.compress(g, "tr_p2", 1.0, 9)
+    assert col.size == 2 * k  # one edge of every triangle left
+
+
+def test_mincount_tie_and_choice():
+    # K3: every edge lies in one triangle; ties go to the smallest pair {0,1}
+    off, col, _ = oracle.compress(gg.complete(3), "tr_mincount", 1.0, 5)
+    assert _edges_of(3, (off, col, None)) == {(0, 2), (1, 2)}
+    # diamond: {1,2} lies in two triangles, so it is never the one deleted
+    for s in range(1, 10):
+        H = _edges_of(4, oracle.compress(gg.diamond(), "tr_mincount", 1.0, s))
+        assert (1, 2) in H
+
+
+def test_mincount_deletes_least_covered_edge():
+    g = gg.rmat(9, 16, seed=4)
+    E = brute.edge_set(g)
+    cnt = brute.edge_triangle_counts(g.n, E)
+    H = _edges_of(g.n, oracle.compress(g, "tr_mincount", 1.0, 2))
+    for a, b, c in (tuple(int(v) for v in t) for t in oracle.triangle_list(g)):
+        es = [(a, b), (a, c), (b, c)]
+        gone = [e for e in es if e not in H]
+        # the triangle's own choice is deleted (others may be deleted by other triangles)
+        assert min(es, key=lambda e: (cnt[e], e)) in gone
+
+
+def test_ct_is_edge_once_packing():
+    # same accepted set as EO, so the same number of deletions; CC preserved
+    g = gg.rmat(10, 16, seed=6)
+    a = oracle.compress(g, "tr_eo", 0.5, 3)[1].size
+    b = oracle.compress(g, "tr_eo_mincount", 0.5, 3)
+    assert a == b[1].size
+    Hm = sp.csr_matrix((np.ones(b[1].size), b[1].astype(np.int64), b[0]), shape=(g.n, g.n))
+    assert connected_components(_scipy(g))[0] == connected_components(Hm)[0]
