@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+    "rmat19": dict(scale=19, ef=16, desc="R-MAT scale 19, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat14": dict(scale=14, ef=16, desc="R-MAT scale 14, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
 }

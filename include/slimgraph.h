@@ -69,6 +69,14 @@ typedef enum sg_status {
  *                      of (r2, a, b, c), each accepted iff none of its edges was
  *                      already considered; keeps the connected components.
  *  SG_TR_EO_MAXW       Edge-Once with the max-weight choice.
+ *  SG_TR_P2            Triangle p-2-Reduction (Sec. 4.3, x = 2): every selected
+ *                      triangle deletes two of its edges and keeps only the
+ *                      one its draw r1 names; deletions accumulate (union).
+ *  SG_TR_MINCOUNT      as SG_TR_RANDOM, deleting the edge of each selected
+ *                      triangle that lies in the fewest triangles of G (ties by
+ *                      endpoint pair); one extra enumeration pass counts them.
+ *  SG_TR_EO_MINCOUNT   Edge-Once with the min-count choice (the "CT" variant
+ *                      of Sec. 7); keeps the connected components.
  */
 typedef enum sg_kernel {
     SG_UNIFORM = 0,
@@ -77,7 +85,10 @@ typedef enum sg_kernel {
     SG_TR_RANDOM = 3,
     SG_TR_MAXW = 4,
     SG_TR_EO = 5,
-    SG_TR_EO_MAXW = 6
+    SG_TR_EO_MAXW = 6,
+    SG_TR_P2 = 7,
+    SG_TR_MINCOUNT = 8,
+    SG_TR_EO_MINCOUNT = 9
 } sg_kernel;
 
 /* Opaque context: device, stream, device error word, launch statistics. */
@@ -188,7 +199,8 @@ void sg_batch_free(sg_batch *b);
  * limit) and keeps the fastest.  outs[i] receives a handle whose arrays live
  * inside the batch: they stay valid until the next sg_compress_batch on this
  * batch or sg_batch_free; release each handle with sg_graph_free.  Edge-once
- * kernels need host-driven rounds and return SG_ERR_UNSUPPORTED here. */
+ * kernels need host-driven rounds and SG_TR_MINCOUNT a counting pass: they
+ * return SG_ERR_UNSUPPORTED here. */
 sg_status sg_compress_batch(sg_ctx *ctx, sg_batch *b, const sg_kernel *kernels, const double *ps,
                             const uint64_t *seeds, int want_weights, sg_graph **outs);
 /* Size of the union and the work-partition setting the autotuner chose

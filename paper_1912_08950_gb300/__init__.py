@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_INVALID_GRAPH", 
                 4: "SG_ERR_OOM", 5: "SG_ERR_CUDA", 6: "SG_ERR_TIMEOUT", 7: "SG_ERR_UNSUPPORTED"}
 
 KERNELS = {"uniform": 0, "spectral_logn": 1, "spectral_avgdeg": 2, "tr_random": 3, "tr_maxw": 4,
-           "tr_eo": 5, "tr_eo_maxw": 6}
+           "tr_eo": 5, "tr_eo_maxw": 6, "tr_p2": 7, "tr_mincount": 8, "tr_eo_mincount": 9}
 
 
 class SgError(RuntimeError):

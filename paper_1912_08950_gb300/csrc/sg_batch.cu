@@ -421,9 +421,11 @@ sg_status sg_compress_batch(sg_ctx *ctx, sg_batch *b, const sg_kernel *kernels, 
     for (int i = 0; i < b->count; ++i) {
         const int k = (int)kernels[i];
         if (!(ps[i] >= 0.0 && ps[i] <= 1.0)) return fail(SG_ERR_INVALID_ARG, "p must lie in [0, 1]");
-        if (k < (int)SG_UNIFORM || k > (int)SG_TR_EO_MAXW) return fail(SG_ERR_INVALID_ARG, "unknown kernel");
-        if (k == (int)SG_TR_EO || k == (int)SG_TR_EO_MAXW)
+        if (k < (int)SG_UNIFORM || k > (int)SG_TR_EO_MINCOUNT) return fail(SG_ERR_INVALID_ARG, "unknown kernel");
+        if (k == (int)SG_TR_EO || k == (int)SG_TR_EO_MAXW || k == (int)SG_TR_EO_MINCOUNT)
             return fail(SG_ERR_UNSUPPORTED, "edge-once kernels need host-driven rounds; use sg_compress");
+        if (k == (int)SG_TR_MINCOUNT)
+            return fail(SG_ERR_UNSUPPORTED, "the min-count kernel needs a counting pass; use sg_compress");
         if (k == (int)SG_TR_MAXW && !b->u.w && b->nnz[i] > 0)
             return fail(SG_ERR_NEEDS_WEIGHTS, "the max-weight kernel needs weights");
     }

@@ -93,6 +93,8 @@ sg_status check_device_error(Ctx *c) {
         return fail(SG_ERR_TIMEOUT, "a device-side wait of the prefix scan gave up; outputs are invalid");
     case kDevBadGraph:
         return fail(SG_ERR_INVALID_GRAPH, "the CSR failed validation");
+    case kDevTableFull:
+        return fail(SG_ERR_CUDA, "a shared-memory cuckoo table overflowed its stash; outputs are invalid");
     default:
         return fail(SG_ERR_CUDA, "device error code " + std::to_string(code));
     }
@@ -406,7 +408,7 @@ sg_status sg_compress(sg_ctx *ctx, const sg_graph *g, sg_kernel kernel, double p
     if (!ctx || !g || !out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (!(p >= 0.0 && p <= 1.0)) return fail(SG_ERR_INVALID_ARG, "p must lie in [0, 1]");
-    if ((int)kernel < (int)SG_UNIFORM || (int)kernel > (int)SG_TR_EO_MAXW)
+    if ((int)kernel < (int)SG_UNIFORM || (int)kernel > (int)SG_TR_EO_MINCOUNT)
         return fail(SG_ERR_INVALID_ARG, "unknown kernel");
     if ((kernel == SG_TR_MAXW || kernel == SG_TR_EO_MAXW) && !g->w && g->nnz > 0)
         return fail(SG_ERR_NEEDS_WEIGHTS, "the max-weight kernels need edge weights");

@@ -1,6 +1,7 @@
 // Triangle enumeration over the degree-ordered orientation E+ and the
-// Triangle p-1-Reduction kernels of Slim Graph (Sec. 4.3; Listing 1
-// p-1-reduction and p-1-reduction-EO).
+// Triangle p-x-Reduction kernels of Slim Graph (Sec. 4.3; Listing 1
+// p-1-reduction and p-1-reduction-EO; x = 2; the min-count "CT" choice of
+// Sec. 7).
 //
 // Enumeration.  Every triangle {u, v, w} with u < v < w in the degree order
 // (d, id) is found exactly once, at the oriented arc u->v, as w in
@@ -14,8 +15,10 @@
 // Decisions.  A hit (a triangle) is pushed to a per-warp queue; whenever 32
 // hits are queued the warp decides all of them at once with full lanes:
 // Philox4x32-10 on the sorted original ids (a, b, c) selects the triangle
-// (r0 < floor(p 2^32)) and picks the edge to delete (r1, or the heaviest edge).
-// Union kernels store del[arc] = 1 (a plain, idempotent byte store).  The
+// (r0 < floor(p 2^32)) and picks the edge to delete (r1, the heaviest edge, or
+// the edge in the fewest triangles of G, counted by an earlier EdgeCount pass);
+// the p-2 kernel deletes the two edges r1 does not pick.  Union kernels store
+// del[arc] = 1 (a plain, idempotent byte store).  The
 // Edge-Once kernel instead reserves each edge of every live selected triangle
 // with a 64-bit atomicMin of (r2 << 32 | third vertex); an edge pass then
 // accepts every triangle that holds all three of its reservations.  Accepted
@@ -38,7 +41,10 @@ constexpr int kTW = 8;            // warps per CTA
 constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
 constexpr int kQ = 96;            // per-warp hit queue entries (31 left over + 2 slabs of hits)
 
-enum class Mode { Count, UnionRandom, UnionMaxw, EoReserve, BatchUnion };
+// Count: totals only.  EdgeCount: adds every triangle to the counters of its
+// three edges.  Union*: the union-semantics TR kernels.  EoReserve: one
+// edge-once bidding pass.  BatchUnion: union kernels over a batch of graphs.
+enum class Mode { Count, EdgeCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCount, EoReserve, BatchUnion };
 
 struct TriArgs {
     const int64_t *offp;
@@ -50,12 +56,15 @@ struct TriArgs {
     uint8_t *del;
     const uint8_t *considered;
     unsigned long long *resv;
+    uint32_t *tcnt;               // triangles of G through each arc of E+ (EdgeCount adds, min-count reads)
+    unsigned long long eo_theta;  // edge-once: only triangles with r2 < eo_theta bid this round
     unsigned long long *ctr;
     const uint32_t *heavy;
     int64_t n_heavy;
     int heavy_log_slots;
     int heavy_cap;               // entries of the phase-1 table; larger N+(u) go in chunks
     int light_max;               // out-degrees up to this go to the warp-per-vertex phase
+    int *err;                    // device error word (a cuckoo stash overflow)
     unsigned long long *work;    // [0] next heavy vertex, [1] next light vertex block
     const unsigned long long *n_heavy_dev;  // if set, the heavy count is read on the device
     // batched union: per-graph parameters and the graph of every vertex
@@ -136,13 +145,26 @@ __device__ __forceinline__ void swap2(T &a, T &b) {
     b = t;
 }
 
+// The edge in the fewest triangles of G under (count, lo, hi).  The arcs are
+// passed in the order (x0,x1), (x0,x2), (x1,x2) of the sorted endpoints, which
+// is also their (lo, hi) order, so a tie keeps the earlier arc.
+template <typename I>
+__device__ __forceinline__ I mincount_arc(const uint32_t *tcnt, I e01, I e02, I e12) {
+    const uint32_t c01 = __ldg(tcnt + e01), c02 = __ldg(tcnt + e02), c12 = __ldg(tcnt + e12);
+    I best = e01;
+    uint32_t bc = c01;
+    if (c02 < bc) { best = e02; bc = c02; }
+    if (c12 < bc) best = e12;
+    return best;
+}
+
 // One triangle (u, v, w) with its three oriented arcs: selection and action.
 // Warp-collective (the edge-once list writer uses ballots); lanes without a
 // triangle pass valid = false.
 template <Mode M>
 __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u, uint32_t v, uint32_t w,
                                        uint32_t iuv, uint32_t iuw, uint32_t ivw, unsigned &live, Emitter &em) {
-    if constexpr (M == Mode::Count) {
+    if constexpr (M == Mode::Count || M == Mode::EdgeCount) {
         return;
     } else {
         bool emit = false;
@@ -170,6 +192,12 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                     } else {
                         const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
                         best = k == 0 ? e01 : (k == 1 ? e02 : e12);
+                        if (P.kernel == (int)SG_TR_P2) {  // the drawn edge is the one kept
+                            if (k != 0) a.del[e01] = 1;
+                            if (k != 1) a.del[e02] = 1;
+                            if (k != 2) a.del[e12] = 1;
+                            return;
+                        }
                     }
                     a.del[best] = 1;
                 }
@@ -188,6 +216,14 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                 if constexpr (M == Mode::UnionRandom) {
                     const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
                     a.del[k == 0 ? e01 : (k == 1 ? e02 : e12)] = 1;
+                } else if constexpr (M == Mode::UnionP2) {
+                    // x = 2: the drawn edge stays, the other two go
+                    const int k = (int)(((unsigned long long)r.y * 3ull) >> 32);
+                    if (k != 0) a.del[e01] = 1;
+                    if (k != 1) a.del[e02] = 1;
+                    if (k != 2) a.del[e12] = 1;
+                } else if constexpr (M == Mode::UnionMinCount) {
+                    a.del[mincount_arc(a.tcnt, e01, e02, e12)] = 1;
                 } else if constexpr (M == Mode::UnionMaxw) {
                     // heaviest edge under (weight, lo, hi)
                     const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
@@ -198,11 +234,14 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                     if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
                     a.del[best] = 1;
                 } else {  // EoReserve
-                    if (!(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
-                        const unsigned long long hi = (unsigned long long)r.z << 32;
-                        atomicMin(a.resv + e01, hi | x2);
-                        atomicMin(a.resv + e02, hi | x1);
-                        atomicMin(a.resv + e12, hi | x0);
+                    if (a.considered == nullptr || !(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
+                        // the round's prefix of the (r2, a, b, c) order bids for its edges
+                        if ((unsigned long long)r.z < a.eo_theta) {
+                            const unsigned long long hi = (unsigned long long)r.z << 32;
+                            atomicMin(a.resv + e01, hi | x2);
+                            atomicMin(a.resv + e02, hi | x1);
+                            atomicMin(a.resv + e12, hi | x0);
+                        }
                         ++live;
                         emit = true;
                         rec = TriRec{x0, x1, x2, r.y, r.z, e01, e02, e12};
@@ -243,32 +282,60 @@ __device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn
     __syncwarp();
 }
 
-__device__ __forceinline__ void table_insert(uint32_t *key, uint16_t *idx, int log_slots, uint32_t w, int i) {
-    const uint32_t mask = (1u << log_slots) - 1u;
-    uint32_t s = slot_of(w, log_slots);
-    for (;;) {
-        const uint32_t old = atomicCAS(key + s, kEmpty, w);
-        if (old == kEmpty) { idx[s] = (uint16_t)i; return; }
-        s = (s + 1) & mask;
+// Shared-memory cuckoo table of N+(u) (Pagh & Rodler's cuckoo hashing; the
+// concurrent exchange-based insertion follows Alcantara et al.'s GPU tables):
+// a slot holds (vertex << 32 | position in N+(u)); every key lives in one of
+// two slots, so a lookup reads exactly two slots with no probe loop and no
+// divergence.  Load <= 1/4.  An insertion that keeps displacing keys for
+// kCuckooIters exchanges leaves its homeless entry in a small stash that
+// lookups then scan; a full stash raises a device error.
+constexpr unsigned long long kSlotEmpty = ~0ull;
+constexpr int kCuckooIters = 32;
+constexpr int kStash = 16;
+
+struct Table {
+    unsigned long long *slot;
+    unsigned long long *stash;
+    int *stash_n;
+};
+
+__device__ __forceinline__ uint32_t h1_of(uint32_t w, int sh) { return (w * 0x9E3779B1u) >> sh; }
+__device__ __forceinline__ uint32_t h2_of(uint32_t w, int sh) { return (w * 0x85EBCA77u) >> sh; }
+
+__device__ __forceinline__ void table_insert(const Table &t, int log_slots, uint32_t w, int i, int *err) {
+    const int sh = 32 - log_slots;
+    unsigned long long cur = ((unsigned long long)w << 32) | (uint32_t)i;
+    uint32_t pos = h1_of(w, sh);
+    for (int it = 0; it < kCuckooIters; ++it) {
+        const unsigned long long old = atomicExch(t.slot + pos, cur);
+        if (old == kSlotEmpty) return;
+        cur = old;
+        const uint32_t k = (uint32_t)(old >> 32);
+        const uint32_t p1 = h1_of(k, sh);
+        pos = (pos == p1) ? h2_of(k, sh) : p1;
     }
+    const int s = atomicAdd(t.stash_n, 1);
+    if (s < kStash) t.stash[s] = cur;
+    else atomicExch(err, (int)kDevTableFull);
 }
 
-// Probe one element w (a lane's share of N+(v)) against the table of N+(u).
-// The first slot is read inline; collisions (load <= 1/4) take the loop.
-__device__ __forceinline__ bool probe_one(const uint32_t *key, int sh, uint32_t mask, uint32_t w, uint32_t &s) {
-    s = (w * 0x9E3779B1u) >> sh;
-    uint32_t k = key[s];
-    while (k != w && k != kEmpty) {
-        s = (s + 1) & mask;
-        k = key[s];
+// w in the table?  t receives its position in N+(u)
+__device__ __forceinline__ bool table_find(const Table &tb, int sh, int stash_n, uint32_t w, uint32_t &t) {
+    const unsigned long long a = tb.slot[h1_of(w, sh)];
+    const unsigned long long b = tb.slot[h2_of(w, sh)];
+    if ((uint32_t)(a >> 32) == w) { t = (uint32_t)a; return true; }
+    if ((uint32_t)(b >> 32) == w) { t = (uint32_t)b; return true; }
+    for (int k = 0; k < stash_n; ++k) {
+        const unsigned long long c = tb.stash[k];
+        if ((uint32_t)(c >> 32) == w) { t = (uint32_t)c; return true; }
     }
-    return k == w;
+    return false;
 }
 
 // Stream N+(v) = colp[ov, ov + dv) through the table of N+(u): two 32-element
 // slabs per iteration (two loads in flight per lane); hits go to the queue.
 template <Mode M>
-__device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key, const uint16_t *idx, int log_slots,
+__device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
                                            uint32_t u, uint32_t iuv, uint32_t ou, uint32_t v, uint32_t ov, int dv,
                                            HitQueue &q, int &qn, unsigned &live, unsigned long long &tris,
                                            Emitter &em) {
@@ -276,30 +343,44 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const uint32_t *key
     const uint32_t lt = lanemask_lt();
     const uint32_t *lst = a.colp + ov;
     const int sh = 32 - log_slots;
-    const uint32_t mask = (1u << log_slots) - 1u;
+    unsigned huv = 0;  // EdgeCount: triangles found on the arc u->v
     for (int j0 = 0; j0 < dv; j0 += 64) {
         const int ja = j0 + lane, jb = ja + 32;
-        uint32_t wa = 0, wb = 0, sa = 0, sb = 0;
+        uint32_t wa = kEmpty, wb = kEmpty, ta = 0, tb2 = 0;
         if (ja < dv) wa = __ldg(lst + ja);
         if (jb < dv) wb = __ldg(lst + jb);
-        const bool ha = ja < dv && probe_one(key, sh, mask, wa, sa);
-        const bool hb = jb < dv && probe_one(key, sh, mask, wb, sb);
+        // kEmpty is never a vertex, so out-of-range lanes miss
+        const bool ha = table_find(tb, sh, stash_n, wa, ta) && ja < dv;
+        const bool hb = table_find(tb, sh, stash_n, wb, tb2) && jb < dv;
         const unsigned ma = __ballot_sync(kFull, ha), mb = __ballot_sync(kFull, hb);
+        if constexpr (M == Mode::EdgeCount) {
+            // each hit closes a triangle through u->w and v->w; u->v is summed once
+            if (ha) { atomicAdd(a.tcnt + ou + ta, 1u); atomicAdd(a.tcnt + ov + (uint32_t)ja, 1u); }
+            if (hb) { atomicAdd(a.tcnt + ou + tb2, 1u); atomicAdd(a.tcnt + ov + (uint32_t)jb, 1u); }
+            huv += (unsigned)(__popc(ma) + __popc(mb));
+            continue;
+        }
         if (ma | mb) {
             int s0 = qn + __popc(ma & lt);
             if (ha) {
                 q.u[s0] = u; q.v[s0] = v; q.w[s0] = wa;
-                q.iuv[s0] = iuv; q.iuw[s0] = ou + idx[sa]; q.ivw[s0] = ov + (uint32_t)ja;
+                q.iuv[s0] = iuv; q.iuw[s0] = ou + ta; q.ivw[s0] = ov + (uint32_t)ja;
             }
             s0 = qn + __popc(ma) + __popc(mb & lt);
             if (hb) {
                 q.u[s0] = u; q.v[s0] = v; q.w[s0] = wb;
-                q.iuv[s0] = iuv; q.iuw[s0] = ou + idx[sb]; q.ivw[s0] = ov + (uint32_t)jb;
+                q.iuv[s0] = iuv; q.iuw[s0] = ou + tb2; q.ivw[s0] = ov + (uint32_t)jb;
             }
             qn += __popc(ma) + __popc(mb);
             if (lane == 0) tris += (unsigned)(__popc(ma) + __popc(mb));
             __syncwarp();
             while (qn >= 32) qn = drain32<M>(a, q, qn, live, em);
+        }
+    }
+    if constexpr (M == Mode::EdgeCount) {
+        if (lane == 0 && huv) {
+            atomicAdd(a.tcnt + iuv, huv);
+            tris += huv;
         }
     }
 }
@@ -327,10 +408,12 @@ __device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, un
 // per vertex with its own small table; warps claim 32 vertex ids at a time.
 // Probe and triangle totals are counted per list and per found triangle.
 template <Mode M>
-__global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
+__global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next;
     __shared__ long long s_h;
+    __shared__ int s_stash_n[kTW + 1];
+    __shared__ unsigned long long s_stash[kTW + 1][kStash];
     HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
     unsigned char *tbl = smem + sizeof(HitQueue) * kTW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -345,9 +428,8 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
     {
         const int cap = a.heavy_cap;  // table capacity: larger N+(u) is processed in chunks
         const int slots = 4 * cap;
-        uint32_t *key = reinterpret_cast<uint32_t *>(tbl);
-        uint16_t *idx = reinterpret_cast<uint16_t *>(key + slots);
-        uint32_t *vv = reinterpret_cast<uint32_t *>(idx + slots);  // v, off+(v), d+(v) of N+(u)
+        Table tb{reinterpret_cast<unsigned long long *>(tbl), s_stash[kTW], &s_stash_n[kTW]};
+        uint32_t *vv = reinterpret_cast<uint32_t *>(tb.slot + slots);  // v, off+(v), d+(v) of N+(u)
         uint32_t *vo = vv + cap;
         int *vd = reinterpret_cast<int *>(vo + cap);
         for (;;) {
@@ -362,13 +444,16 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
             for (int c0 = 0; c0 < d; c0 += cap) {
                 const int cn = min(cap, d - c0);
                 const int log_slots = ceil_log2(4 * cn) < 3 ? 3 : ceil_log2(4 * cn);
-                for (int s2 = threadIdx.x; s2 < (1 << log_slots); s2 += blockDim.x) key[s2] = kEmpty;
-                if (threadIdx.x == 0) s_next = 0;
+                for (int s2 = threadIdx.x; s2 < (1 << log_slots); s2 += blockDim.x) tb.slot[s2] = kSlotEmpty;
+                if (threadIdx.x == 0) {
+                    s_next = 0;
+                    *tb.stash_n = 0;
+                }
                 __syncthreads();
                 for (int k = threadIdx.x; k < cn; k += blockDim.x) {
                     const int i = c0 + k;
                     const uint32_t v = __ldg(a.colp + ou + i);
-                    const bool dead = M == Mode::EoReserve && a.considered[ou + i];
+                    const bool dead = M == Mode::EoReserve && a.considered != nullptr && a.considered[ou + i];
                     if (staged) {
                         const int64_t ov = __ldg(a.offp + v);
                         vv[i] = v;
@@ -376,9 +461,10 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
                         // a considered arc u->v closes no live triangle
                         vd[i] = dead ? 0 : (int)(__ldg(a.offp + v + 1) - ov);
                     }
-                    if (!dead) table_insert(key, idx, log_slots, v, k);
+                    if (!dead) table_insert(tb, log_slots, v, k, a.err);
                 }
                 __syncthreads();
+                const int stash_n = min(*tb.stash_n, kStash);
                 for (;;) {
                     int i = 0;
                     if (lane == 0) i = atomicAdd(&s_next, 1);
@@ -394,13 +480,13 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
                         v = __ldg(a.colp + ou + i);
                         const int64_t o64 = __ldg(a.offp + v);
                         ov = (uint32_t)o64;
-                        dv = (M == Mode::EoReserve && a.considered[ou + i]) ? 0
+                        dv = (M == Mode::EoReserve && a.considered != nullptr && a.considered[ou + i]) ? 0
                                                                             : (int)(__ldg(a.offp + v + 1) - o64);
                     }
                     // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
                     if (lane == 0 && c0 == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou + (uint32_t)c0, v, ov, dv, q, qn,
-                                  live, tris, em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou + (uint32_t)c0, v, ov, dv, q,
+                                  qn, live, tris, em);
                 }
                 __syncthreads();  // the table is rebuilt for the next chunk or vertex
             }
@@ -409,8 +495,7 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
 
     // ---- phase 2: light vertices
     {
-        uint32_t *key = reinterpret_cast<uint32_t *>(tbl) + warp * kLightSlots;
-        uint16_t *idx = reinterpret_cast<uint16_t *>(tbl + sizeof(uint32_t) * kLightSlots * kTW) + warp * kLightSlots;
+        Table tb{reinterpret_cast<unsigned long long *>(tbl) + warp * kLightSlots, s_stash[warp], &s_stash_n[warp]};
         for (;;) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(a.work + 1, 32ull);
@@ -432,17 +517,20 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
                 const uint32_t ou = __shfl_sync(kFull, oul, src);
                 const int d = __shfl_sync(kFull, dl, src);
                 const int log_slots = max(3, ceil_log2(4 * d));
-                for (int s2 = lane; s2 < (1 << log_slots); s2 += 32) key[s2] = kEmpty;
+                for (int s2 = lane; s2 < (1 << log_slots); s2 += 32) tb.slot[s2] = kSlotEmpty;
+                if (lane == 0) *tb.stash_n = 0;
                 __syncwarp();
                 // lane k holds N+(u)[k] and N+(u)[k + 32] with their list bounds
-                uint32_t n0 = 0, n1 = 0, o0 = 0, o1 = 0;
+                uint32_t n0 = kEmpty, n1 = kEmpty, o0 = 0, o1 = 0;
                 int d0 = 0, d1 = 0;
+                bool live0 = false, live1 = false;  // the arc u->w may close a live triangle
                 if (lane < d) {
                     n0 = __ldg(a.colp + ou + lane);
                     const int64_t b0 = __ldg(a.offp + n0);
                     o0 = (uint32_t)b0;
                     d0 = (int)(__ldg(a.offp + n0 + 1) - b0);
-                    if (M != Mode::EoReserve || !a.considered[ou + lane]) table_insert(key, idx, log_slots, n0, lane);
+                    live0 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane];
+                    if (live0) table_insert(tb, log_slots, n0, lane, a.err);
                     else d0 = 0;
                 }
                 if (lane + 32 < d) {
@@ -450,18 +538,20 @@ __global__ void __launch_bounds__(kTW * 32) tri_enum_kernel(TriArgs a) {
                     const int64_t b1 = __ldg(a.offp + n1);
                     o1 = (uint32_t)b1;
                     d1 = (int)(__ldg(a.offp + n1 + 1) - b1);
-                    if (M != Mode::EoReserve || !a.considered[ou + lane + 32])
-                        table_insert(key, idx, log_slots, n1, lane + 32);
+                    live1 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane + 32];
+                    if (live1) table_insert(tb, log_slots, n1, lane + 32, a.err);
                     else d1 = 0;
                 }
                 __syncwarp();
+                const int stash_n = min(*tb.stash_n, kStash);
                 for (int i = 0; i < d; ++i) {
                     const bool lo = i < 32;
                     const uint32_t v = __shfl_sync(kFull, lo ? n0 : n1, i & 31);
                     const uint32_t ov = __shfl_sync(kFull, lo ? o0 : o1, i & 31);
                     const int dv = __shfl_sync(kFull, lo ? d0 : d1, i & 31);
                     if (lane == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, key, idx, log_slots, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris, em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris,
+                                  em);
                 }
                 __syncwarp();
             }
@@ -538,7 +628,10 @@ __device__ __forceinline__ int64_t arc_between(const int64_t *off, const int64_t
     return (i < end && __ldg(colp + i) == key) ? i : -1;
 }
 
-template <bool MAXW>
+// Which edge an accepted triangle deletes.
+enum Choice { kChoiceRandom = 0, kChoiceMaxw = 1, kChoiceMinCount = 2 };
+
+template <int CH>
 __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uint8_t *considered) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -563,7 +656,9 @@ __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uin
             if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
             if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
             int64_t chosen;
-            if constexpr (MAXW) {
+            if constexpr (CH == kChoiceMinCount) {
+                chosen = mincount_arc(a.tcnt, e01, e02, e12);
+            } else if constexpr (CH == kChoiceMaxw) {
                 const float w01 = __ldg(a.wp + e01), w02 = __ldg(a.wp + e02), w12 = __ldg(a.wp + e12);
                 chosen = e01;
                 float bw = w01;
@@ -583,10 +678,10 @@ __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uin
 // Edge-once rounds over the list of live selected triangles.
 // Accept: a triangle holding the reservations of all three of its edges is
 // accepted; accepted triangles are edge-disjoint, so their stores never race.
-template <bool MAXW>
+template <int CH>
 __global__ void eo_list_accept_kernel(const TriRec *__restrict__ L, int64_t len,
                                       const unsigned long long *__restrict__ resv, uint8_t *considered,
-                                      uint8_t *del, const float *__restrict__ wp) {
+                                      uint8_t *del, const float *__restrict__ wp, const uint32_t *__restrict__ tcnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         const TriRec r = L[i];
@@ -597,7 +692,9 @@ __global__ void eo_list_accept_kernel(const TriRec *__restrict__ L, int64_t len,
         considered[r.e02] = 1;
         considered[r.e12] = 1;
         uint32_t chosen;
-        if constexpr (MAXW) {
+        if constexpr (CH == kChoiceMinCount) {
+            chosen = mincount_arc(tcnt, r.e01, r.e02, r.e12);
+        } else if constexpr (CH == kChoiceMaxw) {
             const float w01 = __ldg(wp + r.e01), w02 = __ldg(wp + r.e02), w12 = __ldg(wp + r.e12);
             chosen = r.e01;
             float bw = w01;
@@ -619,7 +716,8 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
                                                               TriRec *__restrict__ out,
                                                               unsigned long long *out_len,
                                                               unsigned long long *resv,
-                                                              const uint8_t *__restrict__ considered) {
+                                                              const uint8_t *__restrict__ considered,
+                                                              unsigned long long theta) {
     __shared__ int s_cnt[8];
     __shared__ unsigned long long s_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -632,10 +730,12 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
             r = L[i];
             if (r.x0 != kSentinel && !(considered[r.e01] | considered[r.e02] | considered[r.e12])) {
                 keep = true;
-                const unsigned long long hi = (unsigned long long)r.r2 << 32;
-                atomicMin(resv + r.e01, hi | r.x2);
-                atomicMin(resv + r.e02, hi | r.x1);
-                atomicMin(resv + r.e12, hi | r.x0);
+                if ((unsigned long long)r.r2 < theta) {
+                    const unsigned long long hi = (unsigned long long)r.r2 << 32;
+                    atomicMin(resv + r.e01, hi | r.x2);
+                    atomicMin(resv + r.e02, hi | r.x1);
+                    atomicMin(resv + r.e12, hi | r.x0);
+                }
             }
         }
         const unsigned bm = __ballot_sync(kFull, keep);
@@ -729,12 +829,12 @@ static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
     // shared memory: hit queues + the larger of the heavy table (4 slots per
     // entry, load <= 1/4, with the list bounds of N+(u)) and the light tables
     const size_t queue_bytes = sizeof(HitQueue) * kTW;
-    const size_t light_bytes = (size_t)kTW * kLightSlots * 6;
+    const size_t light_bytes = (size_t)kTW * kLightSlots * 8;
     int cap = 8;
     while (cap < pl->max_deg && cap < kHeavyCap) cap *= 2;
     pl->heavy_cap = cap;
     pl->log_slots = ceil_log2_host(4 * cap);
-    const size_t heavy_bytes = (size_t)cap * (4 * 6 + 12);
+    const size_t heavy_bytes = (size_t)cap * (4 * 8 + 12);
     pl->smem = queue_bytes + std::max(light_bytes, heavy_bytes);
     return SG_OK;
 }
@@ -786,6 +886,7 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
     a.wp = o.w;
     a.n = o.n;
     a.ctr = c->d_ctr;
+    a.err = c->d_err;
     return a;
 }
 
@@ -796,7 +897,7 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
 // edge pass and the next round enumerates again.
 static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
     const size_t m = (size_t)std::max<int64_t>(o.m, 1);
-    const bool maxw = (k == SG_TR_EO_MAXW);
+    const int choice = k == SG_TR_EO_MAXW ? kChoiceMaxw : (k == SG_TR_EO_MINCOUNT ? kChoiceMinCount : kChoiceRandom);
     uint8_t *considered = nullptr;
     unsigned long long *resv = nullptr, *lctr = nullptr;
     int *lovf = nullptr;
@@ -815,9 +916,16 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     const int64_t acc_blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
     if (st == SG_OK && cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "memset");
-    for (int round = 0; st == SG_OK; ++round) {
+    // Prefix schedule: round r lets only triangles with r2 < theta bid, theta
+    // doubling from 2^27.  A bidder that holds all three reservations is the
+    // smallest live triangle on each of its edges (every non-bidder has a
+    // larger key), so the accepted set equals the unrestricted greedy scan's,
+    // while most triangles die before they ever bid.
+    unsigned long long theta = 1ull << 27;
+    for (int round = 0; st == SG_OK; ++round, theta = std::min(theta * 2, 1ull << 32)) {
         if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
-        // ---- reserve: every live selected triangle bids for its three edges
+        a.eo_theta = theta;
+        // ---- reserve: every live selected triangle of the prefix bids for its three edges
         unsigned long long live = 0;
         if (LA == nullptr) {
             // enumeration round, writing the list when it fits
@@ -839,7 +947,10 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                 }
             }
             SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+            // nothing is considered before the first acceptance: skip the flag reads
+            a.considered = round == 0 ? nullptr : considered;
             st = launch_enum<Mode::EoReserve>(c, a, pl);
+            a.considered = considered;
             if (st != SG_OK) break;
             st = read_ctr(c, kCtrLive, 1, &live);
             if (st != SG_OK || live == 0) break;
@@ -869,7 +980,8 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
             if (blocks > 0) {
                 SG_LAUNCH(c, "tri_eo_list_reserve");
-                eo_list_reserve_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, LB, lctr, resv, considered);
+                eo_list_reserve_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, LB, lctr, resv, considered,
+                                                                                theta);
             }
             SG_CUDA(cudaGetLastError());
             SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
@@ -882,24 +994,34 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         ++c->eo_rounds;
         // ---- accept: triangles holding all three reservations.  A long list is
         // cheaper to judge from the edges' side (one pass over m reservations).
-        const bool small_list = LA != nullptr && (double)lenA * sizeof(TriRec) <= 8.0 * (double)m;
+        // judging from the edge side costs a binary search per reserved arc;
+        // once the list holds at most two triangles per edge, read the list
+        const bool small_list = LA != nullptr && (double)lenA <= 2.0 * (double)m;
         if (small_list) {
             const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
             SG_LAUNCH(c, "tri_eo_list_accept");
-            if (maxw)
-                eo_list_accept_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered, a.del, a.wp);
+            if (choice == kChoiceMaxw)
+                eo_list_accept_kernel<kChoiceMaxw><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered,
+                                                                                             a.del, a.wp, a.tcnt);
+            else if (choice == kChoiceMinCount)
+                eo_list_accept_kernel<kChoiceMinCount><<<(unsigned)blocks, 256, 0, c->stream>>>(
+                    LA, lenA, resv, considered, a.del, a.wp, a.tcnt);
             else
-                eo_list_accept_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered, a.del, a.wp);
+                eo_list_accept_kernel<kChoiceRandom><<<(unsigned)blocks, 256, 0, c->stream>>>(
+                    LA, lenA, resv, considered, a.del, a.wp, a.tcnt);
         } else {
             SG_LAUNCH(c, "tri_eo_accept");
-            if (maxw)
-                eo_accept_kernel<true><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            if (choice == kChoiceMaxw)
+                eo_accept_kernel<kChoiceMaxw><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            else if (choice == kChoiceMinCount)
+                eo_accept_kernel<kChoiceMinCount><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
             else
-                eo_accept_kernel<false><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+                eo_accept_kernel<kChoiceRandom><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
         }
         SG_CUDA(cudaGetLastError());
-        // ---- reset the reservations for the next round
-        if (small_list) {
+        // ---- reset the reservations for the next round: three scattered
+        // writes per listed triangle beat clearing all m words only for short lists
+        if (LA != nullptr && (double)lenA * 96.0 <= 8.0 * (double)m) {
             const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
             SG_LAUNCH(c, "tri_eo_list_reset");
             eo_list_reset_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv);
@@ -924,11 +1046,26 @@ sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double
     a.k1 = (uint32_t)(seed >> 32);
     a.tp = prob_threshold(p);
     a.del = del;
-    if (st == SG_OK && (k == SG_TR_RANDOM || k == SG_TR_MAXW)) {
-        st = (k == SG_TR_RANDOM) ? launch_enum<Mode::UnionRandom>(c, a, pl) : launch_enum<Mode::UnionMaxw>(c, a, pl);
-    } else if (st == SG_OK) {
-        st = eo_rounds(c, g, o, k, pl, a);
+    uint32_t *tcnt = nullptr;
+    if (st == SG_OK && (k == SG_TR_MINCOUNT || k == SG_TR_EO_MINCOUNT)) {
+        // the min-count choice needs the triangle count of every edge of G first
+        const size_t bytes = sizeof(uint32_t) * (size_t)std::max<int64_t>(o.m, 1);
+        st = dalloc(c, (void **)&tcnt, bytes);
+        if (st == SG_OK && cudaMemsetAsync(tcnt, 0, bytes, c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync(tcnt)");
+        a.tcnt = tcnt;
+        if (st == SG_OK) st = launch_enum<Mode::EdgeCount>(c, a, pl);
     }
+    if (st == SG_OK) {
+        switch (k) {
+        case SG_TR_RANDOM: st = launch_enum<Mode::UnionRandom>(c, a, pl); break;
+        case SG_TR_MAXW: st = launch_enum<Mode::UnionMaxw>(c, a, pl); break;
+        case SG_TR_P2: st = launch_enum<Mode::UnionP2>(c, a, pl); break;
+        case SG_TR_MINCOUNT: st = launch_enum<Mode::UnionMinCount>(c, a, pl); break;
+        default: st = eo_rounds(c, g, o, k, pl, a); break;
+        }
+    }
+    dfree(c, tcnt);
     free_plan(c, &pl);
     return st;
 }

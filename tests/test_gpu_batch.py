@@ -8,7 +8,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-EDGE_TR = ["uniform", "spectral_logn", "spectral_avgdeg", "tr_random"]
+EDGE_TR = ["uniform", "tr_random", "spectral_logn", "tr_p2", "spectral_avgdeg"]
 
 
 @pytest.fixture(scope="module")
@@ -62,7 +62,7 @@ def _check_batch(sg, ctx, graphs, kernels, ps, seeds, want_weights=False):
 def test_batch_matches_solo_unweighted(sg, ctx):
     graphs = _graphs(40, False, 100)
     n = len(graphs)
-    kernels = [EDGE_TR[i % 4] for i in range(n)]
+    kernels = [EDGE_TR[i % len(EDGE_TR)] for i in range(n)]
     ps = [(0.2, 0.5, 0.8)[i % 3] for i in range(n)]
     seeds = [i + 1 for i in range(n)]
     B, G = _check_batch(sg, ctx, graphs, kernels, ps, seeds, want_weights=True)
@@ -92,7 +92,8 @@ def test_batch_matches_solo_weighted_maxw(sg, ctx):
 def test_batch_rejects_edge_once(sg, ctx):
     G = [sg.Graph.from_csr(ctx, gg.complete(5))]
     B = sg.Batch(ctx, G)
-    with pytest.raises(sg.SgError) as e:
-        B.compress(["tr_eo"], [0.5], [1])
-    assert e.value.status == sg.SG_ERR_UNSUPPORTED
+    for kern in ("tr_eo", "tr_eo_maxw", "tr_eo_mincount", "tr_mincount"):
+        with pytest.raises(sg.SgError) as e:
+            B.compress([kern], [0.5], [1])
+        assert e.value.status == sg.SG_ERR_UNSUPPORTED
     B.free()

@@ -60,22 +60,23 @@ def _has_edge(off, col, x, y):
     return k < hi - lo and col[lo + k] == y
 
 
-def test_tr_random_sampled_edges(sg, big):
+@pytest.mark.parametrize("kern", ["tr_random", "tr_p2", "tr_mincount"])
+def test_tr_union_sampled_edges(sg, big, kern):
     g, G = big
-    H = sg.compress(G, "tr_random", 0.5, 1)
+    H = sg.compress(G, kern, 0.5, 1)
     off, col, _ = H.download()
     rows, cols = _edge_sample(g, 3000, 5)
     for x, y in zip(rows, cols):
-        deleted = oracle.tr_union_edge_deleted(g, "tr_random", 0.5, 1, int(x), int(y))
+        deleted = oracle.tr_union_edge_deleted(g, kern, 0.5, 1, int(x), int(y))
         assert _has_edge(off, col, int(x), int(y)) == (not deleted)
     assert 0 < col.size < g.nnz
     H.free()
 
 
-@pytest.mark.parametrize("p", [0.2, 0.5, 0.8])
-def test_tr_eo_invariants_full_size(sg, big, p):
+@pytest.mark.parametrize("kern,p", [("tr_eo", 0.2), ("tr_eo", 0.5), ("tr_eo", 0.8), ("tr_eo_mincount", 0.5)])
+def test_tr_eo_invariants_full_size(sg, big, kern, p):
     g, G = big
-    H = sg.compress(G, "tr_eo", p, 1)
+    H = sg.compress(G, kern, p, 1)
     off, col, _ = H.download()
     goff, gcol, _ = g.numpy()
     dg, dh = np.diff(goff), np.diff(off)

@@ -13,7 +13,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = ["uniform", "spectral_logn", "spectral_avgdeg", "tr_random", "tr_eo"]
+KERNELS = ["uniform", "spectral_logn", "spectral_avgdeg", "tr_random", "tr_eo", "tr_p2", "tr_mincount",
+           "tr_eo_mincount"]
 WKERNELS = ["tr_maxw", "tr_eo_maxw"]
 
 
@@ -91,7 +92,7 @@ def test_spectral_weights_bit_exact(sg, ctx, rmat14, kern):
     _same(sg, ctx, rmat14, kern, 0.5, 3, want_weights=True)
 
 
-@pytest.mark.parametrize("kern", WKERNELS + ["uniform", "tr_random", "tr_eo"])
+@pytest.mark.parametrize("kern", WKERNELS + ["uniform", "tr_random", "tr_eo", "tr_p2", "tr_mincount", "tr_eo_mincount"])
 def test_weighted_bit_exact(sg, ctx, kern):
     g = gg.attach_weights(gg.rmat(12, 16, seed=4), seed=4)
     _same(sg, ctx, g, kern, 0.6, 5)
@@ -132,7 +133,7 @@ def test_triangle_count(sg, ctx, rmat14):
 
 
 @pytest.mark.parametrize("cap", [-1, 4096, 60000, 0])
-@pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw"])
+@pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw", "tr_eo_mincount"])
 def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
     # -1: enumerate every round; small caps overflow and fall back to the edge
     # pass, then retry the list in a later round; 0: automatic
@@ -249,7 +250,8 @@ def test_errors(sg, ctx):
     G.free()
 
 
-@pytest.mark.parametrize("kern,p", [("tr_random", 0.3), ("tr_eo", 0.5), ("tr_eo", 1.0)])
+@pytest.mark.parametrize("kern,p", [("tr_random", 0.3), ("tr_eo", 0.5), ("tr_eo", 1.0), ("tr_p2", 0.4),
+                                    ("tr_mincount", 0.6), ("tr_eo_mincount", 1.0)])
 def test_chunked_heavy_tables(sg, ctx, kern, p):
     # K600 has out-degrees up to 599: the largest vertices' N+(u) exceeds one
     # shared-memory table and is processed in chunks
@@ -257,4 +259,23 @@ def test_chunked_heavy_tables(sg, ctx, kern, p):
     _same(sg, ctx, g, kern, p, 12)
     G = sg.Graph.from_csr(ctx, g)
     assert sg.triangle_count(G) == 600 * 599 * 598 // 6
+    G.free()
+
+
+def test_edge_triangle_counts_through_mincount(sg, ctx):
+    # at p = 1 every triangle is selected, so min-count TR deletes exactly the
+    # per-triangle minima of the counts -- a wrong count anywhere shows up
+    g = gg.rmat(13, 32, seed=21)
+    _same(sg, ctx, g, "tr_mincount", 1.0, 2)
+    _same(sg, ctx, g, "tr_eo_mincount", 1.0, 2)
+
+
+def test_p2_at_p1_on_disjoint_triangles(sg, ctx):
+    k = 3000
+    g = gg.disjoint_union(*[gg.complete(3)] * k)
+    G = sg.Graph.from_csr(ctx, g)
+    H = sg.compress(G, "tr_p2", 1.0, 5)
+    off, col, _ = H.download()
+    assert col.size == 2 * k
+    H.free()
     G.free()
