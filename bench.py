@@ -104,13 +104,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def byte_model(n, m, A_out, probes_total, launches, kernel):
-    """Algorithmic bytes of one launch of a named kernel (see DESIGN.md)."""
+def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0):
+    """Algorithmic bytes of one launch of a named kernel."""
     A = 2 * m
     if kernel == "tri_enum":
-        # off+ (8 B/vertex), N+(u) lists (4 B/arc), off+ pair of every v (8 B/arc),
-        # one 4-byte read per probe (W = sum over u->v of d+(v))
-        return (8 * (n + 1) + 4 * m + 8 * m) + 4.0 * probes_total / max(launches, 1)
+        # off+ and the in-list length of every vertex (8 + 4 B), N+(x) staged in
+        # the tables (4 B/arc), the off+ pair of every streamed list (8 B/arc),
+        # the in-list records (8 B per arc streamed from the head's side) and one
+        # 4-byte read per probe (W = sum over arcs of min(d+(u), d+(v)))
+        return (8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs) + 4.0 * probes_total / max(launches, 1)
+    if kernel == "tri_inarcs":
+        # off+ and N+(u) of every vertex, the off+ pair and symmetric offsets of
+        # every head, one 8-byte record written per gathered arc
+        return 8 * (n + 1) + 4 * m + 8 * m + 16 * head_arcs + 8 * head_arcs
     if kernel == "compact_orient":
         return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * m + A / 8
     if kernel == "compact_trmask":
@@ -177,8 +183,8 @@ def run_ours(args, rank, world):
     ms = ev0.elapsed_time(ev1) / args.steps
     st = ctx.stats()
     kt = {}
-    for name in ("tri_enum", "tri_eo_list_reserve", "tri_eo_list_accept", "tri_eo_accept", "tri_classify",
-                 "compact_orient", "compact_trmask", "row_maps"):
+    for name in ("tri_enum", "tri_inarcs", "tri_eo_list_reserve", "tri_eo_list_accept", "tri_eo_accept",
+                 "tri_classify", "compact_orient", "compact_trmask", "row_maps"):
         kt[name] = ctx.kernel_time(name)
     enum_ms = kt["tri_enum"][0]
     enum_launches = max(kt["tri_enum"][1], 1)
@@ -189,7 +195,8 @@ def run_ours(args, rank, world):
 
     hbm, peak_src = peaks()
     cand = {
-        "tri_enum": (enum_ms, enum_launches, byte_model(n, m, A_out, st["probes"], enum_launches, "tri_enum")),
+        "tri_enum": (enum_ms, enum_launches, byte_model(n, m, A_out, st["probes"], enum_launches, "tri_enum",
+                                                        work["head_arcs"])),
         "compact_orient": (kt["compact_orient"][0], kt["compact_orient"][1],
                            byte_model(n, m, A_out, 0, 1, "compact_orient")),
         "compact_trmask": (kt["compact_trmask"][0], kt["compact_trmask"][1],
@@ -282,6 +289,7 @@ def run_ours(args, rank, world):
         "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "n": n, "m": m,
                    "eo_list_capacity": args.eo_list_cap,
                    "arcs": 2 * m, "triangles": work["triangles"], "probes_per_pass": work["probes"],
+                   "head_arcs": work["head_arcs"],
                    "max_out_degree": work["max_out_degree"], "kept_arcs": int(A_out),
                    "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},

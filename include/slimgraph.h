@@ -231,11 +231,15 @@ sg_status sg_cc_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out, uint32
 /* Number of triangles of G (each counted once), with the degree-ordered
  * enumeration used by the TR kernels. */
 sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out);
-/* Work model of the degree-ordered enumeration of G: m, the probe count
- * W = sum over oriented arcs u->v of d+(v), the maximum out-degree and the
- * triangle count.  Used to turn kernel times into algorithmic bytes. */
+/* Work model of the degree-ordered enumeration of G (runs one counting pass):
+ * m; the probe count W = sum over oriented arcs u->v of the shorter of
+ * d+(u), d+(v) (each arc streams its shorter list through a table of the
+ * longer one, ties to d+(v)); the maximum out-degree; the triangle count; and
+ * the number of arcs streamed from the head's side (those with
+ * d+(u) < d+(v), gathered into per-vertex in-lists of 8 bytes each).  Used
+ * to turn kernel times into algorithmic bytes.  Any out pointer may be NULL. */
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out,
-                     int64_t *max_out_degree, int64_t *triangles_out);
+                     int64_t *max_out_degree, int64_t *triangles_out, int64_t *head_arcs_out);
 
 /* ------------------------------------------------- no-allocation variant */
 

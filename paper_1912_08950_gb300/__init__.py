@@ -82,7 +82,7 @@ _SIGS = {
     "sg_batch_info": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                       C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                   C.POINTER(C.c_int64)],
+                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -309,9 +309,10 @@ def triangle_count(g: Graph) -> int:
 
 
 def tr_work(g: Graph) -> dict:
-    m, w, md, t = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
-    _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t)))
-    return {"m": m.value, "probes": w.value, "max_out_degree": md.value, "triangles": t.value}
+    m, w, md, t, ha = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t), C.byref(ha)))
+    return {"m": m.value, "probes": w.value, "max_out_degree": md.value, "triangles": t.value,
+            "head_arcs": ha.value}
 
 
 class Batch:

@@ -119,7 +119,7 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
         BatchTri bt = b->bt;
         bt.light_max = t.light_max;
         bt.grid_per_sm = t.enum_per_sm;
-        st = batch_tr_mark(c, b->o, dev, bt, b->del);
+        st = batch_tr_mark(c, &b->u, b->o, dev, bt, b->del);
         if (st != SG_OK) return st;
         st = batch_final(c, &b->u, b->rm, b->o, dev, b->del, b->off_c, b->out_col, b->u.w, b->out_w,
                          b->st_final, t.compact_per_sm);
@@ -359,7 +359,7 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
         }
         if (st == SG_OK)
             st = batch_orient(c, &u, b->rm, BatchDev{b->d_params, b->vgid}, false, &b->o, b->st_orient, 0);
-        if (st == SG_OK) st = batch_tr_prepare(c, b->o, &b->bt);
+        if (st == SG_OK) st = batch_tr_prepare(c, &u, b->o, &b->bt);
         if (st == SG_OK) st = check_device_error(c);
     }
     if (st != SG_OK) {

@@ -160,7 +160,7 @@ sg_status sg_ctx_create(int device, void *cuda_stream, sg_ctx **out) {
     }
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(unsigned long long) * kCtrCount);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_pinned, 256);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_pinned, 4096);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(unsigned long long) * kCtrCount);
     if (e == cudaSuccess) {
@@ -489,22 +489,23 @@ sg_status sg_divergence(sg_ctx *ctx, const sg_graph *g, const sg_graph *h, float
 }
 
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out, int64_t *max_out_degree,
-                     int64_t *triangles_out) {
+                     int64_t *triangles_out, int64_t *head_arcs_out) {
     if (!ctx || !g) return fail(SG_ERR_INVALID_ARG, "NULL argument");
     Ctx *c = C_(ctx);
     sg_status st = set_device(c);
     if (st != SG_OK) return st;
     RowMaps rm;
     Oriented o;
-    int64_t t = 0, w = 0, md = 0;
+    int64_t t = 0, w = 0, md = 0, ha = 0;
     st = build_row_maps(c, G_(g), &rm);
     if (st == SG_OK) st = orient(c, G_(g), rm, false, &o);
-    if (st == SG_OK) st = tr_count(c, G_(g), o, &t, &w, &md);
+    if (st == SG_OK) st = tr_count(c, G_(g), o, &t, &w, &md, &ha);
     if (st == SG_OK) st = check_device_error(c);
     if (m_out) *m_out = g->nnz / 2;
     if (probes_out) *probes_out = w;
     if (max_out_degree) *max_out_degree = md;
     if (triangles_out) *triangles_out = t;
+    if (head_arcs_out) *head_arcs_out = ha;
     free_oriented(c, &o);
     free_row_maps(c, &rm);
     return st;
@@ -512,7 +513,7 @@ sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *pr
 
 sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out) {
     if (!count_out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
-    return sg_tr_work(ctx, g, nullptr, nullptr, nullptr, count_out);
+    return sg_tr_work(ctx, g, nullptr, nullptr, nullptr, count_out, nullptr);
 }
 
 }  // extern "C"

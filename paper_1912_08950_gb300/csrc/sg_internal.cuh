@@ -51,7 +51,7 @@ struct Ctx {
 };
 
 enum CtrIdx { kCtrProbes = 0, kCtrTriangles = 1, kCtrLive = 2, kCtrHeavy = 3, kCtrMaxDeg = 4, kCtrAux = 5,
-              kCtrCount = 8 };
+              kCtrInArcs = 7, kCtrCount = 8 };  // kCtrAux holds two words
 
 struct Graph {
     Ctx *ctx = nullptr;
@@ -205,19 +205,23 @@ sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented 
 // triangles (sg_triangles.cu)
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed,
                   uint8_t *del);
-sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg);
+sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg,
+                   int64_t *in_arcs);
 // batched union TR, with no host synchronisation (capturable in a CUDA graph)
 struct BatchTri {
     uint32_t *heavy = nullptr;
     unsigned long long *buckets = nullptr;  // counts, fills, total
+    uint32_t *din = nullptr;                // in-arcs streamed from the head's side
+    uint2 *inl = nullptr;
     int log_slots = 3;
     size_t smem = 0;
     int max_deg = 1;      // largest out-degree (sizes the heavy vertex arrays)
     int light_max = 64;
     int grid_per_sm = 0;  // 0: occupancy limit
 };
-sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt);
-sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const BatchTri &bt, uint8_t *del);
+sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *bt);
+sg_status batch_tr_mark(Ctx *c, const Graph *u, const Oriented &o, const BatchDev &b, const BatchTri &bt,
+                        uint8_t *del);
 void batch_tr_free(Ctx *c, BatchTri *bt);
 
 // analytics (sg_analytics.cu)

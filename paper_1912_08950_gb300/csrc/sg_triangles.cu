@@ -6,11 +6,16 @@
 // Enumeration.  Every triangle {u, v, w} with u < v < w in the degree order
 // (d, id) is found exactly once, at the oriented arc u->v, as w in
 // N+(u) ∩ N+(v) (the forward algorithm behind the O(m^{3/2}) bound the paper
-// quotes).  For each u the set N+(u) is staged in a shared-memory hash table
-// (linear probing, load <= 1/4) and the warp streams every list N+(v),
-// v in N+(u), through it with coalesced 128-byte reads: one probe per element
-// of N+(v), W = sum_{u->v} d+(v) probes in all.  Vertices with d+(u) <= 64
-// get one warp each; larger ones get a whole CTA whose warps split N+(u).
+// quotes).  The intersection streams the shorter of the two lists through a
+// shared-memory hash table of the longer one: every vertex x stages N+(x) in
+// a table once and streams (a) N+(v) for its out-arcs x->v with
+// d+(v) <= d+(x) and (b) N+(u) for its in-arcs u->x with d+(u) < d+(x); the
+// in-arcs of kind (b) are gathered per vertex by one scatter pass.  Each arc
+// is handled once, at the end with the longer list, so the probes number
+// sum over arcs of min(d+(u), d+(v)) -- under half of the plain forward
+// algorithm's sum of d+(v) on power-law graphs.  Vertices with a short N+(x)
+// and few in-arcs get one warp each; the others get a whole CTA whose warps
+// split the arcs.
 //
 // Decisions.  A hit (a triangle) is pushed to a per-warp queue; whenever 32
 // hits are queued the warp decides all of them at once with full lanes:
@@ -36,10 +41,12 @@ namespace sg {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kLightMax = 64;     // largest out-degree processed by one warp
+constexpr int kLightItems = 256;  // ... with at most this many lists to stream
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
 constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
 constexpr int kQ = 96;            // per-warp hit queue entries (31 left over + 2 slabs of hits)
+constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
 
 // Count: totals only.  EdgeCount: adds every triangle to the counters of its
 // three edges.  Union*: the union-semantics TR kernels.  EoReserve: one
@@ -49,6 +56,9 @@ enum class Mode { Count, EdgeCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCou
 struct TriArgs {
     const int64_t *offp;
     const uint32_t *colp;
+    const int64_t *offs;          // symmetric offsets: in-arcs of x live at inl[offs(x) - offp(x) ...]
+    const uint32_t *din;          // in-arcs u->x with d+(u) < d+(x), per x
+    const uint2 *inl;             // (u, arc u->x) of those in-arcs
     const float *wp;
     int64_t n;
     uint32_t k0, k1;
@@ -64,16 +74,19 @@ struct TriArgs {
     int heavy_log_slots;
     int heavy_cap;               // entries of the phase-1 table; larger N+(u) go in chunks
     int light_max;               // out-degrees up to this go to the warp-per-vertex phase
+    int light_items;             // ... when they also have at most this many arcs to stream
     int *err;                    // device error word (a cuckoo stash overflow)
     unsigned long long *work;    // [0] next heavy vertex, [1] next light vertex block
     const unsigned long long *n_heavy_dev;  // if set, the heavy count is read on the device
     // batched union: per-graph parameters and the graph of every vertex
     const BatchParam *bparams;
     const uint32_t *vgid;
-    // edge-once: optional list of the live selected triangles
+    // edge-once: optional list of the live selected triangles, split into
+    // buckets by the round in which each first bids
     struct TriRec *list;
-    unsigned long long *list_ctr;  // slots handed out (chunks of kChunk)
-    int64_t list_cap;
+    unsigned long long *list_ctr;  // [kEoBuckets] slots handed out per bucket
+    unsigned long long list_base[kEoBuckets], list_cap[kEoBuckets];
+    int eo_round;                  // this enumeration's round: earlier buckets fold into it
     int *list_overflow;
 };
 
@@ -85,40 +98,64 @@ struct __align__(16) TriRec {
     uint32_t r2, e01, e02, e12;
 };
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;
-constexpr int kChunk = 1024;  // list slots a warp claims at a time
 
-// Per-warp list writer: claims chunks of kChunk slots, fills them in order and
-// seals the unused tail of a chunk with sentinels.
+// Bucket b of the list holds the triangles whose r2 lies in
+// [2^(26+b), 2^(27+b)) (bucket 0: r2 < 2^27), i.e. those that first bid in
+// edge-once round b of the doubling prefix schedule.
+__device__ __forceinline__ int eo_bucket(uint32_t r2) { return r2 < (1u << 27) ? 0 : (31 - __clz((int)r2)) - 26; }
+// list slots a warp claims at a time, in proportion to the bucket's share
+__host__ __device__ constexpr int eo_chunk(int b) { return b <= 1 ? 64 : (32 << b); }
+
+// Per-warp list writer: per bucket it claims chunks of slots, fills them in
+// order and seals the unused tail of a chunk with sentinels.  The cursors live
+// in shared memory (cur, end per bucket).
 struct Emitter {
-    unsigned long long cur = 0, end = 0;
+    unsigned long long *st = nullptr;  // [2 * kEoBuckets]: cur[b], end[b]
     bool dead = false;
 };
 
-__device__ __forceinline__ void emit_seal(const TriArgs &a, Emitter &em) {
+__device__ __forceinline__ void emit_seal(const TriArgs &a, Emitter &em, int b) {
     const int lane = threadIdx.x & 31;
-    for (unsigned long long i = em.cur + lane; i < em.end; i += 32) a.list[i].x0 = kSentinel;
-    em.cur = em.end;
+    const unsigned long long cur = em.st[b], end = em.st[kEoBuckets + b];
+    for (unsigned long long i = cur + lane; i < end; i += 32) a.list[i].x0 = kSentinel;
+    __syncwarp();
+    if (lane == 0) em.st[b] = end;
+    __syncwarp();
 }
 
 __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool want, const TriRec &rec) {
-    const unsigned bm = __ballot_sync(kFull, want);
-    if (!bm || em.dead) return;
-    const int cnt = __popc(bm);
-    if (em.end - em.cur < (unsigned long long)cnt) {
-        emit_seal(a, em);
-        unsigned long long base = 0;
-        if ((threadIdx.x & 31) == 0) base = atomicAdd(a.list_ctr, (unsigned long long)kChunk);
-        base = __shfl_sync(kFull, base, 0);
-        if (base + kChunk > (unsigned long long)a.list_cap) {
-            if ((threadIdx.x & 31) == 0) atomicExch(a.list_overflow, 1);
-            em.dead = true;
-            return;
+    if (em.dead) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int mb = want ? max(eo_bucket(rec.r2), min(a.eo_round, kEoBuckets - 1)) : -1;
+    unsigned pend = __ballot_sync(kFull, want);
+    while (pend) {
+        const int b = __shfl_sync(kFull, mb, __ffs(pend) - 1);
+        const unsigned bm = __ballot_sync(kFull, mb == b);
+        pend &= ~bm;
+        const int cnt = __popc(bm);
+        if (em.st[kEoBuckets + b] - em.st[b] < (unsigned long long)cnt) {
+            emit_seal(a, em, b);
+            const unsigned long long chunk = (unsigned long long)eo_chunk(b);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.list_ctr + b, chunk);
+            base = __shfl_sync(kFull, base, 0);
+            if (base + chunk > a.list_cap[b]) {
+                if (lane == 0) atomicExch(a.list_overflow, 1);
+                em.dead = true;
+                return;
+            }
+            if (lane == 0) {
+                em.st[b] = a.list_base[b] + base;
+                em.st[kEoBuckets + b] = a.list_base[b] + base + chunk;
+            }
+            __syncwarp();
         }
-        em.cur = base;
-        em.end = base + kChunk;
+        const unsigned long long cur = em.st[b];
+        if (mb == b) a.list[cur + __popc(bm & lanemask_lt())] = rec;
+        __syncwarp();
+        if (lane == 0) em.st[b] = cur + cnt;
+        __syncwarp();
     }
-    if (want) a.list[em.cur + __popc(bm & lanemask_lt())] = rec;
-    em.cur += cnt;
 }
 
 // Oriented arcs are addressed with 32-bit indices (E+ holds fewer than 2^32 arcs).
@@ -333,7 +370,8 @@ __device__ __forceinline__ bool table_find(const Table &tb, int sh, int stash_n,
 }
 
 // Stream N+(v) = colp[ov, ov + dv) through the table of N+(u): two 32-element
-// slabs per iteration (two loads in flight per lane); hits go to the queue.
+// slabs per iteration, the next two loaded while these are probed (up to four
+// loads in flight per lane); hits go to the queue.
 template <Mode M>
 __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
                                            uint32_t u, uint32_t iuv, uint32_t ou, uint32_t v, uint32_t ov, int dv,
@@ -344,11 +382,18 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
     const uint32_t *lst = a.colp + ov;
     const int sh = 32 - log_slots;
     unsigned huv = 0;  // EdgeCount: triangles found on the arc u->v
+    uint32_t na = kEmpty, nb = kEmpty;
+    if (lane < dv) na = __ldg(lst + lane);
+    if (lane + 32 < dv) nb = __ldg(lst + lane + 32);
     for (int j0 = 0; j0 < dv; j0 += 64) {
         const int ja = j0 + lane, jb = ja + 32;
-        uint32_t wa = kEmpty, wb = kEmpty, ta = 0, tb2 = 0;
-        if (ja < dv) wa = __ldg(lst + ja);
-        if (jb < dv) wb = __ldg(lst + jb);
+        const uint32_t wa = na, wb = nb;
+        uint32_t ta = 0, tb2 = 0;
+        // the next two slabs are in flight while these are probed
+        na = kEmpty;
+        nb = kEmpty;
+        if (ja + 64 < dv) na = __ldg(lst + ja + 64);
+        if (jb + 64 < dv) nb = __ldg(lst + jb + 64);
         // kEmpty is never a vertex, so out-of-range lanes miss
         const bool ha = table_find(tb, sh, stash_n, wa, ta) && ja < dv;
         const bool hb = table_find(tb, sh, stash_n, wb, tb2) && jb < dv;
@@ -385,12 +430,43 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
     }
 }
 
+// Stream the in-lists [first, first + cnt) (cnt <= 32) of the table vertex u:
+// the lanes load the arcs' records and list bounds in parallel, then the warp
+// streams the lists one by one.
+template <Mode M>
+__device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
+                                                uint32_t u, uint32_t tbase, int64_t ib, int first, int cnt,
+                                                HitQueue &q, int &qn, unsigned &live, unsigned long long &probes,
+                                                unsigned long long &tris, Emitter &em, bool count_probes) {
+    const int lane = threadIdx.x & 31;
+    uint32_t sv = 0, so = 0, se = 0;
+    int sd = 0;
+    if (lane < cnt) {
+        const uint2 it = __ldg(a.inl + ib + first + lane);
+        sv = it.x;
+        se = it.y;
+        const int64_t b0 = __ldg(a.offp + sv);
+        so = (uint32_t)b0;
+        sd = (M == Mode::EoReserve && a.considered != nullptr && a.considered[se])
+                 ? 0 : (int)(__ldg(a.offp + sv + 1) - b0);
+    }
+    for (int i = 0; i < cnt; ++i) {
+        const uint32_t v = __shfl_sync(kFull, sv, i);
+        const uint32_t ov = __shfl_sync(kFull, so, i);
+        const uint32_t e = __shfl_sync(kFull, se, i);
+        const int dv = __shfl_sync(kFull, sd, i);
+        if (lane == 0 && count_probes) probes += (unsigned)dv;
+        probe_list<M>(a, tb, log_slots, stash_n, u, e, tbase, v, ov, dv, q, qn, live, tris, em);
+    }
+}
+
 template <Mode M>
 __device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, unsigned live,
                                        unsigned long long probes, unsigned long long tris, Emitter &em) {
     flush_hits<M>(a, q, qn, live, em);
     if constexpr (M == Mode::EoReserve) {
-        if (a.list != nullptr && !em.dead) emit_seal(a, em);
+        if (a.list != nullptr && !em.dead)
+            for (int b = 0; b < kEoBuckets; ++b) emit_seal(a, em, b);
     }
     const unsigned long long P = warp_sum(probes), T = warp_sum(tris);
     const unsigned L = warp_sum(live);
@@ -414,6 +490,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
     __shared__ long long s_h;
     __shared__ int s_stash_n[kTW + 1];
     __shared__ unsigned long long s_stash[kTW + 1][kStash];
+    __shared__ unsigned long long s_emit[M == Mode::EoReserve ? kTW : 1][2 * kEoBuckets];
     HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
     unsigned char *tbl = smem + sizeof(HitQueue) * kTW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -422,6 +499,11 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
     Emitter em;
+    if constexpr (M == Mode::EoReserve) {
+        em.st = s_emit[warp];
+        if (lane < 2 * kEoBuckets) em.st[lane] = 0;
+        __syncwarp();
+    }
     const int64_t n_heavy = a.n_heavy_dev ? (int64_t)*a.n_heavy_dev : a.n_heavy;
 
     // ---- phase 1: heavy vertices
@@ -440,6 +522,9 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
             const uint32_t u = __ldg(a.heavy + h);
             const uint32_t ou = (uint32_t)__ldg(a.offp + u);
             const int d = (int)(__ldg(a.offp + u + 1) - (int64_t)ou);
+            const int nin = (int)__ldg(a.din + u);
+            const int items = d + (nin + 31) / 32;                    // out-arcs, then groups of 32 in-arcs
+            const int64_t ib = __ldg(a.offs + u) - (int64_t)ou;       // start of u's in-arcs in inl
             const bool staged = d <= cap;  // list bounds of N+(u) kept in shared memory
             for (int c0 = 0; c0 < d; c0 += cap) {
                 const int cn = min(cap, d - c0);
@@ -456,10 +541,12 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     const bool dead = M == Mode::EoReserve && a.considered != nullptr && a.considered[ou + i];
                     if (staged) {
                         const int64_t ov = __ldg(a.offp + v);
+                        const int dv = (int)(__ldg(a.offp + v + 1) - ov);
                         vv[i] = v;
                         vo[i] = (uint32_t)ov;
-                        // a considered arc u->v closes no live triangle
-                        vd[i] = dead ? 0 : (int)(__ldg(a.offp + v + 1) - ov);
+                        // a considered arc u->v closes no live triangle; an arc
+                        // with d+(v) > d+(u) is streamed from v's side
+                        vd[i] = (dead || dv > d) ? 0 : dv;
                     }
                     if (!dead) table_insert(tb, log_slots, v, k, a.err);
                 }
@@ -469,7 +556,15 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     int i = 0;
                     if (lane == 0) i = atomicAdd(&s_next, 1);
                     i = __shfl_sync(kFull, i, 0);
-                    if (i >= d) break;
+                    if (i >= items) break;
+                    if (i >= d) {  // 32 in-arcs v->u with d+(v) < d+(u): stream each N+(v)
+                        const int g0 = (i - d) * 32;
+                        stream_in_group<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)c0, ib, g0, min(32, nin - g0),
+                                           q, qn, live, probes, tris, em, c0 == 0);
+                        continue;
+                    }
+                    // out-arc u->v: stream N+(v)
+                    const uint32_t e = ou + (uint32_t)i;
                     uint32_t v, ov;
                     int dv;
                     if (staged) {
@@ -477,16 +572,16 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                         ov = vo[i];
                         dv = vd[i];
                     } else {
-                        v = __ldg(a.colp + ou + i);
+                        v = __ldg(a.colp + e);
                         const int64_t o64 = __ldg(a.offp + v);
                         ov = (uint32_t)o64;
-                        dv = (M == Mode::EoReserve && a.considered != nullptr && a.considered[ou + i]) ? 0
-                                                                            : (int)(__ldg(a.offp + v + 1) - o64);
+                        dv = (int)(__ldg(a.offp + v + 1) - o64);
+                        if (dv > d || (M == Mode::EoReserve && a.considered != nullptr && a.considered[e])) dv = 0;
                     }
                     // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
                     if (lane == 0 && c0 == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou + (uint32_t)c0, v, ov, dv, q,
-                                  qn, live, tris, em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, e, ou + (uint32_t)c0, v, ov, dv, q, qn, live, tris,
+                                  em);
                 }
                 __syncthreads();  // the table is rebuilt for the next chunk or vertex
             }
@@ -503,19 +598,22 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
             if ((int64_t)base >= a.n) break;
             const int64_t ul = (int64_t)base + lane;
             uint32_t oul = 0;
-            int dl = 0;
+            int dl = 0, nl = 0;
             if (ul < a.n) {
                 const int64_t o0 = __ldg(a.offp + ul);
                 oul = (uint32_t)o0;
                 dl = (int)(__ldg(a.offp + ul + 1) - o0);
+                nl = (int)__ldg(a.din + ul);
             }
-            unsigned lm = __ballot_sync(kFull, dl >= 2 && dl <= a.light_max);
+            // d+(u) < 2 closes no triangle at u (and then u has no in-arcs to stream)
+            unsigned lm = __ballot_sync(kFull, dl >= 2 && dl <= a.light_max && dl + nl <= a.light_items);
             while (lm) {
                 const int src = __ffs(lm) - 1;
                 lm &= lm - 1;
                 const uint32_t u = (uint32_t)(base + src);
                 const uint32_t ou = __shfl_sync(kFull, oul, src);
                 const int d = __shfl_sync(kFull, dl, src);
+                const int nin = __shfl_sync(kFull, nl, src);
                 const int log_slots = max(3, ceil_log2(4 * d));
                 for (int s2 = lane; s2 < (1 << log_slots); s2 += 32) tb.slot[s2] = kSlotEmpty;
                 if (lane == 0) *tb.stash_n = 0;
@@ -531,7 +629,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     d0 = (int)(__ldg(a.offp + n0 + 1) - b0);
                     live0 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane];
                     if (live0) table_insert(tb, log_slots, n0, lane, a.err);
-                    else d0 = 0;
+                    if (!live0 || d0 > d) d0 = 0;  // streamed from n0's side when d+(n0) > d+(u)
                 }
                 if (lane + 32 < d) {
                     n1 = __ldg(a.colp + ou + lane + 32);
@@ -540,7 +638,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     d1 = (int)(__ldg(a.offp + n1 + 1) - b1);
                     live1 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane + 32];
                     if (live1) table_insert(tb, log_slots, n1, lane + 32, a.err);
-                    else d1 = 0;
+                    if (!live1 || d1 > d) d1 = 0;
                 }
                 __syncwarp();
                 const int stash_n = min(*tb.stash_n, kStash);
@@ -553,6 +651,11 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris,
                                   em);
                 }
+                // in-arcs v->u with d+(v) < d+(u), in groups of 32
+                const int64_t ib = nin > 0 ? __ldg(a.offs + u) - (int64_t)ou : 0;
+                for (int c = 0; c < nin; c += 32)
+                    stream_in_group<M>(a, tb, log_slots, stash_n, u, ou, ib, c, min(32, nin - c), q, qn, live, probes,
+                                       tris, em, true);
                 __syncwarp();
             }
         }
@@ -563,11 +666,60 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
 // Heavy vertices in decreasing out-degree order, by log2 buckets: pass 1
 // counts the vertices of each bucket (and the maximum out-degree), pass 2
 // scatters them so that larger buckets come first.
-constexpr int kBuckets = 17;  // floor(log2(d+)) for d+ < 2^17
+constexpr int kBuckets = 52;  // floor(log2) of the work bound d+ (d+ + in-arcs)
 
-__device__ __forceinline__ int bucket_of(int64_t d) { return 63 - __clzll((unsigned long long)d); }
+__device__ __forceinline__ int bucket_of(unsigned long long d) { return 63 - __clzll(d); }
 
-__global__ void classify_count_kernel(const int64_t *__restrict__ offp, int64_t n, int light_max,
+// A vertex goes to the CTA phase when its table or its arc count is too large
+// for one warp; the bucket orders those vertices by the bound d+(x) * (d+(x) +
+// in-arcs(x)) on the probes made there (every streamed list is at most d+(x)).
+__device__ __forceinline__ bool is_heavy(int64_t d, int64_t nin, int light_max, int light_items) {
+    return d >= 2 && (d > light_max || d + nin > light_items);
+}
+__device__ __forceinline__ int heavy_bucket(int64_t d, int64_t nin) {
+    return min(bucket_of((unsigned long long)d * (unsigned long long)(d + nin)), kBuckets - 1);
+}
+
+// In-arcs streamed from the head's side: for every arc u->v of E+ with
+// d+(u) < d+(v), append (u, arc) to v's in-list.  The row of v in the
+// symmetric CSR holds its d(v) - d+(v) in-arcs, so v's list has room at
+// inl[offs(v) - offp(v) ...].  The order inside a list is whatever the
+// atomics give; nothing downstream depends on it.  A list that would outgrow
+// that room (an asymmetric input) raises kDevBadGraph instead of writing.
+__global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uint32_t *__restrict__ colp,
+                                     const int64_t *__restrict__ offs, int64_t n, uint32_t *din, uint2 *inl,
+                                     unsigned long long *ctr, int *err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long cnt = 0;
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n; u += nw) {
+        const int64_t ou = __ldg(offp + u), du = __ldg(offp + u + 1) - ou;
+        for (int64_t i = lane; i < du; i += 32) {
+            const uint32_t v = __ldg(colp + ou + i);
+            const int64_t ov = __ldg(offp + v);
+            const int64_t dv = __ldg(offp + v + 1) - ov;
+            if (du < dv) {
+                const int64_t sv = __ldg(offs + v);
+                const int64_t room = (__ldg(offs + v + 1) - sv) - dv;
+                const uint32_t k = atomicAdd(din + v, 1u);
+                if ((int64_t)k < room) {
+                    inl[sv - ov + k] = make_uint2((uint32_t)u, (uint32_t)(ou + i));
+                    ++cnt;
+                } else {
+                    atomicExch(err, (int)kDevBadGraph);
+                }
+            }
+        }
+    }
+    cnt = warp_sum(cnt);
+    if (lane == 0 && cnt) atomicAdd(ctr + kCtrInArcs, cnt);
+}
+
+// Also clamps every in-list length to its room (only an asymmetric input,
+// already flagged by the scatter, can exceed it), so that no later read
+// leaves the in-arc array.
+__global__ void classify_count_kernel(const int64_t *__restrict__ offp, const int64_t *__restrict__ offs,
+                                      uint32_t *din, int64_t n, int light_max, int light_items,
                                       unsigned long long *bucket_cnt, unsigned long long *ctr) {
     __shared__ unsigned int s_cnt[kBuckets];
     if (threadIdx.x < kBuckets) s_cnt[threadIdx.x] = 0;
@@ -577,7 +729,15 @@ __global__ void classify_count_kernel(const int64_t *__restrict__ offp, int64_t 
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
         const int64_t d = offp[u + 1] - offp[u];
         dmax = d > (int64_t)dmax ? (unsigned long long)d : dmax;
-        if (d > light_max) atomicAdd(&s_cnt[min(bucket_of(d), kBuckets - 1)], 1u);
+        int64_t nin = din[u];
+        if (nin > 0) {
+            const int64_t room = (offs[u + 1] - offs[u]) - d;
+            if (nin > room) {
+                nin = room < 0 ? 0 : room;
+                din[u] = (uint32_t)nin;
+            }
+        }
+        if (is_heavy(d, nin, light_max, light_items)) atomicAdd(&s_cnt[heavy_bucket(d, nin)], 1u);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -589,7 +749,8 @@ __global__ void classify_count_kernel(const int64_t *__restrict__ offp, int64_t 
     if (threadIdx.x < kBuckets && s_cnt[threadIdx.x]) atomicAdd(bucket_cnt + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
 }
 
-__global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, int64_t n, int light_max,
+__global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, const uint32_t *__restrict__ din,
+                                        int64_t n, int light_max, int light_items,
                                         const unsigned long long *__restrict__ bucket_cnt,
                                         unsigned long long *bucket_fill, uint32_t *heavy,
                                         unsigned long long *total_out) {
@@ -606,8 +767,9 @@ __global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, int64_
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
         const int64_t d = offp[u + 1] - offp[u];
-        if (d > light_max) {
-            const int b = min(bucket_of(d), kBuckets - 1);
+        const int64_t nin = din[u];
+        if (is_heavy(d, nin, light_max, light_items)) {
+            const int b = heavy_bucket(d, nin);
             heavy[s_off[b] + atomicAdd(bucket_fill + b, 1ull)] = (uint32_t)u;
         }
     }
@@ -773,8 +935,12 @@ __global__ void eo_list_reset_kernel(const TriRec *__restrict__ L, int64_t len, 
 struct Plan {
     uint32_t *heavy = nullptr;
     unsigned long long *buckets = nullptr;  // counts [kBuckets], fills [kBuckets]
+    uint32_t *din = nullptr;                // in-arcs streamed from the head's side, per vertex
+    uint2 *inl = nullptr;                   // their (tail, arc), at offs(v) - offp(v) per vertex
+    const int64_t *offs = nullptr;          // symmetric offsets of the graph
     int64_t n_heavy = 0, max_deg = 0;
     int light_max = kLightMax;
+    int light_items = kLightItems;
     int log_slots = 3;
     size_t smem = 0;
     int heavy_cap = 8;  // phase-1 table entries
@@ -791,23 +957,47 @@ static sg_status read_ctr(Ctx *c, int first, int count, unsigned long long *out)
 static void free_plan(Ctx *c, Plan *pl) {
     dfree(c, pl->heavy);
     dfree(c, pl->buckets);
+    dfree(c, pl->din);
+    dfree(c, pl->inl);
     pl->heavy = nullptr;
     pl->buckets = nullptr;
+    pl->din = nullptr;
+    pl->inl = nullptr;
 }
 
-static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
+// Gather the in-arcs streamed from the head's side (zeroed counts, then the
+// scatter); the classification that follows clamps the counts.
+static sg_status launch_inarcs(Ctx *c, const Oriented &o, const int64_t *offs, uint32_t *din, uint2 *inl) {
+    SG_CUDA(cudaMemsetAsync(din, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1), c->stream));
+    if (o.n == 0) return SG_OK;
+    const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 16));
+    {
+        SG_LAUNCH(c, "tri_inarcs");
+        inarc_scatter_kernel<<<(unsigned)wblocks, 256, 0, c->stream>>>(o.off, o.col, offs, o.n, din, inl, c->d_ctr,
+                                                                       c->d_err);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64_t nnz, Plan *pl) {
     if (o.m >= (int64_t)0xFFFFFFFFll)
         return fail(SG_ERR_UNSUPPORTED, "triangle kernels address oriented arcs with 32 bits: m must be < 2^32");
+    pl->offs = offs;
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kBuckets);
+    if (st == SG_OK) st = dalloc(c, (void **)&pl->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&pl->inl, sizeof(uint2) * (size_t)std::max<int64_t>(nnz - o.m, 1));
     if (st != SG_OK) return st;
     SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, c->stream));
     SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
+    st = launch_inarcs(c, o, offs, pl->din, pl->inl);
+    if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     if (o.n > 0) {
         SG_LAUNCH(c, "tri_classify");
-        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->light_max, pl->buckets,
-                                                                       c->d_ctr);
+        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, offs, pl->din, o.n, pl->light_max,
+                                                                       pl->light_items, pl->buckets, c->d_ctr);
     }
     SG_CUDA(cudaGetLastError());
     SG_CUDA(cudaMemcpyAsync(c->h_pinned, pl->buckets, sizeof(unsigned long long) * kBuckets, cudaMemcpyDeviceToHost,
@@ -822,7 +1012,8 @@ static sg_status make_plan(Ctx *c, const Oriented &o, Plan *pl) {
     pl->max_deg = (int64_t)cnt[kBuckets];
     if (pl->n_heavy > 0) {
         SG_LAUNCH(c, "tri_classify");
-        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, pl->light_max, pl->buckets,
+        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, pl->din, o.n, pl->light_max,
+                                                                         pl->light_items, pl->buckets,
                                                                          pl->buckets + kBuckets, pl->heavy, nullptr);
     }
     SG_CUDA(cudaGetLastError());
@@ -865,6 +1056,10 @@ static sg_status launch_enum(Ctx *c, const TriArgs &base, const Plan &pl) {
     a.heavy_log_slots = pl.log_slots;
     a.heavy_cap = pl.heavy_cap;
     a.light_max = pl.light_max;
+    a.light_items = pl.light_items;
+    a.offs = pl.offs;
+    a.din = pl.din;
+    a.inl = pl.inl;
     a.work = c->d_ctr + kCtrAux;
     SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
     SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
@@ -890,25 +1085,39 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
     return a;
 }
 
-// Edge-once rounds.  While no list is held, a round enumerates the triangles
-// (reserving the edges of every live selected triangle) and also writes those
-// triangles to a list if it fits the memory budget; rounds then continue on the
-// shrinking list alone.  A round whose list overflowed accepts through the
-// edge pass and the next round enumerates again.
+// Edge-once rounds.  Round r lets the live selected triangles with
+// r2 < theta_r = 2^(27+r) bid (all of them from round 5 on).  A bidder that
+// holds all three reservations is the smallest live triangle on each of its
+// edges (every non-bidder has a larger key), so the accepted set equals the
+// unrestricted greedy scan's, while most triangles die before they ever bid.
+//
+// While no list is held, a round enumerates the triangles (bidding as it goes)
+// and, if it fits a quarter of free memory, also writes every live selected
+// triangle to a list split into buckets by the round in which it first bids.
+// Later rounds run on lists alone: the survivors of the last round plus the
+// bucket of this round are filtered (dead triangles dropped), bid and are
+// compacted into the next active list, so a triangle is first read in the
+// round it bids.  A list that overflowed is dropped: that round accepts from
+// the edges' side and the next round enumerates again.
 static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
     const size_t m = (size_t)std::max<int64_t>(o.m, 1);
     const int choice = k == SG_TR_EO_MAXW ? kChoiceMaxw : (k == SG_TR_EO_MINCOUNT ? kChoiceMinCount : kChoiceRandom);
     uint8_t *considered = nullptr;
-    unsigned long long *resv = nullptr, *lctr = nullptr;
+    unsigned long long *resv = nullptr, *lctr = nullptr;  // lctr: [kEoBuckets] bucket fills, [kEoBuckets] out length
     int *lovf = nullptr;
-    TriRec *LA = nullptr, *LB = nullptr;
-    int64_t capA = 0, lenA = 0;
-    bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
+    TriRec *L = nullptr;   // bucketed list of an enumeration round
+    TriRec *A = nullptr;   // this round's bidders when a list is held
+    bool a_owned = false;  // A was allocated here (not a bucket of L)
+    int64_t lenA = 0;
+    int64_t ubase[kEoBuckets] = {}, used[kEoBuckets] = {};
+    int next_bucket = kEoBuckets;  // first bucket not merged into the active list yet
+    bool listed = false;
+    const bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
     sg_status st = dalloc(c, (void **)&considered, m);
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
-    if (st == SG_OK) st = dalloc(c, (void **)&lctr, 2 * sizeof(unsigned long long) + sizeof(int));
+    if (st == SG_OK) st = dalloc(c, (void **)&lctr, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int));
     if (st == SG_OK) {
-        lovf = reinterpret_cast<int *>(lctr + 2);
+        lovf = reinterpret_cast<int *>(lctr + kEoBuckets + 1);
         if (cudaMemsetAsync(considered, 0, m, c->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
     }
     a.considered = considered;
@@ -916,33 +1125,48 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     const int64_t acc_blocks = std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 8);
     if (st == SG_OK && cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "memset");
-    // Prefix schedule: round r lets only triangles with r2 < theta bid, theta
-    // doubling from 2^27.  A bidder that holds all three reservations is the
-    // smallest live triangle on each of its edges (every non-bidder has a
-    // larger key), so the accepted set equals the unrestricted greedy scan's,
-    // while most triangles die before they ever bid.
-    unsigned long long theta = 1ull << 27;
-    for (int round = 0; st == SG_OK; ++round, theta = std::min(theta * 2, 1ull << 32)) {
+    auto list_blocks = [&](int64_t len) { return std::min<int64_t>((len + 255) / 256, (int64_t)c->num_sms * 8); };
+    for (int round = 0; st == SG_OK; ++round) {
         if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
+        const unsigned long long theta = round >= 5 ? (1ull << 32) : (1ull << (27 + round));
         a.eo_theta = theta;
-        // ---- reserve: every live selected triangle of the prefix bids for its three edges
         unsigned long long live = 0;
-        if (LA == nullptr) {
-            // enumeration round, writing the list when it fits
+        if (!listed) {
+            // ---- enumeration round, writing the bucketed list when it fits
             a.list = nullptr;
             if (use_list) {
                 size_t fr = 0, tot = 0;
                 if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
-                capA = (int64_t)(fr / 4 / sizeof(TriRec));
-                if (c->eo_list_cap > 0) capA = std::min<int64_t>(capA, c->eo_list_cap);
-                if (capA >= 4 * kChunk && dalloc(c, (void **)&LA, (size_t)capA * sizeof(TriRec)) == SG_OK) {
-                    a.list = LA;
+                int64_t cap = (int64_t)(fr / 4 / sizeof(TriRec));
+                if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
+                // bucket shares of the draws r2: 1,1,2,4,8,16 of 32; earlier buckets fold into this round's
+                const int rb = std::min(round, kEoBuckets - 1);
+                double wsum = 0.0, w[kEoBuckets];
+                for (int b = 0; b < kEoBuckets; ++b) {
+                    const double share = b <= 1 ? 1.0 : (double)(1 << (b - 1));
+                    w[b] = b < rb ? 0.0 : share;
+                }
+                for (int b = 0; b < rb; ++b) w[rb] += b <= 1 ? 1.0 : (double)(1 << (b - 1));
+                for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
+                int64_t run = 0;
+                bool big = true;
+                for (int b = 0; b < kEoBuckets; ++b) {
+                    const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
+                    a.list_base[b] = (unsigned long long)run;
+                    a.list_cap[b] = (unsigned long long)cb;
+                    ubase[b] = run;
+                    run += cb;
+                    if (w[b] > 0.0 && cb < 4 * eo_chunk(b)) big = false;
+                }
+                if (big && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(TriRec)) == SG_OK) {
+                    a.list = L;
                     a.list_ctr = lctr;
-                    a.list_cap = capA;
                     a.list_overflow = lovf;
-                    SG_CUDA(cudaMemsetAsync(lctr, 0, 2 * sizeof(unsigned long long) + sizeof(int), c->stream));
+                    a.eo_round = round;
+                    SG_CUDA(cudaMemsetAsync(lctr, 0, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int),
+                                            c->stream));
                 } else {
-                    LA = nullptr;
+                    L = nullptr;
                     set_error("");
                 }
             }
@@ -955,60 +1179,80 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             st = read_ctr(c, kCtrLive, 1, &live);
             if (st != SG_OK || live == 0) break;
             if (a.list != nullptr) {
-                unsigned long long used = 0;
+                unsigned long long fill[kEoBuckets];
                 int ovf = 0;
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned + 1, lovf, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(fill), cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(c->h_pinned) + sizeof(fill), lovf, sizeof(int),
+                                        cudaMemcpyDeviceToHost, c->stream));
                 SG_CUDA(cudaStreamSynchronize(c->stream));
-                std::memcpy(&used, c->h_pinned, sizeof(used));
-                std::memcpy(&ovf, c->h_pinned + 1, sizeof(int));
+                std::memcpy(fill, c->h_pinned, sizeof(fill));
+                std::memcpy(&ovf, reinterpret_cast<char *>(c->h_pinned) + sizeof(fill), sizeof(int));
                 if (ovf) {
-                    dfree(c, LA);
-                    LA = nullptr;
+                    dfree(c, L);
+                    L = nullptr;
                 } else {
-                    lenA = (int64_t)std::min<unsigned long long>(used, (unsigned long long)capA);
+                    listed = true;
+                    for (int b = 0; b < kEoBuckets; ++b)
+                        used[b] = (int64_t)std::min<unsigned long long>(fill[b], a.list_cap[b]);
+                    const int rb = std::min(round, kEoBuckets - 1);
+                    A = L + ubase[rb];
+                    a_owned = false;
+                    lenA = used[rb];
+                    next_bucket = rb + 1;
                 }
             }
             a.list = nullptr;
         } else {
-            // list round: drop dead triangles, reserve, compact into LB
-            if (LB == nullptr) {
-                st = dalloc(c, (void **)&LB, (size_t)std::max<int64_t>(lenA, 1) * sizeof(TriRec));
-                if (st != SG_OK) break;
-            }
-            SG_CUDA(cudaMemsetAsync(lctr, 0, sizeof(unsigned long long), c->stream));
-            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
-            if (blocks > 0) {
+            // ---- list round: last round's survivors plus this round's bucket
+            const int64_t fresh = next_bucket < kEoBuckets ? used[next_bucket] : 0;
+            TriRec *B = nullptr;
+            st = dalloc(c, (void **)&B, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec));
+            if (st != SG_OK) break;
+            unsigned long long *out_len = lctr + kEoBuckets;
+            SG_CUDA(cudaMemsetAsync(out_len, 0, sizeof(unsigned long long), c->stream));
+            if (lenA > 0) {
                 SG_LAUNCH(c, "tri_eo_list_reserve");
-                eo_list_reserve_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, LB, lctr, resv, considered,
-                                                                                theta);
+                eo_list_reserve_kernel<<<(unsigned)list_blocks(lenA), 256, 0, c->stream>>>(A, lenA, B, out_len, resv,
+                                                                                         considered, theta);
             }
+            if (fresh > 0) {
+                SG_LAUNCH(c, "tri_eo_list_reserve");
+                eo_list_reserve_kernel<<<(unsigned)list_blocks(fresh), 256, 0, c->stream>>>(
+                    L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta);
+            }
+            if (next_bucket < kEoBuckets) ++next_bucket;
             SG_CUDA(cudaGetLastError());
-            SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+            SG_CUDA(cudaMemcpyAsync(c->h_pinned, out_len, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    c->stream));
             SG_CUDA(cudaStreamSynchronize(c->stream));
             std::memcpy(&live, c->h_pinned, sizeof(live));
-            if (live == 0) break;
-            std::swap(LA, LB);
+            if (a_owned) dfree(c, A);
+            A = B;
+            a_owned = true;
             lenA = (int64_t)live;
+            if (live == 0) {
+                if (next_bucket >= kEoBuckets) break;  // no triangle left anywhere
+                continue;                              // nothing bid this round
+            }
         }
         ++c->eo_rounds;
-        // ---- accept: triangles holding all three reservations.  A long list is
-        // cheaper to judge from the edges' side (one pass over m reservations).
-        // judging from the edge side costs a binary search per reserved arc;
-        // once the list holds at most two triangles per edge, read the list
-        const bool small_list = LA != nullptr && (double)lenA <= 2.0 * (double)m;
-        if (small_list) {
-            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
+        if (listed && lenA == 0) continue;  // nothing bid this round (its bucket was empty)
+        // ---- accept: triangles holding all three reservations.  Judging from
+        // the edge side costs a pass over m reservations plus a binary search
+        // per reserved arc; once the list holds at most two triangles per
+        // edge, read the list instead
+        if (listed && (double)lenA <= 2.0 * (double)m) {
             SG_LAUNCH(c, "tri_eo_list_accept");
+            const unsigned blocks = (unsigned)list_blocks(lenA);
             if (choice == kChoiceMaxw)
-                eo_list_accept_kernel<kChoiceMaxw><<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv, considered,
-                                                                                             a.del, a.wp, a.tcnt);
+                eo_list_accept_kernel<kChoiceMaxw><<<blocks, 256, 0, c->stream>>>(A, lenA, resv, considered, a.del,
+                                                                                  a.wp, a.tcnt);
             else if (choice == kChoiceMinCount)
-                eo_list_accept_kernel<kChoiceMinCount><<<(unsigned)blocks, 256, 0, c->stream>>>(
-                    LA, lenA, resv, considered, a.del, a.wp, a.tcnt);
+                eo_list_accept_kernel<kChoiceMinCount><<<blocks, 256, 0, c->stream>>>(A, lenA, resv, considered,
+                                                                                      a.del, a.wp, a.tcnt);
             else
-                eo_list_accept_kernel<kChoiceRandom><<<(unsigned)blocks, 256, 0, c->stream>>>(
-                    LA, lenA, resv, considered, a.del, a.wp, a.tcnt);
+                eo_list_accept_kernel<kChoiceRandom><<<blocks, 256, 0, c->stream>>>(A, lenA, resv, considered, a.del,
+                                                                                    a.wp, a.tcnt);
         } else {
             SG_LAUNCH(c, "tri_eo_accept");
             if (choice == kChoiceMaxw)
@@ -1021,17 +1265,16 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         SG_CUDA(cudaGetLastError());
         // ---- reset the reservations for the next round: three scattered
         // writes per listed triangle beat clearing all m words only for short lists
-        if (LA != nullptr && (double)lenA * 96.0 <= 8.0 * (double)m) {
-            const int64_t blocks = std::min<int64_t>((lenA + 255) / 256, (int64_t)c->num_sms * 8);
+        if (listed && (double)lenA * 96.0 <= 8.0 * (double)m) {
             SG_LAUNCH(c, "tri_eo_list_reset");
-            eo_list_reset_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(LA, lenA, resv);
+            eo_list_reset_kernel<<<(unsigned)list_blocks(lenA), 256, 0, c->stream>>>(A, lenA, resv);
         } else {
             SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
         }
         SG_CUDA(cudaGetLastError());
     }
-    dfree(c, LA);
-    dfree(c, LB);
+    if (a_owned) dfree(c, A);
+    dfree(c, L);
     dfree(c, lctr);
     dfree(c, considered);
     dfree(c, resv);
@@ -1040,7 +1283,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
 
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed, uint8_t *del) {
     Plan pl;
-    sg_status st = make_plan(c, o, &pl);
+    sg_status st = make_plan(c, o, g->off, g->nnz, &pl);
     TriArgs a = base_args(c, o);
     a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(seed >> 32);
@@ -1070,26 +1313,28 @@ sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double
     return st;
 }
 
-sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg) {
-    (void)g;
+sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg,
+                   int64_t *in_arcs) {
     Plan pl;
-    sg_status st = make_plan(c, o, &pl);
-    unsigned long long v0[2] = {0, 0}, v1[2] = {0, 0};
-    if (st == SG_OK) st = read_ctr(c, 0, 2, v0);
+    unsigned long long v0[kCtrCount] = {}, v1[kCtrCount] = {};
+    sg_status st = read_ctr(c, 0, kCtrCount, v0);
+    if (st == SG_OK) st = make_plan(c, o, g->off, g->nnz, &pl);
     if (st == SG_OK) st = launch_enum<Mode::Count>(c, base_args(c, o), pl);
-    if (st == SG_OK) st = read_ctr(c, 0, 2, v1);
+    if (st == SG_OK) st = read_ctr(c, 0, kCtrCount, v1);
     if (count) *count = (int64_t)(v1[kCtrTriangles] - v0[kCtrTriangles]);
     if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
     if (maxdeg) *maxdeg = pl.max_deg;
+    if (in_arcs) *in_arcs = (int64_t)(v1[kCtrInArcs] - v0[kCtrInArcs]);
     free_plan(c, &pl);
     return st;
 }
 
 // ---------------------------------------------------------- batched union
-sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt) {
+sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *bt) {
     Plan pl;
     pl.light_max = bt->light_max;
-    sg_status st = make_plan(c, o, &pl);
+    pl.light_items = 4 * bt->light_max;
+    sg_status st = make_plan(c, o, u->off, u->nnz, &pl);
     if (st == SG_OK) {
         bt->log_slots = pl.log_slots;
         bt->smem = pl.smem;
@@ -1100,29 +1345,41 @@ sg_status batch_tr_prepare(Ctx *c, const Oriented &o, BatchTri *bt) {
     if (!bt->heavy) st = dalloc(c, (void **)&bt->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK && !bt->buckets)
         st = dalloc(c, (void **)&bt->buckets, sizeof(unsigned long long) * (2 * kBuckets + 1));
+    if (st == SG_OK && !bt->din) st = dalloc(c, (void **)&bt->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    if (st == SG_OK && !bt->inl)
+        st = dalloc(c, (void **)&bt->inl, sizeof(uint2) * (size_t)std::max<int64_t>(u->nnz - o.m, 1));
     return st;
 }
 
 void batch_tr_free(Ctx *c, BatchTri *bt) {
     dfree(c, bt->heavy);
     dfree(c, bt->buckets);
+    dfree(c, bt->din);
+    dfree(c, bt->inl);
     bt->heavy = nullptr;
     bt->buckets = nullptr;
+    bt->din = nullptr;
+    bt->inl = nullptr;
 }
 
 // No host synchronisation: the heavy-vertex count stays on the device.
-sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const BatchTri &bt, uint8_t *del) {
+sg_status batch_tr_mark(Ctx *c, const Graph *u, const Oriented &o, const BatchDev &b, const BatchTri &bt,
+                        uint8_t *del) {
     if (o.n == 0) return SG_OK;
+    const int light_items = 4 * bt.light_max;
     SG_CUDA(cudaMemsetAsync(bt.buckets, 0, sizeof(unsigned long long) * (2 * kBuckets + 1), c->stream));
+    sg_status st = launch_inarcs(c, o, u->off, bt.din, bt.inl);
+    if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     {
         SG_LAUNCH(c, "tri_classify");
-        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, bt.light_max, bt.buckets,
-                                                                       c->d_ctr);
+        classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, u->off, bt.din, o.n, bt.light_max,
+                                                                       light_items, bt.buckets, c->d_ctr);
     }
     {
         SG_LAUNCH(c, "tri_classify");
-        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, o.n, bt.light_max, bt.buckets,
+        classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, bt.din, o.n, bt.light_max,
+                                                                         light_items, bt.buckets,
                                                                          bt.buckets + kBuckets, bt.heavy,
                                                                          bt.buckets + 2 * kBuckets);
     }
@@ -1135,6 +1392,10 @@ sg_status batch_tr_mark(Ctx *c, const Oriented &o, const BatchDev &b, const Batc
     a.heavy_log_slots = bt.log_slots;
     a.heavy_cap = bt.max_deg;
     a.light_max = bt.light_max;
+    a.light_items = light_items;
+    a.offs = u->off;
+    a.din = bt.din;
+    a.inl = bt.inl;
     a.work = c->d_ctr + kCtrAux;
     a.bparams = b.params;
     a.vgid = b.vgid;
