@@ -45,13 +45,17 @@ constexpr int kLightItems = 256;  // ... with at most this many lists to stream
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
 constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
-constexpr int kQ = 96;            // per-warp hit queue entries (31 left over + 2 slabs of hits)
+constexpr int kQ = 128;           // per-warp hit ring (<= 31 left over + 2 slabs of hits fit)
 constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
 
 // Count: totals only.  EdgeCount: adds every triangle to the counters of its
 // three edges.  Union*: the union-semantics TR kernels.  EoReserve: one
-// edge-once bidding pass.  BatchUnion: union kernels over a batch of graphs.
-enum class Mode { Count, EdgeCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCount, EoReserve, BatchUnion };
+// edge-once bidding pass.  EoEmit: lists the live selected triangles for the
+// edge-once list rounds.  BatchUnion: union kernels over a batch of graphs.
+enum class Mode { Count, EdgeCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCount, EoReserve, EoEmit, BatchUnion };
+// the edge-once passes skip arcs that are already considered
+template <Mode M>
+constexpr bool kEdgeOnce = M == Mode::EoReserve || M == Mode::EoEmit;
 
 struct TriArgs {
     const int64_t *offp;
@@ -81,18 +85,21 @@ struct TriArgs {
     // batched union: per-graph parameters and the graph of every vertex
     const BatchParam *bparams;
     const uint32_t *vgid;
-    // edge-once: optional list of the live selected triangles, split into
+    // edge-once: list of the live selected triangles (EoEmit), split into
     // buckets by the round in which each first bids
-    struct TriRec *list;
+    uint4 *list;
     unsigned long long *list_ctr;  // [kEoBuckets] slots handed out per bucket
     unsigned long long list_base[kEoBuckets], list_cap[kEoBuckets];
     int eo_round;                  // this enumeration's round: earlier buckets fold into it
     int *list_overflow;
 };
 
-// One live selected triangle: sorted original ids x0 < x1 < x2, its draws
-// r1 (edge choice) and r2 (edge-once order), and the oriented arcs joining
-// (x0,x1), (x0,x2), (x1,x2).  x0 == kSentinel marks an unused slot.
+// One live selected triangle of an active list: sorted original ids
+// x0 < x1 < x2, its draws r1 (edge choice) and r2 (edge-once order), and the
+// oriented arcs joining (x0,x1), (x0,x2), (x1,x2).  x0 == kSentinel marks an
+// unused slot.  The enumeration writes the smaller record (a, e_ab, e_ac,
+// e_bc) instead -- a < b < c in the degree order, so b and c are the heads of
+// e_ab and e_ac -- and a triangle is expanded when it first bids.
 struct __align__(16) TriRec {
     uint32_t x0, x1, x2, r1;
     uint32_t r2, e01, e02, e12;
@@ -107,34 +114,33 @@ __device__ __forceinline__ int eo_bucket(uint32_t r2) { return r2 < (1u << 27) ?
 __host__ __device__ constexpr int eo_chunk(int b) { return b <= 1 ? 64 : (32 << b); }
 
 // Per-warp list writer: per bucket it claims chunks of slots, fills them in
-// order and seals the unused tail of a chunk with sentinels.  The cursors live
-// in shared memory (cur, end per bucket).
+// order and seals the unused tail of a chunk with sentinels.  The cursors
+// live in registers spread over the lanes: lane b holds the next free slot of
+// bucket b and lane 8 + b the end of its chunk.
 struct Emitter {
-    unsigned long long *st = nullptr;  // [2 * kEoBuckets]: cur[b], end[b]
+    unsigned long long cur = 0;  // this lane's cursor (see above)
     bool dead = false;
 };
 
-__device__ __forceinline__ void emit_seal(const TriArgs &a, Emitter &em, int b) {
+__device__ __forceinline__ void emit_seal(const TriArgs &a, unsigned long long cur, unsigned long long end) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long cur = em.st[b], end = em.st[kEoBuckets + b];
-    for (unsigned long long i = cur + lane; i < end; i += 32) a.list[i].x0 = kSentinel;
-    __syncwarp();
-    if (lane == 0) em.st[b] = end;
-    __syncwarp();
+    for (unsigned long long i = cur + lane; i < end; i += 32) a.list[i].x = kSentinel;
 }
 
-__device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool want, const TriRec &rec) {
+__device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool want, const uint4 &rec, uint32_t r2) {
     if (em.dead) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
-    const int mb = want ? max(eo_bucket(rec.r2), min(a.eo_round, kEoBuckets - 1)) : -1;
+    const int mb = want ? max(eo_bucket(r2), min(a.eo_round, kEoBuckets - 1)) : -1;
     unsigned pend = __ballot_sync(kFull, want);
     while (pend) {
         const int b = __shfl_sync(kFull, mb, __ffs(pend) - 1);
         const unsigned bm = __ballot_sync(kFull, mb == b);
         pend &= ~bm;
-        const int cnt = __popc(bm);
-        if (em.st[kEoBuckets + b] - em.st[b] < (unsigned long long)cnt) {
-            emit_seal(a, em, b);
+        const unsigned cnt = (unsigned)__popc(bm);
+        unsigned long long cur = __shfl_sync(kFull, em.cur, b);
+        const unsigned long long end = __shfl_sync(kFull, em.cur, 8 + b);
+        if (end - cur < cnt) {
+            emit_seal(a, cur, end);
             const unsigned long long chunk = (unsigned long long)eo_chunk(b);
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(a.list_ctr + b, chunk);
@@ -144,24 +150,24 @@ __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool wa
                 em.dead = true;
                 return;
             }
-            if (lane == 0) {
-                em.st[b] = a.list_base[b] + base;
-                em.st[kEoBuckets + b] = a.list_base[b] + base + chunk;
-            }
-            __syncwarp();
+            cur = a.list_base[b] + base;
+            if (lane == 8 + b) em.cur = cur + chunk;
         }
-        const unsigned long long cur = em.st[b];
         if (mb == b) a.list[cur + __popc(bm & lanemask_lt())] = rec;
-        __syncwarp();
-        if (lane == 0) em.st[b] = cur + cnt;
-        __syncwarp();
+        if (lane == b) em.cur = cur + cnt;
     }
 }
 
-// Oriented arcs are addressed with 32-bit indices (E+ holds fewer than 2^32 arcs).
+// Per-warp ring of found triangles, waiting to be decided 32 at a time.  The
+// table vertex u is the same for every entry (the ring is flushed before the
+// warp moves to another table) and w is the head of the arc iuw, so an entry
+// keeps v and the three arcs.  Oriented arcs are addressed with 32-bit
+// indices (E+ holds fewer than 2^32 arcs).
 struct HitQueue {
-    uint32_t u[kQ], v[kQ], w[kQ];
-    uint32_t iuv[kQ], iuw[kQ], ivw[kQ];
+    uint32_t v[kQ], iuv[kQ], iuw[kQ], ivw[kQ];
+};
+struct QState {
+    int head = 0, n = 0;
 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t key, int log_slots) {
@@ -205,7 +211,8 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
         return;
     } else {
         bool emit = false;
-        TriRec rec;
+        uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t rec_r2 = 0;
         if constexpr (M == Mode::BatchUnion) {
             if (valid) {
                 // the triangle's graph: its own seed, p and kernel, local ids as keys
@@ -270,7 +277,7 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                     if (w02 > bw || (w02 == bw && (x0 > bl || (x0 == bl && x2 > bh)))) { best = e02; bw = w02; bl = x0; bh = x2; }
                     if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
                     a.del[best] = 1;
-                } else {  // EoReserve
+                } else if constexpr (M == Mode::EoReserve) {
                     if (a.considered == nullptr || !(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
                         // the round's prefix of the (r2, a, b, c) order bids for its edges
                         if ((unsigned long long)r.z < a.eo_theta) {
@@ -280,43 +287,54 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                             atomicMin(a.resv + e12, hi | x0);
                         }
                         ++live;
+                    }
+                } else {  // EoEmit: list the live selected triangle, bid later
+                    if (a.considered == nullptr || !(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
+                        ++live;
                         emit = true;
-                        rec = TriRec{x0, x1, x2, r.y, r.z, e01, e02, e12};
+                        rec_r2 = r.z;
+                        // w is last in the degree order; of u and v the head of iuv is the later one
+                        const bool u_first = __ldg(a.colp + iuv) == v;
+                        rec = make_uint4(u_first ? u : v, iuv, u_first ? iuw : ivw, u_first ? ivw : iuw);
                     }
                 }
             }
         }
-        if constexpr (M == Mode::EoReserve) {
-            if (a.list != nullptr) emit_push(a, em, emit, rec);
+        if constexpr (M == Mode::EoEmit) emit_push(a, em, emit, rec, rec_r2);
+    }
+}
+
+// Decide the 32 oldest queued triangles with all lanes.  Kept out of line so
+// that the probe loop's register budget stays small.
+template <Mode M>
+__device__ __noinline__ void drain32(const TriArgs &a, const HitQueue &q, int head, uint32_t u, unsigned &live,
+                                     Emitter &em) {
+    const int k = (head + (threadIdx.x & 31)) & (kQ - 1);
+    const uint32_t iuw = q.iuw[k];
+    decide<M>(a, true, u, q.v[k], __ldg(a.colp + iuw), q.iuv[k], iuw, q.ivw[k], live, em);
+    __syncwarp();
+}
+
+// Decide everything queued for the table vertex u (the last group with idle lanes).
+template <Mode M>
+__device__ __forceinline__ void flush_hits(const TriArgs &a, const HitQueue &q, QState &qs, uint32_t u,
+                                           unsigned &live, Emitter &em) {
+    if constexpr (M != Mode::Count && M != Mode::EdgeCount) {
+        const int lane = threadIdx.x & 31;
+        while (qs.n >= 32) {
+            drain32<M>(a, q, qs.head, u, live, em);
+            qs.head = (qs.head + 32) & (kQ - 1);
+            qs.n -= 32;
         }
+        const bool valid = lane < qs.n;
+        const int k = (qs.head + lane) & (kQ - 1);
+        const uint32_t iuw = valid ? q.iuw[k] : 0u;
+        decide<M>(a, valid, u, valid ? q.v[k] : 0u, valid ? __ldg(a.colp + iuw) : 0u, valid ? q.iuv[k] : 0u, iuw,
+                  valid ? q.ivw[k] : 0u, live, em);
+        __syncwarp();
     }
-}
-
-// Decide the 32 oldest queued triangles with all lanes and shift the rest down.
-// Kept out of line so that the probe loop's register budget stays small.
-template <Mode M>
-__device__ __noinline__ int drain32(const TriArgs &a, HitQueue &q, int qn, unsigned &live, Emitter &em) {
-    const int lane = threadIdx.x & 31;
-    decide<M>(a, true, q.u[lane], q.v[lane], q.w[lane], q.iuv[lane], q.iuw[lane], q.ivw[lane], live, em);
-    __syncwarp();
-    const int rest = qn - 32;
-    for (int k = lane; k < rest; k += 32) {
-        q.u[k] = q.u[k + 32]; q.v[k] = q.v[k + 32]; q.w[k] = q.w[k + 32];
-        q.iuv[k] = q.iuv[k + 32]; q.iuw[k] = q.iuw[k + 32]; q.ivw[k] = q.ivw[k + 32];
-        __syncwarp(__activemask());
-    }
-    __syncwarp();
-    return rest;
-}
-
-template <Mode M>
-__device__ __forceinline__ void flush_hits(const TriArgs &a, HitQueue &q, int qn, unsigned &live, Emitter &em) {
-    const int lane = threadIdx.x & 31;
-    while (qn >= 32) qn = drain32<M>(a, q, qn, live, em);
-    const bool valid = lane < qn;
-    decide<M>(a, valid, valid ? q.u[lane] : 0u, valid ? q.v[lane] : 0u, valid ? q.w[lane] : 0u,
-              valid ? q.iuv[lane] : 0u, valid ? q.iuw[lane] : 0u, valid ? q.ivw[lane] : 0u, live, em);
-    __syncwarp();
+    qs.head = 0;
+    qs.n = 0;
 }
 
 // Shared-memory cuckoo table of N+(u) (Pagh & Rodler's cuckoo hashing; the
@@ -375,7 +393,7 @@ __device__ __forceinline__ bool table_find(const Table &tb, int sh, int stash_n,
 template <Mode M>
 __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
                                            uint32_t u, uint32_t iuv, uint32_t ou, uint32_t v, uint32_t ov, int dv,
-                                           HitQueue &q, int &qn, unsigned &live, unsigned long long &tris,
+                                           HitQueue &q, QState &qs, unsigned &live, unsigned long long &tris,
                                            Emitter &em) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
@@ -405,21 +423,29 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
             huv += (unsigned)(__popc(ma) + __popc(mb));
             continue;
         }
-        if (ma | mb) {
-            int s0 = qn + __popc(ma & lt);
-            if (ha) {
-                q.u[s0] = u; q.v[s0] = v; q.w[s0] = wa;
-                q.iuv[s0] = iuv; q.iuw[s0] = ou + ta; q.ivw[s0] = ov + (uint32_t)ja;
-            }
-            s0 = qn + __popc(ma) + __popc(mb & lt);
-            if (hb) {
-                q.u[s0] = u; q.v[s0] = v; q.w[s0] = wb;
-                q.iuv[s0] = iuv; q.iuw[s0] = ou + tb2; q.ivw[s0] = ov + (uint32_t)jb;
-            }
-            qn += __popc(ma) + __popc(mb);
+        if constexpr (M == Mode::Count) {
             if (lane == 0) tris += (unsigned)(__popc(ma) + __popc(mb));
+            continue;
+        }
+        if (ma | mb) {
+            const int pa = __popc(ma), pb = __popc(mb);
+            const int tail = qs.head + qs.n;
+            if (ha) {
+                const int s0 = (tail + __popc(ma & lt)) & (kQ - 1);
+                q.v[s0] = v; q.iuv[s0] = iuv; q.iuw[s0] = ou + ta; q.ivw[s0] = ov + (uint32_t)ja;
+            }
+            if (hb) {
+                const int s0 = (tail + pa + __popc(mb & lt)) & (kQ - 1);
+                q.v[s0] = v; q.iuv[s0] = iuv; q.iuw[s0] = ou + tb2; q.ivw[s0] = ov + (uint32_t)jb;
+            }
+            qs.n += pa + pb;
+            if (lane == 0) tris += (unsigned)(pa + pb);
             __syncwarp();
-            while (qn >= 32) qn = drain32<M>(a, q, qn, live, em);
+            while (qs.n >= 32) {
+                drain32<M>(a, q, qs.head, u, live, em);
+                qs.head = (qs.head + 32) & (kQ - 1);
+                qs.n -= 32;
+            }
         }
     }
     if constexpr (M == Mode::EdgeCount) {
@@ -436,7 +462,7 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
 template <Mode M>
 __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
                                                 uint32_t u, uint32_t tbase, int64_t ib, int first, int cnt,
-                                                HitQueue &q, int &qn, unsigned &live, unsigned long long &probes,
+                                                HitQueue &q, QState &qs, unsigned &live, unsigned long long &probes,
                                                 unsigned long long &tris, Emitter &em, bool count_probes) {
     const int lane = threadIdx.x & 31;
     uint32_t sv = 0, so = 0, se = 0;
@@ -447,7 +473,7 @@ __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &t
         se = it.y;
         const int64_t b0 = __ldg(a.offp + sv);
         so = (uint32_t)b0;
-        sd = (M == Mode::EoReserve && a.considered != nullptr && a.considered[se])
+        sd = (kEdgeOnce<M> && a.considered != nullptr && a.considered[se])
                  ? 0 : (int)(__ldg(a.offp + sv + 1) - b0);
     }
     for (int i = 0; i < cnt; ++i) {
@@ -456,17 +482,17 @@ __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &t
         const uint32_t e = __shfl_sync(kFull, se, i);
         const int dv = __shfl_sync(kFull, sd, i);
         if (lane == 0 && count_probes) probes += (unsigned)dv;
-        probe_list<M>(a, tb, log_slots, stash_n, u, e, tbase, v, ov, dv, q, qn, live, tris, em);
+        probe_list<M>(a, tb, log_slots, stash_n, u, e, tbase, v, ov, dv, q, qs, live, tris, em);
     }
 }
 
 template <Mode M>
-__device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, unsigned live,
-                                       unsigned long long probes, unsigned long long tris, Emitter &em) {
-    flush_hits<M>(a, q, qn, live, em);
-    if constexpr (M == Mode::EoReserve) {
-        if (a.list != nullptr && !em.dead)
-            for (int b = 0; b < kEoBuckets; ++b) emit_seal(a, em, b);
+__device__ __forceinline__ void finish(const TriArgs &a, unsigned live, unsigned long long probes,
+                                       unsigned long long tris, Emitter &em) {
+    if constexpr (M == Mode::EoEmit) {
+        if (!em.dead)
+            for (int b = 0; b < kEoBuckets; ++b)
+                emit_seal(a, __shfl_sync(kFull, em.cur, b), __shfl_sync(kFull, em.cur, 8 + b));
     }
     const unsigned long long P = warp_sum(probes), T = warp_sum(tris);
     const unsigned L = warp_sum(live);
@@ -478,32 +504,28 @@ __device__ __forceinline__ void finish(const TriArgs &a, HitQueue &q, int qn, un
 }
 
 // One persistent launch per enumeration pass.
-// Phase 1: heavy vertices (d+(u) > light_max), largest out-degree first; a CTA
-// stages N+(u) in a shared-memory table (plus every v's list bounds) and its
-// warps claim the lists N+(v) one at a time.  Phase 2: light vertices, a warp
-// per vertex with its own small table; warps claim 32 vertex ids at a time.
-// Probe and triangle totals are counted per list and per found triangle.
+// Phase 1: heavy vertices (large N+(u) or many lists to stream), largest work
+// bound first; a CTA stages N+(u) in a shared-memory table (plus every
+// out-neighbour's list bounds) and its warps claim out-arcs one at a time and
+// in-arcs 32 at a time.  Phase 2: light vertices, a warp per vertex with its
+// own small table; warps claim 32 vertex ids at a time.  Probe and triangle
+// totals are counted per list and per found triangle.  The listing pass keeps
+// more registers per thread (4 CTAs per SM): its record assembly spills at 48.
 template <Mode M>
-__global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
+__global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_kernel(TriArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next;
     __shared__ long long s_h;
     __shared__ int s_stash_n[kTW + 1];
     __shared__ unsigned long long s_stash[kTW + 1][kStash];
-    __shared__ unsigned long long s_emit[M == Mode::EoReserve ? kTW : 1][2 * kEoBuckets];
     HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
     unsigned char *tbl = smem + sizeof(HitQueue) * kTW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     HitQueue &q = qs[warp];
-    int qn = 0;
+    QState qst;
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
     Emitter em;
-    if constexpr (M == Mode::EoReserve) {
-        em.st = s_emit[warp];
-        if (lane < 2 * kEoBuckets) em.st[lane] = 0;
-        __syncwarp();
-    }
     const int64_t n_heavy = a.n_heavy_dev ? (int64_t)*a.n_heavy_dev : a.n_heavy;
 
     // ---- phase 1: heavy vertices
@@ -538,7 +560,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                 for (int k = threadIdx.x; k < cn; k += blockDim.x) {
                     const int i = c0 + k;
                     const uint32_t v = __ldg(a.colp + ou + i);
-                    const bool dead = M == Mode::EoReserve && a.considered != nullptr && a.considered[ou + i];
+                    const bool dead = kEdgeOnce<M> && a.considered != nullptr && a.considered[ou + i];
                     if (staged) {
                         const int64_t ov = __ldg(a.offp + v);
                         const int dv = (int)(__ldg(a.offp + v + 1) - ov);
@@ -560,7 +582,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     if (i >= d) {  // 32 in-arcs v->u with d+(v) < d+(u): stream each N+(v)
                         const int g0 = (i - d) * 32;
                         stream_in_group<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)c0, ib, g0, min(32, nin - g0),
-                                           q, qn, live, probes, tris, em, c0 == 0);
+                                           q, qst, live, probes, tris, em, c0 == 0);
                         continue;
                     }
                     // out-arc u->v: stream N+(v)
@@ -576,15 +598,16 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                         const int64_t o64 = __ldg(a.offp + v);
                         ov = (uint32_t)o64;
                         dv = (int)(__ldg(a.offp + v + 1) - o64);
-                        if (dv > d || (M == Mode::EoReserve && a.considered != nullptr && a.considered[e])) dv = 0;
+                        if (dv > d || (kEdgeOnce<M> && a.considered != nullptr && a.considered[e])) dv = 0;
                     }
                     // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
                     if (lane == 0 && c0 == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, tb, log_slots, stash_n, u, e, ou + (uint32_t)c0, v, ov, dv, q, qn, live, tris,
-                                  em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, e, ou + (uint32_t)c0, v, ov, dv, q, qst, live,
+                                  tris, em);
                 }
                 __syncthreads();  // the table is rebuilt for the next chunk or vertex
             }
+            flush_hits<M>(a, q, qst, u, live, em);
         }
     }
 
@@ -627,7 +650,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     const int64_t b0 = __ldg(a.offp + n0);
                     o0 = (uint32_t)b0;
                     d0 = (int)(__ldg(a.offp + n0 + 1) - b0);
-                    live0 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane];
+                    live0 = !kEdgeOnce<M> || a.considered == nullptr || !a.considered[ou + lane];
                     if (live0) table_insert(tb, log_slots, n0, lane, a.err);
                     if (!live0 || d0 > d) d0 = 0;  // streamed from n0's side when d+(n0) > d+(u)
                 }
@@ -636,7 +659,7 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     const int64_t b1 = __ldg(a.offp + n1);
                     o1 = (uint32_t)b1;
                     d1 = (int)(__ldg(a.offp + n1 + 1) - b1);
-                    live1 = M != Mode::EoReserve || a.considered == nullptr || !a.considered[ou + lane + 32];
+                    live1 = !kEdgeOnce<M> || a.considered == nullptr || !a.considered[ou + lane + 32];
                     if (live1) table_insert(tb, log_slots, n1, lane + 32, a.err);
                     if (!live1 || d1 > d) d1 = 0;
                 }
@@ -648,19 +671,20 @@ __global__ void __launch_bounds__(kTW * 32, 5) tri_enum_kernel(TriArgs a) {
                     const uint32_t ov = __shfl_sync(kFull, lo ? o0 : o1, i & 31);
                     const int dv = __shfl_sync(kFull, lo ? d0 : d1, i & 31);
                     if (lane == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, q, qn, live, tris,
-                                  em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, q, qst, live,
+                                  tris, em);
                 }
                 // in-arcs v->u with d+(v) < d+(u), in groups of 32
                 const int64_t ib = nin > 0 ? __ldg(a.offs + u) - (int64_t)ou : 0;
                 for (int c = 0; c < nin; c += 32)
-                    stream_in_group<M>(a, tb, log_slots, stash_n, u, ou, ib, c, min(32, nin - c), q, qn, live, probes,
-                                       tris, em, true);
+                    stream_in_group<M>(a, tb, log_slots, stash_n, u, ou, ib, c, min(32, nin - c), q, qst, live,
+                                       probes, tris, em, true);
+                flush_hits<M>(a, q, qst, u, live, em);
                 __syncwarp();
             }
         }
     }
-    finish<M>(a, q, qn, live, probes, tris, em);
+    finish<M>(a, live, probes, tris, em);
 }
 
 // Heavy vertices in decreasing out-degree order, by log2 buckets: pass 1
@@ -918,6 +942,61 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
     }
 }
 
+// Reserve for a bucket written by the enumeration: drop the triangles that
+// lost an edge, expand the survivors to full records (vertices from the arc
+// heads, draws recomputed), bid and append them to `out` like the kernel above.
+__global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__restrict__ F, int64_t len,
+                                                               TriRec *__restrict__ out, unsigned long long *out_len,
+                                                               unsigned long long *resv,
+                                                               const uint8_t *__restrict__ considered,
+                                                               unsigned long long theta,
+                                                               const uint32_t *__restrict__ colp, uint32_t k0,
+                                                               uint32_t k1) {
+    __shared__ int s_cnt[8];
+    __shared__ unsigned long long s_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool keep = false;
+        TriRec r{kSentinel, 0, 0, 0, 0, 0, 0, 0};
+        if (i < len) {
+            const uint4 f = F[i];
+            if (f.x != kSentinel && !(considered[f.y] | considered[f.z] | considered[f.w])) {
+                keep = true;
+                uint32_t x0 = f.x, x1 = __ldg(colp + f.y), x2 = __ldg(colp + f.z);
+                uint32_t e01 = f.y, e02 = f.z, e12 = f.w;
+                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+                if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+                const uint4 d = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), k0, k1);
+                r = TriRec{x0, x1, x2, d.y, d.z, e01, e02, e12};
+                if ((unsigned long long)d.z < theta) {
+                    const unsigned long long hi = (unsigned long long)d.z << 32;
+                    atomicMin(resv + e01, hi | x2);
+                    atomicMin(resv + e02, hi | x1);
+                    atomicMin(resv + e12, hi | x0);
+                }
+            }
+        }
+        const unsigned bm = __ballot_sync(kFull, keep);
+        if (lane == 0) s_cnt[warp] = __popc(bm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int c = s_cnt[k];
+                s_cnt[k] = tot;
+                tot += c;
+            }
+            s_base = tot ? atomicAdd(out_len, (unsigned long long)tot) : 0ull;
+        }
+        __syncthreads();
+        if (keep) out[s_base + s_cnt[warp] + __popc(bm & lanemask_lt())] = r;
+        __syncthreads();
+    }
+}
+
 // Clear the reservations of the listed triangles' edges (cheaper than a full
 // reset once the list is short): every reserved edge belongs to a listed triangle.
 __global__ void eo_list_reset_kernel(const TriRec *__restrict__ L, int64_t len, unsigned long long *resv) {
@@ -1091,28 +1170,29 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
 // edges (every non-bidder has a larger key), so the accepted set equals the
 // unrestricted greedy scan's, while most triangles die before they ever bid.
 //
-// While no list is held, a round enumerates the triangles (bidding as it goes)
-// and, if it fits a quarter of free memory, also writes every live selected
-// triangle to a list split into buckets by the round in which it first bids.
-// Later rounds run on lists alone: the survivors of the last round plus the
-// bucket of this round are filtered (dead triangles dropped), bid and are
-// compacted into the next active list, so a triangle is first read in the
-// round it bids.  A list that overflowed is dropped: that round accepts from
-// the edges' side and the next round enumerates again.
+// The first round enumerates the triangles once and lists every live selected
+// one (16 bytes each, within a quarter of free memory), split into buckets by
+// the round in which it first bids.  Each later round works on lists alone:
+// the survivors of the last round plus this round's bucket are filtered
+// (triangles that lost an edge are dropped), bid and are compacted into the
+// next active list, so a listed triangle is read once before it bids.  If the
+// list does not fit, the round enumerates again and bids directly, accepting
+// from the edges' side; a later round retries the list once the live
+// triangles fit.
 static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
     const size_t m = (size_t)std::max<int64_t>(o.m, 1);
     const int choice = k == SG_TR_EO_MAXW ? kChoiceMaxw : (k == SG_TR_EO_MINCOUNT ? kChoiceMinCount : kChoiceRandom);
     uint8_t *considered = nullptr;
-    unsigned long long *resv = nullptr, *lctr = nullptr;  // lctr: [kEoBuckets] bucket fills, [kEoBuckets] out length
+    unsigned long long *resv = nullptr, *lctr = nullptr;  // lctr: [kEoBuckets] bucket fills, then an out length
     int *lovf = nullptr;
-    TriRec *L = nullptr;   // bucketed list of an enumeration round
-    TriRec *A = nullptr;   // this round's bidders when a list is held
-    bool a_owned = false;  // A was allocated here (not a bucket of L)
+    uint4 *L = nullptr;    // bucketed list written by the enumeration
+    TriRec *A = nullptr;   // active list: this round's bidders
     int64_t lenA = 0;
     int64_t ubase[kEoBuckets] = {}, used[kEoBuckets] = {};
-    int next_bucket = kEoBuckets;  // first bucket not merged into the active list yet
+    int next_bucket = kEoBuckets;  // next bucket to merge into the active list
     bool listed = false;
     const bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
+    bool try_list = use_list;
     sg_status st = dalloc(c, (void **)&considered, m);
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
     if (st == SG_OK) st = dalloc(c, (void **)&lctr, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int));
@@ -1126,122 +1206,138 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     if (st == SG_OK && cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "memset");
     auto list_blocks = [&](int64_t len) { return std::min<int64_t>((len + 255) / 256, (int64_t)c->num_sms * 8); };
+    auto list_capacity = [&]() -> int64_t {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+        int64_t cap = (int64_t)(fr / 4 / sizeof(uint4));
+        if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
+        return cap;
+    };
     for (int round = 0; st == SG_OK; ++round) {
         if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
         const unsigned long long theta = round >= 5 ? (1ull << 32) : (1ull << (27 + round));
         a.eo_theta = theta;
         unsigned long long live = 0;
-        if (!listed) {
-            // ---- enumeration round, writing the bucketed list when it fits
-            a.list = nullptr;
-            if (use_list) {
-                size_t fr = 0, tot = 0;
-                if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
-                int64_t cap = (int64_t)(fr / 4 / sizeof(TriRec));
-                if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
-                // bucket shares of the draws r2: 1,1,2,4,8,16 of 32; earlier buckets fold into this round's
-                const int rb = std::min(round, kEoBuckets - 1);
-                double wsum = 0.0, w[kEoBuckets];
-                for (int b = 0; b < kEoBuckets; ++b) {
-                    const double share = b <= 1 ? 1.0 : (double)(1 << (b - 1));
-                    w[b] = b < rb ? 0.0 : share;
-                }
-                for (int b = 0; b < rb; ++b) w[rb] += b <= 1 ? 1.0 : (double)(1 << (b - 1));
-                for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
-                int64_t run = 0;
-                bool big = true;
-                for (int b = 0; b < kEoBuckets; ++b) {
-                    const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
-                    a.list_base[b] = (unsigned long long)run;
-                    a.list_cap[b] = (unsigned long long)cb;
-                    ubase[b] = run;
-                    run += cb;
-                    if (w[b] > 0.0 && cb < 4 * eo_chunk(b)) big = false;
-                }
-                if (big && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(TriRec)) == SG_OK) {
-                    a.list = L;
-                    a.list_ctr = lctr;
-                    a.list_overflow = lovf;
-                    a.eo_round = round;
-                    SG_CUDA(cudaMemsetAsync(lctr, 0, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int),
-                                            c->stream));
-                } else {
-                    L = nullptr;
-                    set_error("");
-                }
+        if (!listed && try_list) {
+            // ---- enumerate and list the live selected triangles, no bids
+            const int64_t cap = list_capacity();
+            // bucket shares of the draws r2: 1,1,2,4,8,16 of 32; earlier buckets fold into this round's
+            const int rb = std::min(round, kEoBuckets - 1);
+            double w[kEoBuckets], wsum = 0.0;
+            for (int b = 0; b < kEoBuckets; ++b) w[b] = b < rb ? 0.0 : (b <= 1 ? 1.0 : (double)(1 << (b - 1)));
+            for (int b = 0; b < rb; ++b) w[rb] += b <= 1 ? 1.0 : (double)(1 << (b - 1));
+            for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
+            int64_t run = 0;
+            bool big = true;
+            for (int b = 0; b < kEoBuckets; ++b) {
+                const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
+                a.list_base[b] = (unsigned long long)run;
+                a.list_cap[b] = (unsigned long long)cb;
+                ubase[b] = run;
+                run += cb;
+                if (w[b] > 0.0 && cb < 4 * eo_chunk(b)) big = false;
             }
+            if (big && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(uint4)) == SG_OK) {
+                a.list = L;
+                a.list_ctr = lctr;
+                a.list_overflow = lovf;
+                a.eo_round = round;
+                SG_CUDA(cudaMemsetAsync(lctr, 0, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int),
+                                        c->stream));
+                SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+                // nothing is considered before the first acceptance: skip the flag reads
+                a.considered = round == 0 ? nullptr : considered;
+                st = launch_enum<Mode::EoEmit>(c, a, pl);
+                a.considered = considered;
+                a.list = nullptr;
+                if (st != SG_OK) break;
+                unsigned long long fill[kEoBuckets + 1];
+                int ovf = 0;
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, kEoBuckets * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned + kEoBuckets, c->d_ctr + kCtrLive, sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, c->stream));
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned + kEoBuckets + 1, lovf, sizeof(int), cudaMemcpyDeviceToHost,
+                                        c->stream));
+                SG_CUDA(cudaStreamSynchronize(c->stream));
+                std::memcpy(fill, c->h_pinned, sizeof(fill));
+                std::memcpy(&ovf, c->h_pinned + kEoBuckets + 1, sizeof(int));
+                live = fill[kEoBuckets];
+                if (live == 0) break;  // no live selected triangle is left
+                if (ovf) {
+                    dfree(c, L);
+                    L = nullptr;
+                    try_list = false;
+                } else {
+                    listed = true;
+                    for (int b = 0; b < kEoBuckets; ++b)
+                        used[b] = (int64_t)std::min<unsigned long long>(fill[b], a.list_cap[b]);
+                    next_bucket = rb;
+                }
+            } else {
+                L = nullptr;
+                set_error("");
+                try_list = false;
+            }
+        }
+        if (!listed) {
+            // ---- enumeration round that bids directly; acceptance from the edges' side
             SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
-            // nothing is considered before the first acceptance: skip the flag reads
             a.considered = round == 0 ? nullptr : considered;
             st = launch_enum<Mode::EoReserve>(c, a, pl);
             a.considered = considered;
             if (st != SG_OK) break;
             st = read_ctr(c, kCtrLive, 1, &live);
             if (st != SG_OK || live == 0) break;
-            if (a.list != nullptr) {
-                unsigned long long fill[kEoBuckets];
-                int ovf = 0;
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, sizeof(fill), cudaMemcpyDeviceToHost, c->stream));
-                SG_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(c->h_pinned) + sizeof(fill), lovf, sizeof(int),
-                                        cudaMemcpyDeviceToHost, c->stream));
-                SG_CUDA(cudaStreamSynchronize(c->stream));
-                std::memcpy(fill, c->h_pinned, sizeof(fill));
-                std::memcpy(&ovf, reinterpret_cast<char *>(c->h_pinned) + sizeof(fill), sizeof(int));
-                if (ovf) {
-                    dfree(c, L);
-                    L = nullptr;
-                } else {
-                    listed = true;
-                    for (int b = 0; b < kEoBuckets; ++b)
-                        used[b] = (int64_t)std::min<unsigned long long>(fill[b], a.list_cap[b]);
-                    const int rb = std::min(round, kEoBuckets - 1);
-                    A = L + ubase[rb];
-                    a_owned = false;
-                    lenA = used[rb];
-                    next_bucket = rb + 1;
-                }
-            }
-            a.list = nullptr;
-        } else {
-            // ---- list round: last round's survivors plus this round's bucket
-            const int64_t fresh = next_bucket < kEoBuckets ? used[next_bucket] : 0;
-            TriRec *B = nullptr;
-            st = dalloc(c, (void **)&B, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec));
-            if (st != SG_OK) break;
-            unsigned long long *out_len = lctr + kEoBuckets;
-            SG_CUDA(cudaMemsetAsync(out_len, 0, sizeof(unsigned long long), c->stream));
-            if (lenA > 0) {
-                SG_LAUNCH(c, "tri_eo_list_reserve");
-                eo_list_reserve_kernel<<<(unsigned)list_blocks(lenA), 256, 0, c->stream>>>(A, lenA, B, out_len, resv,
-                                                                                         considered, theta);
-            }
-            if (fresh > 0) {
-                SG_LAUNCH(c, "tri_eo_list_reserve");
-                eo_list_reserve_kernel<<<(unsigned)list_blocks(fresh), 256, 0, c->stream>>>(
-                    L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta);
-            }
-            if (next_bucket < kEoBuckets) ++next_bucket;
+            // retry the list next round once the live triangles fit it
+            try_list = use_list && (double)live * 1.25 <= (double)list_capacity();
+            ++c->eo_rounds;
+            SG_LAUNCH(c, "tri_eo_accept");
+            if (choice == kChoiceMaxw)
+                eo_accept_kernel<kChoiceMaxw><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            else if (choice == kChoiceMinCount)
+                eo_accept_kernel<kChoiceMinCount><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+            else
+                eo_accept_kernel<kChoiceRandom><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
             SG_CUDA(cudaGetLastError());
-            SG_CUDA(cudaMemcpyAsync(c->h_pinned, out_len, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                    c->stream));
-            SG_CUDA(cudaStreamSynchronize(c->stream));
-            std::memcpy(&live, c->h_pinned, sizeof(live));
-            if (a_owned) dfree(c, A);
-            A = B;
-            a_owned = true;
-            lenA = (int64_t)live;
-            if (live == 0) {
-                if (next_bucket >= kEoBuckets) break;  // no triangle left anywhere
-                continue;                              // nothing bid this round
-            }
+            SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
+            continue;
+        }
+        // ---- list round: last round's survivors plus this round's bucket
+        const int64_t fresh = next_bucket < kEoBuckets ? used[next_bucket] : 0;
+        TriRec *B = nullptr;
+        st = dalloc(c, (void **)&B, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec));
+        if (st != SG_OK) break;
+        unsigned long long *out_len = lctr + kEoBuckets;
+        SG_CUDA(cudaMemsetAsync(out_len, 0, sizeof(unsigned long long), c->stream));
+        if (lenA > 0) {
+            SG_LAUNCH(c, "tri_eo_list_reserve");
+            eo_list_reserve_kernel<<<(unsigned)list_blocks(lenA), 256, 0, c->stream>>>(A, lenA, B, out_len, resv,
+                                                                                     considered, theta);
+        }
+        if (fresh > 0) {
+            SG_LAUNCH(c, "tri_eo_list_reserve");
+            eo_fresh_reserve_kernel<<<(unsigned)list_blocks(fresh), 256, 0, c->stream>>>(
+                L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta, a.colp, a.k0, a.k1);
+        }
+        if (next_bucket < kEoBuckets) ++next_bucket;
+        SG_CUDA(cudaGetLastError());
+        SG_CUDA(cudaMemcpyAsync(c->h_pinned, out_len, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+        SG_CUDA(cudaStreamSynchronize(c->stream));
+        std::memcpy(&live, c->h_pinned, sizeof(live));
+        dfree(c, A);
+        A = B;
+        lenA = (int64_t)live;
+        if (live == 0) {
+            if (next_bucket >= kEoBuckets) break;  // no triangle left anywhere
+            continue;                              // nothing bid this round
         }
         ++c->eo_rounds;
-        if (listed && lenA == 0) continue;  // nothing bid this round (its bucket was empty)
         // ---- accept: triangles holding all three reservations.  Judging from
         // the edge side costs a pass over m reservations plus a binary search
         // per reserved arc; once the list holds at most two triangles per
         // edge, read the list instead
-        if (listed && (double)lenA <= 2.0 * (double)m) {
+        if ((double)lenA <= 2.0 * (double)m) {
             SG_LAUNCH(c, "tri_eo_list_accept");
             const unsigned blocks = (unsigned)list_blocks(lenA);
             if (choice == kChoiceMaxw)
@@ -1265,7 +1361,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         SG_CUDA(cudaGetLastError());
         // ---- reset the reservations for the next round: three scattered
         // writes per listed triangle beat clearing all m words only for short lists
-        if (listed && (double)lenA * 96.0 <= 8.0 * (double)m) {
+        if ((double)lenA * 96.0 <= 8.0 * (double)m) {
             SG_LAUNCH(c, "tri_eo_list_reset");
             eo_list_reset_kernel<<<(unsigned)list_blocks(lenA), 256, 0, c->stream>>>(A, lenA, resv);
         } else {
@@ -1273,7 +1369,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         }
         SG_CUDA(cudaGetLastError());
     }
-    if (a_owned) dfree(c, A);
+    dfree(c, A);
     dfree(c, L);
     dfree(c, lctr);
     dfree(c, considered);
