@@ -69,6 +69,14 @@ def _load():
     lib.orc_cc_count.restype = i64
     lib.orc_mst_weight_units.argtypes = [i64, vp, vp, vp]
     lib.orc_mst_weight_units.restype = i64
+    lib.orc_low_degree.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+    lib.orc_low_degree.restype = i64
+    lib.orc_bfs_levels.argtypes = [i64, vp, vp, i64, vp]
+    lib.orc_bfs_levels.restype = None
+    lib.orc_critical_edges.argtypes = [i64, vp, vp, i64]
+    lib.orc_critical_edges.restype = i64
+    lib.orc_reordered_neighbours.argtypes = [i64, vp, vp, vp, vp]
+    lib.orc_reordered_neighbours.restype = i64
     _lib = lib
     return lib
 
@@ -184,3 +192,37 @@ def divergence(g, h, damping: float = 0.85, iters: int = 50):
     Q, rh = pagerank(h, damping, iters)
     return {"kl_bits": kl_divergence(P, Q), "cc_g": cc_count(g), "cc_h": cc_count(h),
             "pr_residual_g": rg, "pr_residual_h": rh}
+
+
+def low_degree(g):
+    """low_degree (Listing 1): drop every vertex of degree 0 or 1.
+    Returns (n', off', col', new_id) with new_id[v] = -1 for dropped vertices."""
+    n, off, col, _ = _arrays(g)
+    new_id = np.zeros(max(n, 1), dtype=np.int64)
+    off_o = np.zeros(n + 1, dtype=np.int64)
+    col_o = np.zeros(max(col.size, 1), dtype=np.uint32)
+    nnz = C.c_int64()
+    k = int(_load().orc_low_degree(n, _p(off), _p(col), _p(new_id), _p(off_o), _p(col_o), C.addressof(nnz)))
+    return k, off_o[:k + 1].copy(), col_o[:nnz.value].copy(), new_id[:n].copy()
+
+
+def bfs_levels(g, root: int) -> np.ndarray:
+    n, off, col, _ = _arrays(g)
+    lev = np.zeros(max(n, 1), dtype=np.int64)
+    _load().orc_bfs_levels(n, _p(off), _p(col), int(root), _p(lev))
+    return lev[:n]
+
+
+def critical_edges(g, root: int) -> int:
+    """|E_cr| of a BFS from root: edges joining consecutive levels (Sec. 5.3)."""
+    n, off, col, _ = _arrays(g)
+    return int(_load().orc_critical_edges(n, _p(off), _p(col), int(root)))
+
+
+def reordered_neighbours(g, x, y) -> int:
+    """Edges of g whose endpoint order under score x differs from that under y (A_REN count)."""
+    n, off, col, _ = _arrays(g)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    assert x.size == n and y.size == n
+    return int(_load().orc_reordered_neighbours(n, _p(off), _p(col), _p(x), _p(y)))

@@ -43,7 +43,18 @@
  *    smaller endpoint pair; CT is Edge-Once with that choice;
  *  - PageRank (Table 1; output "P", a distribution) uses damping d, uniform
  *    teleport and uniform redistribution of dangling mass; KL divergence is
- *    sum_i P(i) log2(P(i)/Q(i)) (Sec. 5.2.3).
+ *    sum_i P(i) log2(P(i)/Q(i)) (Sec. 5.2.3);
+ *  - the single-vertex kernel low_degree (Listing 1; Sec. 4.4) deletes, in
+ *    one pass over the input degrees, every vertex of degree 0 or 1 with its
+ *    edges; the kept vertices are renumbered in increasing id order;
+ *  - BFS critical edges (Sec. 5.3): for a root r, the tree edges plus the
+ *    edges that could replace a tree edge, i.e. every edge joining BFS
+ *    levels L and L + 1; the metric is |E~_cr| / |E_cr| with both sets taken
+ *    from traversals of G and of the compressed graph from the same root;
+ *  - reordered neighbours A_REN (Sec. 5.2.2): the edges {u,v} of G whose
+ *    endpoint scores change relative order (sign of x_u - x_v differs from
+ *    sign of y_u - y_v, compared in the scores' own float precision), as a
+ *    fraction of m.
  */
 #include <math.h>
 #include <stdint.h>
@@ -614,4 +625,90 @@ int64_t orc_mst_weight_units(int64_t n, const int64_t *off, const uint32_t *col,
     free(parent);
     free(E);
     return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* single-vertex kernel low_degree (Listing 1; Sec. 4.4)                     */
+/* ------------------------------------------------------------------------ */
+/* Keeps the vertices of input degree >= 2 and the edges among them.          */
+/* new_id[v] = new index of a kept vertex, or -1.  Returns the kept vertex     */
+/* count; off_out[n'+1], col_out (arcs with both ends kept, renumbered).       */
+int64_t orc_low_degree(int64_t n, const int64_t *off, const uint32_t *col, int64_t *new_id,
+                       int64_t *off_out, uint32_t *col_out, int64_t *nnz_out)
+{
+    int64_t kept = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t d = off[v + 1] - off[v];
+        new_id[v] = (d == 0 || d == 1) ? -1 : kept++;
+    }
+    int64_t k = 0;
+    off_out[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (new_id[v] < 0) continue;
+        for (int64_t i = off[v]; i < off[v + 1]; ++i)
+            if (new_id[col[i]] >= 0) col_out[k++] = (uint32_t)new_id[col[i]];
+        off_out[new_id[v] + 1] = k;
+    }
+    *nnz_out = k;
+    return kept;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BFS critical edges (Sec. 5.3)                                             */
+/* ------------------------------------------------------------------------ */
+/* BFS levels from root (-1 = unreached), by a plain FIFO queue.               */
+void orc_bfs_levels(int64_t n, const int64_t *off, const uint32_t *col, int64_t root, int64_t *level)
+{
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    if (root < 0 || root >= n) return;
+    int64_t *queue = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t head = 0, tail = 0;
+    level[root] = 0;
+    queue[tail++] = root;
+    while (head < tail) {
+        int64_t x = queue[head++];
+        for (int64_t i = off[x]; i < off[x + 1]; ++i) {
+            uint32_t y = col[i];
+            if (level[y] < 0) {
+                level[y] = level[x] + 1;
+                queue[tail++] = y;
+            }
+        }
+    }
+    free(queue);
+}
+
+/* |E_cr|: undirected edges {x,y} with level(y) = level(x) + 1 -- the tree   */
+/* edges and every edge that could stand in for one.                          */
+int64_t orc_critical_edges(int64_t n, const int64_t *off, const uint32_t *col, int64_t root)
+{
+    int64_t *level = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    orc_bfs_levels(n, off, col, root, level);
+    int64_t cnt = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (level[x] < 0) continue;
+        for (int64_t i = off[x]; i < off[x + 1]; ++i)
+            if (level[col[i]] == level[x] + 1) ++cnt;
+    }
+    free(level);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* reordered neighbours A_REN (Sec. 5.2.2)                                   */
+/* ------------------------------------------------------------------------ */
+static int fsign(float a, float b) { return (a > b) - (a < b); }
+
+/* Number of undirected edges {u,v} of G with sign(x_u - x_v) != sign(y_u - y_v). */
+int64_t orc_reordered_neighbours(int64_t n, const int64_t *off, const uint32_t *col, const float *x,
+                                 const float *y)
+{
+    int64_t cnt = 0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+            uint32_t v = col[i];
+            if ((int64_t)v <= u) continue; /* each edge once */
+            if (fsign(x[u], x[v]) != fsign(y[u], y[v])) ++cnt;
+        }
+    return cnt;
 }

@@ -144,3 +144,19 @@ def tr_eo_mincount(n, E, p, seed):
         considered.update(es)
         D.add(min(es, key=lambda e: (cnt[e], e)))
     return E - D
+
+
+def low_degree(n, E):
+    """Induced subgraph on the vertices of degree >= 2, renumbered by id."""
+    deg = [0] * n
+    for a, b in E:
+        deg[a] += 1
+        deg[b] += 1
+    keep = [v for v in range(n) if deg[v] >= 2]
+    new = {v: i for i, v in enumerate(keep)}
+    return len(keep), {(new[a], new[b]) for a, b in E if a in new and b in new}
+
+
+def reordered(E, x, y):
+    sgn = lambda p, q: int(p > q) - int(p < q)
+    return sum(1 for a, b in E if sgn(x[a], x[b]) != sgn(y[a], y[b]))

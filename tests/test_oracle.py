@@ -534,3 +534,94 @@ def test_ct_is_edge_once_packing():
     assert a == b[1].size
     Hm = sp.csr_matrix((np.ones(b[1].size), b[1].astype(np.int64), b[0]), shape=(g.n, g.n))
     assert connected_components(_scipy(g))[0] == connected_components(Hm)[0]
+
+
+# --------------------------------------------------------------------------
+# single-vertex kernel low_degree (Listing 1; Sec. 4.4)
+# --------------------------------------------------------------------------
+def _low_edges(res):
+    k, off, col, _ = res
+    return brute.edge_set_arrays(k, off, col)
+
+
+@pytest.mark.parametrize("n,q,seed", [(20, 0.08, 1), (40, 0.05, 2), (60, 0.03, 3), (30, 0.3, 4)])
+def test_low_degree_matches_brute_force(n, q, seed):
+    g = gg.gnp(n, q, seed)
+    k, E2 = brute.low_degree(n, brute.edge_set(g))
+    res = oracle.low_degree(g)
+    assert res[0] == k and _low_edges(res) == E2
+    # new ids are increasing in the old ids and -1 exactly for degree <= 1
+    deg = np.diff(g.numpy()[0])
+    nid = res[3]
+    assert np.array_equal(nid < 0, deg <= 1)
+    kept = nid[nid >= 0]
+    assert np.array_equal(kept, np.arange(k))
+
+
+def test_low_degree_closed_forms():
+    # a path loses its two ends and keeps a path of n - 2 vertices
+    k, off, col, _ = oracle.low_degree(gg.path(10))
+    assert k == 8 and col.size == 2 * 7
+    # a star keeps only its centre, now isolated (one pass over input degrees)
+    k, off, col, _ = oracle.low_degree(gg.star(9))
+    assert k == 1 and col.size == 0
+    # cycles and cliques are unchanged
+    for g in (gg.cycle(11), gg.complete(6)):
+        k, off, col, _ = oracle.low_degree(g)
+        o, c, _ = g.numpy()
+        assert k == g.n and np.array_equal(off, o) and np.array_equal(col, c)
+    # isolated vertices and isolated edges vanish
+    k, off, col, _ = oracle.low_degree(gg.disjoint_union(gg.from_edge_list(3, []), gg.path(2), gg.cycle(4)))
+    assert k == 4 and col.size == 8
+
+
+# --------------------------------------------------------------------------
+# BFS critical edges (Sec. 5.3) and reordered neighbours A_REN (Sec. 5.2.2)
+# --------------------------------------------------------------------------
+def _hops(g, root):
+    from scipy.sparse.csgraph import shortest_path
+    d = shortest_path(_scipy(g), unweighted=True, indices=root)
+    return np.where(np.isinf(d), -1, d).astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bfs_levels_match_scipy(seed):
+    g = gg.rmat(10, 8, seed=seed)
+    for root in (0, 5, g.n - 1):
+        assert np.array_equal(oracle.bfs_levels(g, root), _hops(g, root))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_critical_edges_brute_force(seed):
+    g = gg.disjoint_union(gg.rmat(9, 8, seed=seed), gg.cycle(7))
+    for root in (0, 3, g.n - 2):
+        h = _hops(g, root)
+        E = brute.edge_set(g)
+        want = sum(1 for a, b in E if h[a] >= 0 and h[b] >= 0 and abs(h[a] - h[b]) == 1)
+        assert oracle.critical_edges(g, root) == want
+
+
+def test_critical_edges_closed_forms():
+    assert oracle.critical_edges(gg.cycle(10), 0) == 10      # even cycle: every edge
+    assert oracle.critical_edges(gg.cycle(11), 4) == 10      # odd cycle: all but the far edge
+    assert oracle.critical_edges(gg.complete(7), 2) == 6     # clique: only the root's edges
+    assert oracle.critical_edges(gg.path(9), 4) == 8         # a tree: every edge
+    st = gg.star(6)
+    assert oracle.critical_edges(st, 0) == st.m and oracle.critical_edges(st, st.n - 1) == st.m  # a tree
+    # a second component is never reached
+    assert oracle.critical_edges(gg.disjoint_union(gg.path(4), gg.complete(5)), 0) == 3
+
+
+def test_reordered_neighbours():
+    g = gg.rmat(10, 8, seed=3)
+    rng = np.random.default_rng(1)
+    x = rng.random(g.n, dtype=np.float32)
+    y = rng.random(g.n, dtype=np.float32)
+    E = brute.edge_set(g)
+    assert oracle.reordered_neighbours(g, x, y) == brute.reordered(E, x, y)
+    assert oracle.reordered_neighbours(g, x, x) == 0
+    # reversing the order flips every edge whose endpoints differ in score
+    differ = sum(1 for a, b in E if x[a] != x[b])
+    assert oracle.reordered_neighbours(g, x, -x) == differ
+    # a tie on one side and an order on the other counts as reordered
+    assert oracle.reordered_neighbours(g, np.zeros(g.n, np.float32), x) == differ
