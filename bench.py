@@ -183,8 +183,8 @@ def run_ours(args, rank, world):
     ms = ev0.elapsed_time(ev1) / args.steps
     st = ctx.stats()
     kt = {}
-    for name in ("tri_enum", "tri_inarcs", "tri_eo_list_reserve", "tri_eo_list_accept", "tri_eo_accept",
-                 "tri_classify", "compact_orient", "compact_trmask", "row_maps"):
+    for name in ("tri_enum", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve", "tri_eo_list_accept",
+                 "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient", "compact_trmask", "row_maps"):
         kt[name] = ctx.kernel_time(name)
     enum_ms = kt["tri_enum"][0]
     enum_launches = max(kt["tri_enum"][1], 1)

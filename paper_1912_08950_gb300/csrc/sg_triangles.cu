@@ -131,31 +131,39 @@ __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool wa
     if (em.dead) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
     const int mb = want ? max(eo_bucket(r2), min(a.eo_round, kEoBuckets - 1)) : -1;
-    unsigned pend = __ballot_sync(kFull, want);
-    while (pend) {
-        const int b = __shfl_sync(kFull, mb, __ffs(pend) - 1);
+    if (!__any_sync(kFull, want)) return;
+    // lanes of my bucket, and (in lane b) the count of bucket b
+    unsigned mine = 0, cnt_b = 0;
+#pragma unroll
+    for (int b = 0; b < kEoBuckets; ++b) {
         const unsigned bm = __ballot_sync(kFull, mb == b);
-        pend &= ~bm;
-        const unsigned cnt = (unsigned)__popc(bm);
-        unsigned long long cur = __shfl_sync(kFull, em.cur, b);
-        const unsigned long long end = __shfl_sync(kFull, em.cur, 8 + b);
-        if (end - cur < cnt) {
-            emit_seal(a, cur, end);
-            const unsigned long long chunk = (unsigned long long)eo_chunk(b);
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(a.list_ctr + b, chunk);
-            base = __shfl_sync(kFull, base, 0);
-            if (base + chunk > a.list_cap[b]) {
-                if (lane == 0) atomicExch(a.list_overflow, 1);
-                em.dead = true;
-                return;
-            }
-            cur = a.list_base[b] + base;
-            if (lane == 8 + b) em.cur = cur + chunk;
-        }
-        if (mb == b) a.list[cur + __popc(bm & lanemask_lt())] = rec;
-        if (lane == b) em.cur = cur + cnt;
+        if (mb == b) mine = bm;
+        if (lane == b) cnt_b = (unsigned)__popc(bm);
     }
+    // a bucket whose chunk is too short for this group claims a new chunk (rare)
+    const unsigned long long end_b = __shfl_down_sync(kFull, em.cur, 8);  // lane b: end of bucket b
+    unsigned need = __ballot_sync(kFull, lane < kEoBuckets && end_b - em.cur < cnt_b);
+    while (need) {
+        const int b = __ffs(need) - 1;
+        need &= need - 1;
+        const unsigned long long cur = __shfl_sync(kFull, em.cur, b);
+        const unsigned long long end = __shfl_sync(kFull, em.cur, 8 + b);
+        emit_seal(a, cur, end);
+        const unsigned long long chunk = (unsigned long long)eo_chunk(b);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.list_ctr + b, chunk);
+        base = __shfl_sync(kFull, base, 0);
+        if (base + chunk > a.list_cap[b]) {
+            if (lane == 0) atomicExch(a.list_overflow, 1);
+            em.dead = true;
+            return;
+        }
+        if (lane == b) em.cur = a.list_base[b] + base;
+        if (lane == 8 + b) em.cur = a.list_base[b] + base + chunk;
+    }
+    const unsigned long long cur = __shfl_sync(kFull, em.cur, mb < 0 ? 0 : mb);
+    if (want) a.list[cur + __popc(mine & lanemask_lt())] = rec;
+    if (lane < kEoBuckets) em.cur += cnt_b;
 }
 
 // Per-warp ring of found triangles, waiting to be decided 32 at a time.  The
@@ -387,22 +395,27 @@ __device__ __forceinline__ bool table_find(const Table &tb, int sh, int stash_n,
     return false;
 }
 
+// First two 32-element slabs of the list colp[ov, ov + dv) (kEmpty past its end).
+__device__ __forceinline__ void first_slabs(const TriArgs &a, uint32_t ov, int dv, uint32_t &na, uint32_t &nb) {
+    const int lane = threadIdx.x & 31;
+    na = lane < dv ? __ldg(a.colp + ov + lane) : kEmpty;
+    nb = lane + 32 < dv ? __ldg(a.colp + ov + lane + 32) : kEmpty;
+}
+
 // Stream N+(v) = colp[ov, ov + dv) through the table of N+(u): two 32-element
-// slabs per iteration, the next two loaded while these are probed (up to four
-// loads in flight per lane); hits go to the queue.
+// slabs per iteration, the next two loaded while these are probed.  The
+// caller passes the first two slabs (na, nb) already loaded, so that it can
+// issue them before finishing the previous list.  Hits go to the queue.
 template <Mode M>
 __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
                                            uint32_t u, uint32_t iuv, uint32_t ou, uint32_t v, uint32_t ov, int dv,
-                                           HitQueue &q, QState &qs, unsigned &live, unsigned long long &tris,
-                                           Emitter &em) {
+                                           uint32_t na, uint32_t nb, HitQueue &q, QState &qs, unsigned &live,
+                                           unsigned long long &tris, Emitter &em) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const uint32_t *lst = a.colp + ov;
     const int sh = 32 - log_slots;
     unsigned huv = 0;  // EdgeCount: triangles found on the arc u->v
-    uint32_t na = kEmpty, nb = kEmpty;
-    if (lane < dv) na = __ldg(lst + lane);
-    if (lane + 32 < dv) nb = __ldg(lst + lane + 32);
     for (int j0 = 0; j0 < dv; j0 += 64) {
         const int ja = j0 + lane, jb = ja + 32;
         const uint32_t wa = na, wb = nb;
@@ -476,13 +489,18 @@ __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &t
         sd = (kEdgeOnce<M> && a.considered != nullptr && a.considered[se])
                  ? 0 : (int)(__ldg(a.offp + sv + 1) - b0);
     }
+    // the next list's first slabs load while the current one is probed
+    uint32_t pa, pb;
+    first_slabs(a, __shfl_sync(kFull, so, 0), __shfl_sync(kFull, sd, 0), pa, pb);
     for (int i = 0; i < cnt; ++i) {
         const uint32_t v = __shfl_sync(kFull, sv, i);
         const uint32_t ov = __shfl_sync(kFull, so, i);
         const uint32_t e = __shfl_sync(kFull, se, i);
         const int dv = __shfl_sync(kFull, sd, i);
+        const uint32_t ca = pa, cb = pb;
+        if (i + 1 < cnt) first_slabs(a, __shfl_sync(kFull, so, i + 1), __shfl_sync(kFull, sd, i + 1), pa, pb);
         if (lane == 0 && count_probes) probes += (unsigned)dv;
-        probe_list<M>(a, tb, log_slots, stash_n, u, e, tbase, v, ov, dv, q, qs, live, tris, em);
+        probe_list<M>(a, tb, log_slots, stash_n, u, e, tbase, v, ov, dv, ca, cb, q, qs, live, tris, em);
     }
 }
 
@@ -602,8 +620,10 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                     }
                     // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
                     if (lane == 0 && c0 == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, tb, log_slots, stash_n, u, e, ou + (uint32_t)c0, v, ov, dv, q, qst, live,
-                                  tris, em);
+                    uint32_t ca, cb;
+                    first_slabs(a, ov, dv, ca, cb);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, e, ou + (uint32_t)c0, v, ov, dv, ca, cb, q, qst,
+                                  live, tris, em);
                 }
                 __syncthreads();  // the table is rebuilt for the next chunk or vertex
             }
@@ -665,14 +685,22 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                 }
                 __syncwarp();
                 const int stash_n = min(*tb.stash_n, kStash);
+                uint32_t pa, pb;  // first slabs of the next list, loading ahead
+                first_slabs(a, __shfl_sync(kFull, o0, 0), __shfl_sync(kFull, d0, 0), pa, pb);
                 for (int i = 0; i < d; ++i) {
                     const bool lo = i < 32;
                     const uint32_t v = __shfl_sync(kFull, lo ? n0 : n1, i & 31);
                     const uint32_t ov = __shfl_sync(kFull, lo ? o0 : o1, i & 31);
                     const int dv = __shfl_sync(kFull, lo ? d0 : d1, i & 31);
+                    const uint32_t ca = pa, cb = pb;
+                    if (i + 1 < d) {
+                        const bool ln = i + 1 < 32;
+                        first_slabs(a, __shfl_sync(kFull, ln ? o0 : o1, (i + 1) & 31),
+                                    __shfl_sync(kFull, ln ? d0 : d1, (i + 1) & 31), pa, pb);
+                    }
                     if (lane == 0) probes += (unsigned)dv;
-                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, q, qst, live,
-                                  tris, em);
+                    probe_list<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)i, ou, v, ov, dv, ca, cb, q, qst,
+                                  live, tris, em);
                 }
                 // in-arcs v->u with d+(v) < d+(u), in groups of 32
                 const int64_t ib = nin > 0 ? __ldg(a.offs + u) - (int64_t)ou : 0;
@@ -1316,7 +1344,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                                                                                      considered, theta);
         }
         if (fresh > 0) {
-            SG_LAUNCH(c, "tri_eo_list_reserve");
+            SG_LAUNCH(c, "tri_eo_fresh_reserve");
             eo_fresh_reserve_kernel<<<(unsigned)list_blocks(fresh), 256, 0, c->stream>>>(
                 L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta, a.colp, a.k0, a.k1);
         }
