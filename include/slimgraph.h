@@ -241,6 +241,59 @@ sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out);
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out,
                      int64_t *max_out_degree, int64_t *triangles_out, int64_t *head_arcs_out);
 
+/* ------------------------------------------ accuracy metrics (Sec. 5) */
+
+/* BFS levels from `root` (Sec. 5.3): levels is a device int32[n] receiving
+ * the hop distance of every vertex, -1 where root does not reach.  Levels are
+ * unique, so the result does not depend on traversal order.
+ * Errors: SG_ERR_INVALID_ARG (root outside [0, n)), SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_bfs_levels(sg_ctx *ctx, const sg_graph *g, int64_t root, int32_t *levels);
+/* |E_cr| of a BFS from `root` (Sec. 5.3): the tree edges plus every edge that
+ * could replace one, i.e. the undirected edges joining levels L and L + 1. */
+sg_status sg_critical_edges(sg_ctx *ctx, const sg_graph *g, int64_t root, int64_t *count_out);
+/* The numerator of A_REN (Sec. 5.2.2): the number of undirected edges {u,v}
+ * of g whose endpoint order under the device score vector x (float[n])
+ * differs from their order under y: sign(x_u - x_v) != sign(y_u - y_v),
+ * compared in float. */
+sg_status sg_reordered_neighbours(sg_ctx *ctx, const sg_graph *g, const float *x, const float *y,
+                                  int64_t *count_out);
+/* Triangles through every vertex (the per-vertex output "TC" of Table 1):
+ * counts is a device uint64[n], overwritten. */
+sg_status sg_vertex_triangle_counts(sg_ctx *ctx, const sg_graph *g, uint64_t *counts);
+
+/* The vertex-level accuracy metrics of one compression G -> H (same n). */
+typedef struct sg_accuracy_result {
+    int64_t m_g;               /* undirected edges of G: the A_REN denominator */
+    int64_t pr_reordered;      /* edges of G whose PageRank order differs in H (FP32 PageRank) */
+    double pr_aren;            /* pr_reordered / m_g */
+    int64_t tc_reordered;      /* the same for the per-vertex triangle counts */
+    double tc_aren;            /* tc_reordered / m_g */
+    int64_t root;              /* the BFS root used */
+    int64_t critical_g;        /* |E_cr| of G */
+    int64_t critical_h;        /* |E~_cr|: critical edges of H for the same root */
+    double critical_fraction;  /* critical_h / critical_g (1 when critical_g = 0) */
+} sg_accuracy_result;
+/* PageRank (damping, iters as in sg_divergence) and per-vertex triangle
+ * counts of G and H with their A_REN, and the BFS critical-edge fraction
+ * |E~_cr| / |E_cr| from `root` (root < 0: the vertex of largest degree in
+ * G, the smallest id on ties).
+ * Errors: SG_ERR_INVALID_ARG (n differs, bad PageRank parameters, root >= n),
+ * SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_accuracy(sg_ctx *ctx, const sg_graph *g, const sg_graph *h, float damping, int iters, int64_t root,
+                      sg_accuracy_result *out);
+
+/* ------------------------------------------------ single-vertex kernel */
+
+/* low_degree(V v) (Listing 1; Sec. 4.4): H is G without its vertices of
+ * degree 0 or 1 -- decided in one pass over the input degrees -- and without
+ * their edges; the kept vertices are renumbered 0..n'-1 in increasing order
+ * of their ids in G, so H has n' <= n vertices.  Weights of kept edges are
+ * carried.  new_to_old: a device uint32 array with room for n entries (or
+ * NULL); entry i < n' receives the id in G of H's vertex i.  *out receives a
+ * new graph owned by the library (release it with sg_graph_free).
+ * Errors: SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg_graph **out);
+
 /* ------------------------------------------------- no-allocation variant */
 
 /* Uniform edge sampling (SG_UNIFORM) that allocates no device memory.  The

@@ -77,6 +77,10 @@ def _load():
     lib.orc_critical_edges.restype = i64
     lib.orc_reordered_neighbours.argtypes = [i64, vp, vp, vp, vp]
     lib.orc_reordered_neighbours.restype = i64
+    lib.orc_vertex_triangle_counts.argtypes = [i64, vp, vp, vp]
+    lib.orc_vertex_triangle_counts.restype = None
+    lib.orc_reordered_neighbours_i64.argtypes = [i64, vp, vp, vp, vp]
+    lib.orc_reordered_neighbours_i64.restype = i64
     _lib = lib
     return lib
 
@@ -220,9 +224,23 @@ def critical_edges(g, root: int) -> int:
 
 
 def reordered_neighbours(g, x, y) -> int:
-    """Edges of g whose endpoint order under score x differs from that under y (A_REN count)."""
+    """Edges of g whose endpoint order under score x differs from that under y (A_REN count).
+    Float32 scores are compared in float32; int64 scores exactly."""
     n, off, col, _ = _arrays(g)
+    if np.asarray(x).dtype.kind in "iu":
+        x = np.ascontiguousarray(x, dtype=np.int64)
+        y = np.ascontiguousarray(y, dtype=np.int64)
+        assert x.size == n and y.size == n
+        return int(_load().orc_reordered_neighbours_i64(n, _p(off), _p(col), _p(x), _p(y)))
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.ascontiguousarray(y, dtype=np.float32)
     assert x.size == n and y.size == n
     return int(_load().orc_reordered_neighbours(n, _p(off), _p(col), _p(x), _p(y)))
+
+
+def vertex_triangle_counts(g) -> np.ndarray:
+    """Triangles through every vertex."""
+    n, off, col, _ = _arrays(g)
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    _load().orc_vertex_triangle_counts(n, _p(off), _p(col), _p(out))
+    return out[:n]

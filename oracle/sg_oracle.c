@@ -712,3 +712,33 @@ int64_t orc_reordered_neighbours(int64_t n, const int64_t *off, const uint32_t *
         }
     return cnt;
 }
+
+/* Triangles through every vertex (the per-vertex output "TC" of Table 1). */
+static void vtc_cb(uint32_t a, uint32_t b, uint32_t c, int64_t eab, int64_t eac, int64_t ebc, void *ctx)
+{
+    (void)eab; (void)eac; (void)ebc;
+    int64_t *t = (int64_t *)ctx;
+    ++t[a]; ++t[b]; ++t[c];
+}
+
+void orc_vertex_triangle_counts(int64_t n, const int64_t *off, const uint32_t *col, int64_t *out)
+{
+    for (int64_t v = 0; v < n; ++v) out[v] = 0;
+    for_each_triangle(n, off, col, vtc_cb, out);
+}
+
+static int isign(int64_t a, int64_t b) { return (a > b) - (a < b); }
+
+/* A_REN count for integer scores (exact). */
+int64_t orc_reordered_neighbours_i64(int64_t n, const int64_t *off, const uint32_t *col, const int64_t *x,
+                                     const int64_t *y)
+{
+    int64_t cnt = 0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+            uint32_t v = col[i];
+            if ((int64_t)v <= u) continue;
+            if (isign(x[u], x[v]) != isign(y[u], y[v])) ++cnt;
+        }
+    return cnt;
+}

@@ -50,6 +50,12 @@ class DivResult(C.Structure):
                 ("m_h", C.c_int64), ("pr_residual_g", C.c_double), ("pr_residual_h", C.c_double)]
 
 
+class AccuracyResult(C.Structure):
+    _fields_ = [("m_g", C.c_int64), ("pr_reordered", C.c_int64), ("pr_aren", C.c_double),
+                ("tc_reordered", C.c_int64), ("tc_aren", C.c_double), ("root", C.c_int64),
+                ("critical_g", C.c_int64), ("critical_h", C.c_int64), ("critical_fraction", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("probes", C.c_uint64), ("triangles", C.c_uint64),
                 ("eo_rounds", C.c_uint64)]
@@ -83,6 +89,12 @@ _SIGS = {
                       C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                    C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "sg_low_degree": [_vp, _vp, _vp, _PP],
+    "sg_bfs_levels": [_vp, _vp, _i64, _vp],
+    "sg_critical_edges": [_vp, _vp, _i64, C.POINTER(C.c_int64)],
+    "sg_reordered_neighbours": [_vp, _vp, _vp, _vp, C.POINTER(C.c_int64)],
+    "sg_vertex_triangle_counts": [_vp, _vp, _vp],
+    "sg_accuracy": [_vp, _vp, _vp, _flt, _int, _i64, C.POINTER(AccuracyResult)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -268,6 +280,24 @@ def compress(g: Graph, kernel, p: float, seed: int, want_weights: bool = False) 
     return Graph(g.ctx, h)
 
 
+def low_degree(g: Graph, return_map: bool = False):
+    """low_degree(V v) (Listing 1): H = G without its vertices of degree 0 or 1,
+    renumbered in id order.  With return_map, also the device uint32 tensor
+    mapping H's vertex ids to G's."""
+    import torch
+
+    nto = torch.empty(max(g.n, 1), dtype=torch.int32, device=f"cuda:{g.ctx.device}") if return_map else None
+    if nto is not None:
+        torch.cuda.current_stream(g.ctx.device).synchronize()
+    h = C.c_void_p()
+    _check(_lib.sg_low_degree(g.ctx.handle, g.handle, None if nto is None else nto.data_ptr(), C.byref(h)))
+    H = Graph(g.ctx, h)
+    if nto is None:
+        return H
+    g.ctx.synchronize()
+    return H, nto[:H.n]
+
+
 def divergence(g: Graph, h: Graph, damping: float = 0.85, iters: int = 50) -> dict:
     r = DivResult()
     _check(_lib.sg_divergence(g.ctx.handle, g.handle, h.handle, float(damping), int(iters), C.byref(r)))
@@ -282,6 +312,66 @@ def pagerank(g: Graph, damping: float = 0.85, iters: int = 50):
     r = C.c_double()
     _check(_lib.sg_pagerank(g.ctx.handle, g.handle, float(damping), int(iters), x.data_ptr(), C.byref(r)))
     return x[:g.n], r.value
+
+
+def _dev_tensor(g: Graph, n: int, dtype):
+    import torch
+
+    t = torch.empty(max(n, 1), dtype=dtype, device=torch.device("cuda", g.ctx.device))
+    g.ctx.torch_stream.wait_stream(torch.cuda.current_stream(g.ctx.device))
+    return t
+
+
+def _publish(ctx: Context):
+    import torch
+
+    torch.cuda.current_stream(ctx.device).wait_stream(ctx.torch_stream)
+
+
+def bfs_levels(g: Graph, root: int):
+    """Hop distance of every vertex from root (int32 CUDA tensor, -1 = unreached; Sec. 5.3)."""
+    import torch
+
+    lev = _dev_tensor(g, g.n, torch.int32)
+    _check(_lib.sg_bfs_levels(g.ctx.handle, g.handle, int(root), lev.data_ptr()))
+    _publish(g.ctx)
+    return lev[:g.n]
+
+
+def critical_edges(g: Graph, root: int) -> int:
+    """|E_cr| of a BFS from root: the edges joining consecutive levels (Sec. 5.3)."""
+    out = C.c_int64()
+    _check(_lib.sg_critical_edges(g.ctx.handle, g.handle, int(root), C.byref(out)))
+    return out.value
+
+
+def reordered_neighbours(g: Graph, x, y) -> int:
+    """Edges of g whose endpoint order under the float32 CUDA score x differs under y (A_REN count)."""
+    import torch
+
+    assert x.dtype == torch.float32 and y.dtype == torch.float32 and x.numel() == g.n and y.numel() == g.n
+    x, y = x.contiguous(), y.contiguous()
+    g.ctx.torch_stream.wait_stream(torch.cuda.current_stream(g.ctx.device))
+    out = C.c_int64()
+    _check(_lib.sg_reordered_neighbours(g.ctx.handle, g.handle, x.data_ptr(), y.data_ptr(), C.byref(out)))
+    return out.value
+
+
+def vertex_triangle_counts(g: Graph):
+    """Triangles through every vertex (int64 CUDA tensor holding the uint64 counts)."""
+    import torch
+
+    t = _dev_tensor(g, g.n, torch.int64)
+    _check(_lib.sg_vertex_triangle_counts(g.ctx.handle, g.handle, t.data_ptr()))
+    _publish(g.ctx)
+    return t[:g.n]
+
+
+def accuracy(g: Graph, h: Graph, damping: float = 0.85, iters: int = 50, root: int = -1) -> dict:
+    """A_REN of PageRank and of per-vertex triangle counts, and the BFS critical-edge fraction (Sec. 5)."""
+    r = AccuracyResult()
+    _check(_lib.sg_accuracy(g.ctx.handle, g.handle, h.handle, float(damping), int(iters), int(root), C.byref(r)))
+    return {k: getattr(r, k) for k, _ in AccuracyResult._fields_}
 
 
 def kl_divergence(ctx: Context, P, Q) -> float:

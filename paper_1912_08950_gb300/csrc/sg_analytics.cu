@@ -377,6 +377,261 @@ sg_status cc_count(Ctx *c, const Graph *g, int64_t *count, uint32_t *labels) {
     return SG_OK;
 }
 
+// ------------------------------------------------------ BFS levels (Sec. 5.3)
+// Level-synchronous BFS over an int32 level array (-1 = unreached).  Each step
+// is top-down (the frontier pushes L + 1 into unreached neighbours) or, once
+// the frontier holds more than n/32 vertices, bottom-up (every unreached
+// vertex looks for a neighbour on level L) -- the direction switch of Beamer,
+// Asanovic and Patterson (SC'12).  Concurrent writes of L + 1 to one entry
+// store the same value, so no atomics are needed; levels are unique, whatever
+// the order of the writes.
+__global__ void __launch_bounds__(256) bfs_top_down_kernel(const int64_t *__restrict__ off,
+                                                           const uint32_t *__restrict__ col, int64_t n,
+                                                           int *level, int L) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nw * 32) {
+        const int64_t v = base + lane;
+        unsigned fm = __ballot_sync(kFull, v < n && level[v] == L);
+        while (fm) {
+            const int src = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int64_t x = base + src;
+            const int64_t o = __ldg(off + x), d = __ldg(off + x + 1) - o;
+            for (int64_t i = lane; i < d; i += 32) {
+                const uint32_t y = __ldg(col + o + i);
+                if (level[y] < 0) level[y] = L + 1;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) bfs_bottom_up_kernel(const int64_t *__restrict__ off,
+                                                            const uint32_t *__restrict__ col, int64_t n,
+                                                            int *level, int L) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (level[v] >= 0) continue;
+        const int64_t e = __ldg(off + v + 1);
+        for (int64_t i = __ldg(off + v); i < e; ++i)
+            if (level[__ldg(col + i)] == L) {
+                level[v] = L + 1;
+                break;
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) count_level_kernel(const int *__restrict__ level, int64_t n, int L,
+                                                          unsigned long long *cnt) {
+    unsigned long long k = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) k += level[v] == L;
+    k = warp_sum(k);
+    if ((threadIdx.x & 31) == 0 && k) atomicAdd(cnt, k);
+}
+
+__global__ void set_root_kernel(int *level, int64_t root) { level[root] = 0; }
+
+sg_status bfs_levels(Ctx *c, const Graph *g, int64_t root, int *level) {
+    if (g->n == 0) return SG_OK;
+    SG_CUDA(cudaMemsetAsync(level, 0xFF, sizeof(int) * (size_t)g->n, c->stream));
+    if (root < 0 || root >= g->n) return SG_OK;  // nothing is reached
+    {
+        SG_LAUNCH(c, "bfs_root");
+        set_root_kernel<<<1, 1, 0, c->stream>>>(level, root);
+    }
+    unsigned long long *cnt = nullptr;
+    sg_status st = dalloc(c, (void **)&cnt, sizeof(unsigned long long));
+    if (st != SG_OK) return st;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 8));
+    unsigned long long frontier = 1;
+    for (int L = 0; frontier > 0 && st == SG_OK; ++L) {
+        if (L > (int)std::min<int64_t>(g->n, INT32_MAX - 1)) { st = fail(SG_ERR_CUDA, "BFS did not terminate"); break; }
+        if (frontier * 32 > (unsigned long long)g->n) {
+            SG_LAUNCH(c, "bfs_step");
+            bfs_bottom_up_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->col, g->n, level, L);
+        } else {
+            SG_LAUNCH(c, "bfs_step");
+            bfs_top_down_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->col, g->n, level, L);
+        }
+        if (cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+            break;
+        }
+        {
+            SG_LAUNCH(c, "bfs_count");
+            count_level_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(level, g->n, L + 1, cnt);
+        }
+        if (cudaGetLastError() != cudaSuccess) { st = fail(SG_ERR_CUDA, "BFS launch"); break; }
+        if (cudaMemcpyAsync(c->h_pinned, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "BFS frontier count");
+            break;
+        }
+        frontier = c->h_pinned[0];
+    }
+    dfree(c, cnt);
+    return st;
+}
+
+// |E_cr| (Sec. 5.3): undirected edges joining BFS levels L and L + 1, each
+// counted once from its lower end.
+__global__ void __launch_bounds__(256) critical_kernel(const int64_t *__restrict__ off,
+                                                       const uint32_t *__restrict__ col, int64_t n,
+                                                       const int *__restrict__ level, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long k = 0;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nw * 32) {
+        const int64_t v = base + lane;
+        const int lv = v < n ? __ldg(level + v) : -1;
+        unsigned fm = __ballot_sync(kFull, lv >= 0);
+        while (fm) {
+            const int src = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int64_t x = base + src;
+            const int lx = __shfl_sync(kFull, lv, src);
+            const int64_t o = __ldg(off + x), d = __ldg(off + x + 1) - o;
+            for (int64_t i = lane; i < d; i += 32) k += __ldg(level + __ldg(col + o + i)) == lx + 1;
+        }
+    }
+    k = warp_sum(k);
+    if (lane == 0 && k) atomicAdd(cnt, k);
+}
+
+sg_status critical_edges(Ctx *c, const Graph *g, int64_t root, int64_t *count) {
+    *count = 0;
+    if (g->n == 0) return SG_OK;
+    int *level = nullptr;
+    unsigned long long *cnt = nullptr;
+    sg_status st = dalloc(c, (void **)&level, sizeof(int) * (size_t)g->n);
+    if (st == SG_OK) st = dalloc(c, (void **)&cnt, sizeof(unsigned long long));
+    if (st == SG_OK) st = bfs_levels(c, g, root, level);
+    if (st == SG_OK && cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    if (st == SG_OK) {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 8));
+        SG_LAUNCH(c, "critical_edges");
+        critical_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->col, g->n, level, cnt);
+        if (cudaGetLastError() != cudaSuccess) st = fail(SG_ERR_CUDA, "critical_edges launch");
+    }
+    if (st == SG_OK) {
+        if (cudaMemcpyAsync(c->h_pinned, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "critical_edges read");
+        else
+            *count = (int64_t)c->h_pinned[0];
+    }
+    dfree(c, level);
+    dfree(c, cnt);
+    return st;
+}
+
+// ----------------------------------------------- A_REN (Sec. 5.2.2)
+// Edges {u,v} of G (each once, from its smaller end) whose endpoint scores
+// change relative order: sign(x_u - x_v) != sign(y_u - y_v), compared in the
+// scores' own type.
+template <typename T>
+__device__ __forceinline__ int order_sign(T a, T b) {
+    return (int)(a > b) - (int)(a < b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) reordered_kernel(const int64_t *__restrict__ off,
+                                                        const uint32_t *__restrict__ col, int64_t n,
+                                                        const T *__restrict__ x, const T *__restrict__ y,
+                                                        unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long k = 0;
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += nw) {
+        const int64_t o = __ldg(off + u), d = __ldg(off + u + 1) - o;
+        const T xu = x[u], yu = y[u];
+        for (int64_t i = lane; i < d; i += 32) {
+            const uint32_t v = __ldg(col + o + i);
+            if ((int64_t)v > u) k += order_sign(xu, x[v]) != order_sign(yu, y[v]);
+        }
+    }
+    k = warp_sum(k);
+    if (lane == 0 && k) atomicAdd(cnt, k);
+}
+
+template <typename T>
+sg_status reordered_neighbours(Ctx *c, const Graph *g, const T *x, const T *y, int64_t *count) {
+    *count = 0;
+    if (g->n == 0) return SG_OK;
+    unsigned long long *cnt = nullptr;
+    sg_status st = dalloc(c, (void **)&cnt, sizeof(unsigned long long));
+    if (st == SG_OK && cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    if (st == SG_OK) {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, (int64_t)c->num_sms * 8));
+        SG_LAUNCH(c, "reordered");
+        reordered_kernel<T><<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->col, g->n, x, y, cnt);
+        if (cudaGetLastError() != cudaSuccess) st = fail(SG_ERR_CUDA, "reordered launch");
+    }
+    if (st == SG_OK) {
+        if (cudaMemcpyAsync(c->h_pinned, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "reordered read");
+        else
+            *count = (int64_t)c->h_pinned[0];
+    }
+    dfree(c, cnt);
+    return st;
+}
+template sg_status reordered_neighbours<float>(Ctx *, const Graph *, const float *, const float *, int64_t *);
+template sg_status reordered_neighbours<unsigned long long>(Ctx *, const Graph *, const unsigned long long *,
+                                                            const unsigned long long *, int64_t *);
+
+// The vertex of largest degree (smallest id on ties): the default BFS root.
+__global__ void max_degree_kernel(const int64_t *__restrict__ off, int64_t n, unsigned long long *best) {
+    unsigned long long b = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long d = (unsigned long long)(off[v + 1] - off[v]);
+        const unsigned long long key = (d << 32) | (0xFFFFFFFFull - (unsigned long long)v);
+        b = key > b ? key : b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, b, o);
+        b = t > b ? t : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+sg_status max_degree_vertex(Ctx *c, const Graph *g, int64_t *v) {
+    *v = -1;
+    if (g->n == 0) return SG_OK;
+    unsigned long long *best = nullptr;
+    sg_status st = dalloc(c, (void **)&best, sizeof(unsigned long long));
+    if (st == SG_OK && cudaMemsetAsync(best, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    if (st == SG_OK) {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 8));
+        SG_LAUNCH(c, "max_degree");
+        max_degree_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->n, best);
+        if (cudaGetLastError() != cudaSuccess) st = fail(SG_ERR_CUDA, "max_degree launch");
+    }
+    if (st == SG_OK) {
+        if (cudaMemcpyAsync(c->h_pinned, best, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "max_degree read");
+        else
+            *v = (int64_t)(0xFFFFFFFFull - (c->h_pinned[0] & 0xFFFFFFFFull));
+    }
+    dfree(c, best);
+    return st;
+}
+
+
 // ---------------------------------------------------------------- validate
 __global__ void validate_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ col, int64_t n,
                                 int64_t nnz, int *err) {

@@ -488,6 +488,119 @@ sg_status sg_divergence(sg_ctx *ctx, const sg_graph *g, const sg_graph *h, float
     return st;
 }
 
+sg_status sg_bfs_levels(sg_ctx *ctx, const sg_graph *g, int64_t root, int32_t *levels) {
+    if (!ctx || !g || (!levels && g->n > 0)) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    if (root < 0 || root >= g->n) return fail(SG_ERR_INVALID_ARG, "root out of range");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st == SG_OK) st = bfs_levels(c, G_(g), root, reinterpret_cast<int *>(levels));
+    if (st == SG_OK) st = check_device_error(c);
+    return st;
+}
+
+sg_status sg_critical_edges(sg_ctx *ctx, const sg_graph *g, int64_t root, int64_t *count_out) {
+    if (!ctx || !g || !count_out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    if (root < 0 || root >= g->n) return fail(SG_ERR_INVALID_ARG, "root out of range");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st == SG_OK) st = critical_edges(c, G_(g), root, count_out);
+    if (st == SG_OK) st = check_device_error(c);
+    return st;
+}
+
+sg_status sg_reordered_neighbours(sg_ctx *ctx, const sg_graph *g, const float *x, const float *y,
+                                  int64_t *count_out) {
+    if (!ctx || !g || !count_out || ((!x || !y) && g->n > 0)) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st == SG_OK) st = reordered_neighbours<float>(c, G_(g), x, y, count_out);
+    if (st == SG_OK) st = check_device_error(c);
+    return st;
+}
+
+sg_status sg_vertex_triangle_counts(sg_ctx *ctx, const sg_graph *g, uint64_t *counts) {
+    if (!ctx || !g || (!counts && g->n > 0)) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st != SG_OK) return st;
+    RowMaps rm;
+    Oriented o;
+    st = build_row_maps(c, G_(g), &rm);
+    if (st == SG_OK) st = orient(c, G_(g), rm, false, &o);
+    if (st == SG_OK) st = tr_vertex_counts(c, G_(g), o, reinterpret_cast<unsigned long long *>(counts));
+    if (st == SG_OK) st = check_device_error(c);
+    free_oriented(c, &o);
+    free_row_maps(c, &rm);
+    return st;
+}
+
+sg_status sg_accuracy(sg_ctx *ctx, const sg_graph *g, const sg_graph *h, float damping, int iters, int64_t root,
+                      sg_accuracy_result *out) {
+    if (!ctx || !g || !h || !out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    if (g->n != h->n) return fail(SG_ERR_INVALID_ARG, "G and H must have the same vertex count");
+    if (iters < 1 || !(damping >= 0.f && damping <= 1.f)) return fail(SG_ERR_INVALID_ARG, "bad PageRank parameters");
+    if (root >= g->n) return fail(SG_ERR_INVALID_ARG, "root out of range");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st != SG_OK) return st;
+    *out = sg_accuracy_result{};
+    out->m_g = g->nnz / 2;
+    const size_t n1 = (size_t)std::max<int64_t>(g->n, 1);
+    float *P = nullptr, *Q = nullptr;
+    unsigned long long *tg = nullptr, *th = nullptr;
+    double rg = 0.0, rh = 0.0;
+    st = dalloc(c, (void **)&P, sizeof(float) * n1);
+    if (st == SG_OK) st = dalloc(c, (void **)&Q, sizeof(float) * n1);
+    if (st == SG_OK) st = dalloc(c, (void **)&tg, sizeof(unsigned long long) * n1);
+    if (st == SG_OK) st = dalloc(c, (void **)&th, sizeof(unsigned long long) * n1);
+    // A_REN of the PageRank vectors
+    if (st == SG_OK) st = pagerank(c, G_(g), damping, iters, P, &rg);
+    if (st == SG_OK) st = pagerank(c, G_(h), damping, iters, Q, &rh);
+    if (st == SG_OK) st = reordered_neighbours<float>(c, G_(g), P, Q, &out->pr_reordered);
+    // A_REN of the per-vertex triangle counts
+    if (st == SG_OK) st = sg_vertex_triangle_counts(ctx, g, reinterpret_cast<uint64_t *>(tg));
+    if (st == SG_OK) st = sg_vertex_triangle_counts(ctx, h, reinterpret_cast<uint64_t *>(th));
+    if (st == SG_OK) st = reordered_neighbours<unsigned long long>(c, G_(g), tg, th, &out->tc_reordered);
+    // BFS critical edges from the same root
+    if (st == SG_OK && root < 0) st = max_degree_vertex(c, G_(g), &root);
+    out->root = root;
+    if (st == SG_OK && g->n > 0) st = critical_edges(c, G_(g), root, &out->critical_g);
+    if (st == SG_OK && g->n > 0) st = critical_edges(c, G_(h), root, &out->critical_h);
+    if (st == SG_OK) st = check_device_error(c);
+    const double m = (double)out->m_g;
+    out->pr_aren = m > 0 ? (double)out->pr_reordered / m : 0.0;
+    out->tc_aren = m > 0 ? (double)out->tc_reordered / m : 0.0;
+    out->critical_fraction = out->critical_g > 0 ? (double)out->critical_h / (double)out->critical_g : 1.0;
+    dfree(c, P);
+    dfree(c, Q);
+    dfree(c, tg);
+    dfree(c, th);
+    return st;
+}
+
+sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg_graph **out) {
+    if (!ctx || !g || !out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st != SG_OK) return st;
+    Graph *h = nullptr;
+    st = low_degree(c, G_(g), new_to_old, &h);
+    if (st != SG_OK) return st;
+    sg_graph *r = new (std::nothrow) sg_graph;
+    if (!r) {
+        dfree(c, h->off);
+        dfree(c, h->col);
+        dfree(c, h->w);
+        delete h;
+        return fail(SG_ERR_OOM, "host allocation failed");
+    }
+    static_cast<Graph &>(*r) = *h;
+    delete h;
+    *out = r;
+    return SG_OK;
+}
+
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out, int64_t *max_out_degree,
                      int64_t *triangles_out, int64_t *head_arcs_out) {
     if (!ctx || !g) return fail(SG_ERR_INVALID_ARG, "NULL argument");

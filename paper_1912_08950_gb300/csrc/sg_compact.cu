@@ -620,6 +620,164 @@ sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented 
                        grid_per_sm);
 }
 
+// ------------------------------------------- low_degree (Listing 1; Sec. 4.4)
+// The single-vertex kernel deletes every vertex of input degree 0 or 1 with
+// its edges.  Kept vertices get new ids 0..n'-1 in increasing old id: one
+// pass over tiles of kVTile vertices with the same decoupled look-back as the
+// arc compaction; the arcs are then compacted with LowDegPol and the row
+// offsets of the kept rows gathered into the new offset array.
+constexpr uint32_t kNoVertex = 0xFFFFFFFFu;
+constexpr int kVPer = 8;                 // vertices per thread
+constexpr int kVTile = 256 * kVPer;      // vertices per tile
+
+__global__ void __launch_bounds__(256) lowdeg_ids_kernel(const int64_t *__restrict__ off, int64_t n,
+                                                         int64_t num_tiles, uint32_t *__restrict__ new_id,
+                                                         uint32_t *__restrict__ new_to_old,
+                                                         unsigned long long *status, unsigned int *ticket,
+                                                         unsigned long long *kept, int *err) {
+    __shared__ int s_warp[8];
+    __shared__ long long s_tile, s_excl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= num_tiles) break;
+        const int64_t v0 = tile * kVTile + (int64_t)threadIdx.x * kVPer;
+        unsigned flags = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k;
+            if (v < n) {
+                const int64_t d = __ldg(off + v + 1) - __ldg(off + v);
+                if (d >= 2) {
+                    flags |= 1u << k;
+                    ++cnt;
+                }
+            }
+        }
+        // exclusive scan of cnt over the CTA
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            int wv = lane < 8 ? s_warp[lane] : 0, winc = wv;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, winc, o);
+                if (lane >= o) winc += t;
+            }
+            const int agg = __shfl_sync(kFull, winc, 7);
+            if (lane < 8) s_warp[lane] = winc - wv;
+            const int64_t excl = tile_lookback(status, tile, agg, err);
+            if (lane == 0) {
+                s_excl = excl;
+                if (agg) atomicAdd(kept, (unsigned long long)agg);
+            }
+        }
+        __syncthreads();
+        uint32_t id = (uint32_t)(s_excl + s_warp[warp] + (inc - cnt));
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k;
+            if (v < n) {
+                if ((flags >> k) & 1u) {
+                    new_id[v] = id;
+                    if (new_to_old) new_to_old[id] = (uint32_t)v;
+                    ++id;
+                } else {
+                    new_id[v] = kNoVertex;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct LowDegPol {
+    static constexpr bool kOrPrefix = false;
+    static constexpr bool kMapCol = true;
+    const uint32_t *new_id;
+    // an arc stays iff both of its ends stay; its head is renumbered
+    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
+        return __ldg(new_id + x) != kNoVertex && __ldg(new_id + y) != kNoVertex;
+    }
+    __device__ __forceinline__ uint32_t map_col(int64_t, uint32_t y) const { return __ldg(new_id + y); }
+};
+
+// off'[new_id[v]] = off_c[v] for every kept row v; off'[n'] = off_c[n]
+__global__ void lowdeg_offsets_kernel(const int64_t *__restrict__ off_c, const uint32_t *__restrict__ new_id,
+                                      int64_t n, int64_t n_kept, int64_t *__restrict__ off_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t id = __ldg(new_id + v);
+        if (id != kNoVertex) off_out[id] = __ldg(off_c + v);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off_out[n_kept] = __ldg(off_c + n);
+}
+
+sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out) {
+    RowMaps rm;
+    const int64_t vtiles = (g->n + kVTile - 1) / kVTile;
+    uint32_t *new_id = nullptr;
+    int64_t *off_c = nullptr;
+    unsigned long long *status = nullptr, *vstatus = nullptr;
+    Graph *h = nullptr;
+    int64_t kept = 0;
+    sg_status st = build_row_maps(c, g, &rm);
+    if (st == SG_OK) st = dalloc(c, (void **)&new_id, sizeof(uint32_t) * (size_t)std::max<int64_t>(g->n, 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&off_c, sizeof(int64_t) * (size_t)(g->n + 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    // tile status words, the tile ticket and the kept-vertex count, zeroed together
+    if (st == SG_OK) st = dalloc(c, (void **)&vstatus, sizeof(unsigned long long) * (size_t)(vtiles + 2));
+    if (st == SG_OK && g->n > 0) {
+        if (cudaMemsetAsync(vstatus, 0, sizeof(unsigned long long) * (size_t)(vtiles + 2), c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+        if (st == SG_OK) {
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(vtiles, (int64_t)c->num_sms * 4));
+            SG_LAUNCH(c, "lowdeg_ids");
+            lowdeg_ids_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(
+                g->off, g->n, vtiles, new_id, new_to_old, vstatus, reinterpret_cast<unsigned int *>(vstatus + vtiles),
+                vstatus + vtiles + 1, c->d_err);
+            if (cudaGetLastError() != cudaSuccess) st = fail(SG_ERR_CUDA, "lowdeg_ids launch");
+        }
+        if (st == SG_OK) st = read_i64(c, reinterpret_cast<const int64_t *>(vstatus + vtiles + 1), &kept);
+    }
+    if (st == SG_OK) st = new_graph(c, kept, g->nnz, g->w != nullptr, &h);
+    if (st == SG_OK && g->n > 0) {
+        LowDegPol pol{new_id};
+        st = run_compact(c, g, rm, pol, g->w, off_c, h->col, h->w, nullptr, status, "compact_lowdeg");
+        if (st == SG_OK) {
+            const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 8));
+            SG_LAUNCH(c, "lowdeg_offsets");
+            lowdeg_offsets_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(off_c, new_id, g->n, kept, h->off);
+            if (cudaGetLastError() != cudaSuccess) st = fail(SG_ERR_CUDA, "lowdeg_offsets launch");
+        }
+    } else if (st == SG_OK) {
+        if (cudaMemsetAsync(h->off, 0, sizeof(int64_t), c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    }
+    if (st == SG_OK) st = read_i64(c, h->off + kept, &h->nnz);
+    if (st == SG_OK) st = check_device_error(c);
+    dfree(c, new_id);
+    dfree(c, off_c);
+    dfree(c, status);
+    dfree(c, vstatus);
+    free_row_maps(c, &rm);
+    if (st != SG_OK) {
+        delete_graph(c, h);
+        return st;
+    }
+    *out = h;
+    return SG_OK;
+}
+
 }  // namespace sg
 
 // ------------------------------------------------ no-allocation entry point

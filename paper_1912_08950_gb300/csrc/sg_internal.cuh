@@ -202,6 +202,9 @@ sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented 
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
                       unsigned long long *status, int grid_per_sm);
 
+// low_degree vertex kernel (sg_compact.cu)
+sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out);
+
 // triangles (sg_triangles.cu)
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed,
                   uint8_t *del);
@@ -224,11 +227,18 @@ sg_status batch_tr_mark(Ctx *c, const Graph *u, const Oriented &o, const BatchDe
                         uint8_t *del);
 void batch_tr_free(Ctx *c, BatchTri *bt);
 
+sg_status tr_vertex_counts(Ctx *c, const Graph *g, const Oriented &o, unsigned long long *vcnt);
+
 // analytics (sg_analytics.cu)
 sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_out, double *resid);
 sg_status kl_divergence(Ctx *c, int64_t n, const float *P, const float *Q, double *kl);
 sg_status cc_count(Ctx *c, const Graph *g, int64_t *count, uint32_t *labels);
 sg_status validate_graph(Ctx *c, const Graph *g);
+sg_status bfs_levels(Ctx *c, const Graph *g, int64_t root, int *level);
+sg_status critical_edges(Ctx *c, const Graph *g, int64_t root, int64_t *count);
+template <typename T>
+sg_status reordered_neighbours(Ctx *c, const Graph *g, const T *x, const T *y, int64_t *count);
+sg_status max_degree_vertex(Ctx *c, const Graph *g, int64_t *v);
 
 uint64_t prob_threshold(double p);
 

@@ -48,11 +48,12 @@ constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
 constexpr int kQ = 128;           // per-warp hit ring (<= 31 left over + 2 slabs of hits fit)
 constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
 
-// Count: totals only.  EdgeCount: adds every triangle to the counters of its
-// three edges.  Union*: the union-semantics TR kernels.  EoReserve: one
+// Count: totals only.  EdgeCount / VertexCount: add every triangle to the
+// counters of its three edges / vertices.  Union*: the union-semantics TR kernels.  EoReserve: one
 // edge-once bidding pass.  EoEmit: lists the live selected triangles for the
 // edge-once list rounds.  BatchUnion: union kernels over a batch of graphs.
-enum class Mode { Count, EdgeCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCount, EoReserve, EoEmit, BatchUnion };
+enum class Mode { Count, EdgeCount, VertexCount, UnionRandom, UnionMaxw, UnionP2, UnionMinCount, EoReserve, EoEmit,
+                  BatchUnion };
 // the edge-once passes skip arcs that are already considered
 template <Mode M>
 constexpr bool kEdgeOnce = M == Mode::EoReserve || M == Mode::EoEmit;
@@ -71,6 +72,7 @@ struct TriArgs {
     const uint8_t *considered;
     unsigned long long *resv;
     uint32_t *tcnt;               // triangles of G through each arc of E+ (EdgeCount adds, min-count reads)
+    unsigned long long *vcnt;     // triangles through each vertex (VertexCount adds)
     unsigned long long eo_theta;  // edge-once: only triangles with r2 < eo_theta bid this round
     unsigned long long *ctr;
     const uint32_t *heavy;
@@ -215,7 +217,7 @@ __device__ __forceinline__ I mincount_arc(const uint32_t *tcnt, I e01, I e02, I 
 template <Mode M>
 __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u, uint32_t v, uint32_t w,
                                        uint32_t iuv, uint32_t iuw, uint32_t ivw, unsigned &live, Emitter &em) {
-    if constexpr (M == Mode::Count || M == Mode::EdgeCount) {
+    if constexpr (M == Mode::Count || M == Mode::EdgeCount || M == Mode::VertexCount) {
         return;
     } else {
         bool emit = false;
@@ -327,7 +329,7 @@ __device__ __noinline__ void drain32(const TriArgs &a, const HitQueue &q, int he
 template <Mode M>
 __device__ __forceinline__ void flush_hits(const TriArgs &a, const HitQueue &q, QState &qs, uint32_t u,
                                            unsigned &live, Emitter &em) {
-    if constexpr (M != Mode::Count && M != Mode::EdgeCount) {
+    if constexpr (M != Mode::Count && M != Mode::EdgeCount && M != Mode::VertexCount) {
         const int lane = threadIdx.x & 31;
         while (qs.n >= 32) {
             drain32<M>(a, q, qs.head, u, live, em);
@@ -436,6 +438,13 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
             huv += (unsigned)(__popc(ma) + __popc(mb));
             continue;
         }
+        if constexpr (M == Mode::VertexCount) {
+            // each hit is a triangle through w; u and v are summed once per list
+            if (ha) atomicAdd(a.vcnt + wa, 1ull);
+            if (hb) atomicAdd(a.vcnt + wb, 1ull);
+            huv += (unsigned)(__popc(ma) + __popc(mb));
+            continue;
+        }
         if constexpr (M == Mode::Count) {
             if (lane == 0) tris += (unsigned)(__popc(ma) + __popc(mb));
             continue;
@@ -464,6 +473,13 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
     if constexpr (M == Mode::EdgeCount) {
         if (lane == 0 && huv) {
             atomicAdd(a.tcnt + iuv, huv);
+            tris += huv;
+        }
+    }
+    if constexpr (M == Mode::VertexCount) {
+        if (lane == 0 && huv) {
+            atomicAdd(a.vcnt + u, (unsigned long long)huv);
+            atomicAdd(a.vcnt + v, (unsigned long long)huv);
             tris += huv;
         }
     }
@@ -1449,6 +1465,20 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
     if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
     if (maxdeg) *maxdeg = pl.max_deg;
     if (in_arcs) *in_arcs = (int64_t)(v1[kCtrInArcs] - v0[kCtrInArcs]);
+    free_plan(c, &pl);
+    return st;
+}
+
+// Triangles through every vertex (device uint64[n], overwritten).
+sg_status tr_vertex_counts(Ctx *c, const Graph *g, const Oriented &o, unsigned long long *vcnt) {
+    Plan pl;
+    sg_status st = make_plan(c, o, g->off, g->nnz, &pl);
+    if (st == SG_OK && cudaMemsetAsync(vcnt, 0, sizeof(unsigned long long) * (size_t)std::max<int64_t>(o.n, 1),
+                                       c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync(vcnt)");
+    TriArgs a = base_args(c, o);
+    a.vcnt = vcnt;
+    if (st == SG_OK) st = launch_enum<Mode::VertexCount>(c, a, pl);
     free_plan(c, &pl);
     return st;
 }

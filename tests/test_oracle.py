@@ -625,3 +625,24 @@ def test_reordered_neighbours():
     assert oracle.reordered_neighbours(g, x, -x) == differ
     # a tie on one side and an order on the other counts as reordered
     assert oracle.reordered_neighbours(g, np.zeros(g.n, np.float32), x) == differ
+
+
+def test_vertex_triangle_counts():
+    g = gg.gnp(40, 0.3, 7)
+    t = oracle.vertex_triangle_counts(g)
+    want = np.zeros(g.n, dtype=np.int64)
+    for a, b, c in brute.triangles(g.n, brute.edge_set(g)):
+        want[[a, b, c]] += 1
+    assert np.array_equal(t, want)
+    assert t.sum() == 3 * oracle.triangle_count(g)
+    assert np.all(oracle.vertex_triangle_counts(gg.complete(7)) == 15)  # C(6,2)
+
+
+def test_reordered_neighbours_integer_scores():
+    g = gg.rmat(9, 8, seed=2)
+    x = oracle.vertex_triangle_counts(g)
+    h = oracle.compress(g, "tr_random", 0.5, 1)
+    y = oracle.vertex_triangle_counts((g.n, h[0], h[1], None))
+    E = brute.edge_set(g)
+    assert oracle.reordered_neighbours(g, x, y) == brute.reordered(E, x, y)
+    assert oracle.reordered_neighbours(g, x, x) == 0
