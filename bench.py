@@ -40,6 +40,36 @@ METRIC = "input edges/s compressed (TR + CSR rebuild)"
 CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than scale 22
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from one ncu capture of this benchmark's own command
+# (the summaries under profiles/ give the command).  Each entry records the
+# digest of the enumeration sources it was taken on; once they change, the
+# figure no longer describes the kernel and the JSON line reports null.
+MEASURED_TRAFFIC = {
+    # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
+    # profiles/tri_enum_rmat22_tr_eo.md: 48.83 GB read + 17.09 GB written
+    ("rmat22", "tr_eo"): (65917852000, "3b1d3687c10928a55992cb9f809c4604595d2a3903cb3ede09af98e85bead169"),
+}
+TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
+
+
+def sources_digest() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, kernel: str):
+    entry = MEASURED_TRAFFIC.get((workload, kernel))
+    if entry is None or entry[1] != sources_digest():
+        return None
+    return entry[0]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -104,15 +134,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0):
+def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0, listed_total=0):
     """Algorithmic bytes of one launch of a named kernel."""
     A = 2 * m
     if kernel == "tri_enum":
         # off+ and the in-list length of every vertex (8 + 4 B), N+(x) staged in
         # the tables (4 B/arc), the off+ pair of every streamed list (8 B/arc),
-        # the in-list records (8 B per arc streamed from the head's side) and one
-        # 4-byte read per probe (W = sum over arcs of min(d+(u), d+(v)))
-        return (8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs) + 4.0 * probes_total / max(launches, 1)
+        # the in-list records (8 B per arc streamed from the head's side), one
+        # 4-byte read per probe (W = sum over arcs of min(d+(u), d+(v))) and,
+        # for edge-once, the 16-byte record of every listed triangle
+        per = max(launches, 1)
+        return (8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs) + (4.0 * probes_total + 16.0 * listed_total) / per
     if kernel == "tri_inarcs":
         # off+ and N+(u) of every vertex, the off+ pair and symmetric offsets of
         # every head, one 8-byte record written per gathered arc
@@ -196,7 +228,7 @@ def run_ours(args, rank, world):
     hbm, peak_src = peaks()
     cand = {
         "tri_enum": (enum_ms, enum_launches, byte_model(n, m, A_out, st["probes"], enum_launches, "tri_enum",
-                                                        work["head_arcs"])),
+                                                        work["head_arcs"], st["eo_listed"])),
         "compact_orient": (kt["compact_orient"][0], kt["compact_orient"][1],
                            byte_model(n, m, A_out, 0, 1, "compact_orient")),
         "compact_trmask": (kt["compact_trmask"][0], kt["compact_trmask"][1],
@@ -209,7 +241,8 @@ def run_ours(args, rank, world):
 
     # other rows of the hot path, timed once each (not part of the metric)
     rows = {}
-    for kern, p in (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5)):
+    for kern, p in (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5), ("tr_p2", 0.5),
+                    ("tr_mincount", 0.5), ("tr_eo_mincount", 0.5)):
         for _ in range(2):
             sg.compress(G, kern, p, 1).free()
         torch.cuda.synchronize()
@@ -236,7 +269,25 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     rows["divergence"] = {"ms": e0.elapsed_time(e1), "kl_bits": div["kl_bits"], "cc_g": div["cc_g"],
                           "cc_h": div["cc_h"]}
+    e0.record(stream)
+    acc = sg.accuracy(G, H)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rows["accuracy"] = {"ms": e0.elapsed_time(e1), "pr_aren": acc["pr_aren"], "tc_aren": acc["tc_aren"],
+                        "critical_fraction": acc["critical_fraction"], "root": acc["root"]}
     H.free()
+    for _ in range(2):
+        sg.low_degree(G).free()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        L0 = sg.low_degree(G)
+        kept_n = L0.n
+        L0.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rows["low_degree"] = {"ms": e0.elapsed_time(e1) / 3, "kept_vertices": kept_n,
+                          "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
 
     # end to end through the C-ABI with pinned host buffers
     off_h = g.off.cpu().pin_memory()
@@ -294,7 +345,8 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": measured_traffic(args.workload, args.kernel) if dom == "tri_enum" else None,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": d_bytes,
                      "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},

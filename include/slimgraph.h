@@ -120,6 +120,7 @@ typedef struct sg_stats {
     uint64_t probes;          /* wedge-closing probes done by triangle kernels */
     uint64_t triangles;       /* triangles found by triangle kernels */
     uint64_t eo_rounds;       /* Edge-Once reservation rounds run */
+    uint64_t eo_listed;       /* triangles written to Edge-Once lists (16 bytes each) */
 } sg_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -44,6 +44,7 @@ struct Ctx {
     int64_t *h_pinned = nullptr;           // pinned host scratch (small reads)
     uint64_t launches = 0;
     uint64_t eo_rounds = 0;
+    uint64_t eo_listed = 0;                // triangles written to edge-once lists
     int64_t eo_list_cap = 0;               // 0 auto, -1 off, > 0 records
     bool profiling = false;
     std::vector<ProfRec> prof;             // events of launches since reset

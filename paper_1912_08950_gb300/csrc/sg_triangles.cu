@@ -314,15 +314,30 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
     }
 }
 
-// Decide the 32 oldest queued triangles with all lanes.  Kept out of line so
-// that the probe loop's register budget stays small.
+// Decide the 32 oldest queued triangles with all lanes.
 template <Mode M>
-__device__ __noinline__ void drain32(const TriArgs &a, const HitQueue &q, int head, uint32_t u, unsigned &live,
-                                     Emitter &em) {
+__device__ __forceinline__ void drain32_body(const TriArgs &a, const HitQueue &q, int head, uint32_t u,
+                                             unsigned &live, Emitter &em) {
     const int k = (head + (threadIdx.x & 31)) & (kQ - 1);
     const uint32_t iuw = q.iuw[k];
     decide<M>(a, true, u, q.v[k], __ldg(a.colp + iuw), q.iuv[k], iuw, q.ivw[k], live, em);
     __syncwarp();
+}
+template <Mode M>
+__device__ __noinline__ void drain32_call(const TriArgs &a, const HitQueue &q, int head, uint32_t u, unsigned &live,
+                                          Emitter &em) {
+    drain32_body<M>(a, q, head, u, live, em);
+}
+// Out of line, so that the probe loop's register budget stays small -- except
+// for the listing pass, whose 64-register budget holds it inline without the
+// spills a call costs there (R-MAT s22: 80 -> 72 ms).
+template <Mode M>
+__device__ __forceinline__ void drain32(const TriArgs &a, const HitQueue &q, int head, uint32_t u, unsigned &live,
+                                        Emitter &em) {
+    if constexpr (M == Mode::EoEmit)
+        drain32_body<M>(a, q, head, u, live, em);
+    else
+        drain32_call<M>(a, q, head, u, live, em);
 }
 
 // Decide everything queued for the table vertex u (the last group with idle lanes).
@@ -988,7 +1003,11 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
 
 // Reserve for a bucket written by the enumeration: drop the triangles that
 // lost an edge, expand the survivors to full records (vertices from the arc
-// heads, draws recomputed), bid and append them to `out` like the kernel above.
+// heads, draws recomputed), bid and append them to `out`.  Each thread takes
+// kFreshPer records per pass (their loads overlap) and a CTA appends its
+// survivors with one atomic per pass.
+constexpr int kFreshPer = 4;
+
 __global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__restrict__ F, int64_t len,
                                                                TriRec *__restrict__ out, unsigned long long *out_len,
                                                                unsigned long long *resv,
@@ -999,32 +1018,28 @@ __global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__re
     __shared__ int s_cnt[8];
     __shared__ unsigned long long s_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        bool keep = false;
-        TriRec r{kSentinel, 0, 0, 0, 0, 0, 0, 0};
-        if (i < len) {
-            const uint4 f = F[i];
-            if (f.x != kSentinel && !(considered[f.y] | considered[f.z] | considered[f.w])) {
-                keep = true;
-                uint32_t x0 = f.x, x1 = __ldg(colp + f.y), x2 = __ldg(colp + f.z);
-                uint32_t e01 = f.y, e02 = f.z, e12 = f.w;
-                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
-                if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
-                if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
-                const uint4 d = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), k0, k1);
-                r = TriRec{x0, x1, x2, d.y, d.z, e01, e02, e12};
-                if ((unsigned long long)d.z < theta) {
-                    const unsigned long long hi = (unsigned long long)d.z << 32;
-                    atomicMin(resv + e01, hi | x2);
-                    atomicMin(resv + e02, hi | x1);
-                    atomicMin(resv + e12, hi | x0);
-                }
-            }
+    const int64_t span = (int64_t)blockDim.x * kFreshPer;
+    for (int64_t base = (int64_t)blockIdx.x * span; base < len; base += (int64_t)gridDim.x * span) {
+        uint4 f[kFreshPer];
+        bool keep[kFreshPer];
+#pragma unroll
+        for (int r = 0; r < kFreshPer; ++r) {
+            const int64_t i = base + r * blockDim.x + threadIdx.x;
+            f[r] = i < len ? __ldg(F + i) : make_uint4(kSentinel, 0u, 0u, 0u);
         }
-        const unsigned bm = __ballot_sync(kFull, keep);
-        if (lane == 0) s_cnt[warp] = __popc(bm);
+#pragma unroll
+        for (int r = 0; r < kFreshPer; ++r)
+            keep[r] = f[r].x != kSentinel && !(considered[f[r].y] | considered[f[r].z] | considered[f[r].w]);
+        int cnt = 0;
+#pragma unroll
+        for (int r = 0; r < kFreshPer; ++r) cnt += keep[r];
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_cnt[warp] = inc;
         __syncthreads();
         if (threadIdx.x == 0) {
             int tot = 0;
@@ -1036,7 +1051,24 @@ __global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__re
             s_base = tot ? atomicAdd(out_len, (unsigned long long)tot) : 0ull;
         }
         __syncthreads();
-        if (keep) out[s_base + s_cnt[warp] + __popc(bm & lanemask_lt())] = r;
+        unsigned long long slot = s_base + s_cnt[warp] + (inc - cnt);
+#pragma unroll
+        for (int r = 0; r < kFreshPer; ++r) {
+            if (!keep[r]) continue;
+            uint32_t x0 = f[r].x, x1 = __ldg(colp + f[r].y), x2 = __ldg(colp + f[r].z);
+            uint32_t e01 = f[r].y, e02 = f[r].z, e12 = f[r].w;
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            if (x1 > x2) { swap2(x1, x2); swap2(e01, e02); }
+            if (x0 > x1) { swap2(x0, x1); swap2(e02, e12); }
+            const uint4 d = philox4x32_10(make_uint4(x0, x1, x2, kTagTri), k0, k1);
+            if ((unsigned long long)d.z < theta) {
+                const unsigned long long hi = (unsigned long long)d.z << 32;
+                atomicMin(resv + e01, hi | x2);
+                atomicMin(resv + e02, hi | x1);
+                atomicMin(resv + e12, hi | x0);
+            }
+            out[slot++] = TriRec{x0, x1, x2, d.y, d.z, e01, e02, e12};
+        }
         __syncthreads();
     }
 }
@@ -1314,6 +1346,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                     try_list = false;
                 } else {
                     listed = true;
+                    c->eo_listed += live;
                     for (int b = 0; b < kEoBuckets; ++b)
                         used[b] = (int64_t)std::min<unsigned long long>(fill[b], a.list_cap[b]);
                     next_bucket = rb;
@@ -1361,7 +1394,8 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         }
         if (fresh > 0) {
             SG_LAUNCH(c, "tri_eo_fresh_reserve");
-            eo_fresh_reserve_kernel<<<(unsigned)list_blocks(fresh), 256, 0, c->stream>>>(
+            eo_fresh_reserve_kernel<<<(unsigned)list_blocks((fresh + kFreshPer - 1) / kFreshPer), 256, 0,
+                                      c->stream>>>(
                 L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta, a.colp, a.k0, a.k1);
         }
         if (next_bucket < kEoBuckets) ++next_bucket;
