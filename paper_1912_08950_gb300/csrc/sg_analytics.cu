@@ -17,24 +17,36 @@ namespace sg {
 
 constexpr int kPrThreads = 256;
 constexpr int kPrWarps = kPrThreads / 32;
-constexpr int kShortRow = 16;  // rows up to this degree are summed by one lane
 
 // x'_v = (1-d)/n + d (sum_{u in N(v)} y_u + D/n), y_u = x_u / d_u; emits
 // y' = x'/d and, per block, the FP32 dangling mass of x' (and, on the last
 // iteration, the FP64 partial L1 residual |x' - x|).
+//
+// Row sums: a warp owns 32 consecutive rows.  Rows longer than 32 arcs are
+// summed by the whole warp, one row at a time (lanes stride the row, then a
+// fixed shuffle tree).  The short rows are summed together: their arcs are
+// numbered consecutively across the 32 rows and streamed in slabs of 32, a
+// lane finds its arc's row among the rows' starts (binary search over the
+// lanes), a segmented shuffle scan sums each row's run inside the slab and the
+// run's last lane adds it to the row's slot in shared memory.  Every order is
+// fixed, so a graph always gives the same vector.
+constexpr int kShortRow = 32;
+constexpr int kHubRow = 1024;    // longer rows are summed in chunks by whole CTAs
+constexpr int kHubChunk = 8192;  // arcs per chunk
+
 __global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(
     const int64_t *__restrict__ off, const uint32_t *__restrict__ col, int64_t n, const float *__restrict__ x,
     const float *__restrict__ y, const float *__restrict__ dangling_in, float base, float damping, float inv_n,
     float *__restrict__ x_new, float *__restrict__ y_new, float *__restrict__ dangling_part,
-    double *__restrict__ resid_part) {
+    double *__restrict__ resid_part, const int *__restrict__ hub_slot, const float *__restrict__ hub_part) {
     __shared__ float s_dang[kPrWarps];
     __shared__ double s_res[kPrWarps];
+    __shared__ float s_acc[kPrWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float dterm = dangling_in[0] * inv_n;
     float dang = 0.f;
     double res = 0.0;
     const int64_t nwarps = (int64_t)gridDim.x * kPrWarps;
-    // each warp owns blocks of 32 consecutive rows
     for (int64_t r0 = ((int64_t)blockIdx.x * kPrWarps + warp) * 32; r0 < n; r0 += nwarps * 32) {
         const int64_t v = r0 + lane;
         int64_t b = 0, e = 0;
@@ -43,12 +55,53 @@ __global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(
             e = __ldg(off + v + 1);
         }
         const int64_t deg = e - b;
-        float s = 0.f;
-        if (deg <= kShortRow) {
-            for (int64_t i = b; i < e; ++i) s += __ldg(y + __ldg(col + i));
+        const bool longr = deg > kShortRow;
+        // short rows: consecutive numbering of their arcs
+        const int sdeg = longr ? 0 : (int)deg;
+        int vs = sdeg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, vs, o);
+            if (lane >= o) vs += t;
+        }
+        const int total = __shfl_sync(kFull, vs, 31);
+        vs -= sdeg;  // exclusive start of this row's arcs
+        s_acc[warp][lane] = 0.f;
+        __syncwarp();
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int i = s0 + lane;
+            const bool valid = i < total;
+            int k = 0;  // the last row whose start is <= i
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int sk = __shfl_sync(kFull, vs, k + step);
+                if (sk <= i) k += step;
+            }
+            const int64_t bk = __shfl_sync(kFull, b, k);
+            const int vk = __shfl_sync(kFull, vs, k);
+            float val = valid ? __ldg(y + __ldg(col + bk + (i - vk))) : 0.f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float t = __shfl_up_sync(kFull, val, o);
+                const int kt = __shfl_up_sync(kFull, k, o);
+                if (lane >= o && kt == k) val += t;
+            }
+            const int kn = __shfl_down_sync(kFull, k, 1);
+            if (valid && (lane == 31 || kn != k || i + 1 >= total)) s_acc[warp][k] += val;
+            __syncwarp();
+        }
+        float s = s_acc[warp][lane];
+        __syncwarp();
+        // hub rows: their chunk sums, in chunk order
+        if (deg > kHubRow) {
+            const int first = __ldg(hub_slot + v);
+            const int nch = (int)((deg + kHubChunk - 1) / kHubChunk);
+            float t = 0.f;
+            for (int c2 = 0; c2 < nch; ++c2) t += __ldg(hub_part + first + c2);
+            s = t;
         }
         // long rows: the whole warp, one row at a time, fixed tree order
-        unsigned longm = __ballot_sync(kFull, deg > kShortRow);
+        unsigned longm = __ballot_sync(kFull, longr && deg <= kHubRow);
         while (longm) {
             const int src = __ffs(longm) - 1;
             longm &= longm - 1;
@@ -87,6 +140,96 @@ __global__ void __launch_bounds__(kPrThreads) pr_iter_kernel(
         }
         dangling_part[blockIdx.x] = bd;
         if (resid_part) resid_part[blockIdx.x] = br;
+    }
+}
+
+// Hub rows (more than kHubRow arcs) are cut into chunks of kHubChunk arcs;
+// a CTA sums one chunk (threads stride it, then a fixed tree) into its slot.
+__global__ void __launch_bounds__(kPrThreads) pr_hub_kernel(const uint32_t *__restrict__ col,
+                                                            const float *__restrict__ y,
+                                                            const int64_t *__restrict__ chunk_begin,
+                                                            const int64_t *__restrict__ chunk_end,
+                                                            float *__restrict__ hub_part) {
+    __shared__ float s[kPrWarps];
+    const int64_t b = chunk_begin[blockIdx.x], e = chunk_end[blockIdx.x];
+    float t = 0.f;
+    for (int64_t i = b + threadIdx.x; i < e; i += kPrThreads) t += __ldg(y + __ldg(col + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float acc = 0.f;
+        for (int w = 0; w < kPrWarps; ++w) acc += s[w];
+        hub_part[blockIdx.x] = acc;
+    }
+}
+
+// Hub rows and their chunk count (the list order is whatever the atomics give).
+__global__ void pr_find_hubs_kernel(const int64_t *__restrict__ off, int64_t n, uint32_t *hubs,
+                                    unsigned long long *counts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t deg = off[v + 1] - off[v];
+        if (deg > kHubRow) {
+            hubs[atomicAdd(counts, 1ull)] = (uint32_t)v;
+            atomicAdd(counts + 1, (unsigned long long)((deg + kHubChunk - 1) / kHubChunk));
+        }
+    }
+}
+
+// One CTA: each hub's first chunk slot (a running block scan over the hub
+// list, 1024 hubs at a time) and the chunk bounds.
+__global__ void __launch_bounds__(1024) pr_hub_chunks_kernel(const int64_t *__restrict__ off,
+                                                             const uint32_t *__restrict__ hubs, int num_hubs,
+                                                             int *hub_slot, int64_t *chunk_begin,
+                                                             int64_t *chunk_end) {
+    __shared__ int s_warp[32];
+    __shared__ int s_run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (int h0 = 0; h0 < num_hubs; h0 += 1024) {
+        const int h = h0 + threadIdx.x;
+        int64_t b = 0, e = 0;
+        uint32_t v = 0;
+        int nch = 0;
+        if (h < num_hubs) {
+            v = hubs[h];
+            b = off[v];
+            e = off[v + 1];
+            nch = (int)((e - b + kHubChunk - 1) / kHubChunk);
+        }
+        int inc = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const int wv = s_warp[lane];
+            int wi = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            s_warp[lane] = wi - wv;
+        }
+        __syncthreads();
+        int slot = s_run + s_warp[warp] + inc - nch;
+        if (h < num_hubs) {
+            hub_slot[v] = slot;
+            for (int64_t c = b; c < e; c += kHubChunk, ++slot) {
+                chunk_begin[slot] = c;
+                chunk_end[slot] = c + kHubChunk < e ? c + kHubChunk : e;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) s_run = slot;  // the last thread's next slot is the running total
+        __syncthreads();
     }
 }
 
@@ -153,6 +296,42 @@ sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_ou
     float *dpart = buf + 4 * nn, *dtot = dpart + blocks;
     const float inv_n = (float)(1.0 / (double)n);
     const float base = (float)((1.0 - (double)damping) / (double)n);
+    // hub rows: list them once, then their chunks are summed before every iteration
+    uint32_t *hubs = nullptr;
+    unsigned long long *hcnt = nullptr;
+    int *hub_slot = nullptr;
+    int64_t *chunk_b = nullptr, *chunk_e = nullptr;
+    float *hub_part = nullptr;
+    int64_t num_hubs = 0, num_chunks = 0;
+    st = dalloc(c, (void **)&hcnt, 2 * sizeof(unsigned long long));
+    if (st == SG_OK) st = dalloc(c, (void **)&hubs, sizeof(uint32_t) * nn);
+    if (st == SG_OK && cudaMemsetAsync(hcnt, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    if (st == SG_OK) {
+        SG_LAUNCH(c, "pr_hubs");
+        pr_find_hubs_kernel<<<blocks, kPrThreads, 0, c->stream>>>(g->off, n, hubs, hcnt);
+        if (cudaMemcpyAsync(c->h_pinned, hcnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "PageRank hub count");
+        num_hubs = c->h_pinned[0];
+        num_chunks = c->h_pinned[1];
+    }
+    if (st == SG_OK && num_hubs > 0) {
+        st = dalloc(c, (void **)&hub_slot, sizeof(int) * nn);
+        if (st == SG_OK) st = dalloc(c, (void **)&chunk_b, sizeof(int64_t) * (size_t)num_chunks);
+        if (st == SG_OK) st = dalloc(c, (void **)&chunk_e, sizeof(int64_t) * (size_t)num_chunks);
+        if (st == SG_OK) st = dalloc(c, (void **)&hub_part, sizeof(float) * (size_t)num_chunks);
+        if (st == SG_OK) {
+            SG_LAUNCH(c, "pr_hubs");
+            pr_hub_chunks_kernel<<<1, 1024, 0, c->stream>>>(g->off, hubs, (int)num_hubs, hub_slot, chunk_b, chunk_e);
+        }
+    }
+    if (st != SG_OK) {
+        dfree(c, hubs); dfree(c, hcnt); dfree(c, hub_slot); dfree(c, chunk_b); dfree(c, chunk_e); dfree(c, hub_part);
+        dfree(c, buf); dfree(c, dres);
+        return st;
+    }
     {
         SG_LAUNCH(c, "pr_init");
         pr_init_kernel<<<blocks, kPrThreads, 0, c->stream>>>(g->off, n, inv_n, xa, ya, dpart);
@@ -164,10 +343,15 @@ sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_ou
     for (int it = 0; it < iters; ++it) {
         const bool last = (it == iters - 1);
         float *xo = last ? x_out : xb;
+        if (num_chunks > 0) {
+            SG_LAUNCH(c, "pr_hub");
+            pr_hub_kernel<<<(unsigned)num_chunks, kPrThreads, 0, c->stream>>>(g->col, ya, chunk_b, chunk_e, hub_part);
+        }
         {
             SG_LAUNCH(c, "pr_iter");
             pr_iter_kernel<<<blocks, kPrThreads, 0, c->stream>>>(g->off, g->col, n, xa, ya, dtot, base, damping, inv_n,
-                                                                 xo, yb, dpart, last ? dres : nullptr);
+                                                                 xo, yb, dpart, last ? dres : nullptr, hub_slot,
+                                                                 hub_part);
         }
         if (!last) {
             SG_LAUNCH(c, "pr_reduce");
@@ -184,6 +368,12 @@ sg_status pagerank(Ctx *c, const Graph *g, float damping, int iters, float *x_ou
     SG_CUDA(cudaMemcpyAsync(c->h_pinned, dres + blocks, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(cudaStreamSynchronize(c->stream));
     std::memcpy(resid, c->h_pinned, sizeof(double));
+    dfree(c, hubs);
+    dfree(c, hcnt);
+    dfree(c, hub_slot);
+    dfree(c, chunk_b);
+    dfree(c, chunk_e);
+    dfree(c, hub_part);
     dfree(c, buf);
     dfree(c, dres);
     return SG_OK;
