@@ -70,6 +70,29 @@ def measured_traffic(workload: str, kernel: str):
     return entry[0]
 
 
+# ------------------------------------------------------------ replicas
+# N > 1: one independent replica per GPU (the path has no exchange step).
+# Rank r compresses its own graph (seed 1 + r; rank 0 is the named
+# workload), the step time is the maximum over ranks, and the whole-job
+# throughput counts every rank's edges.
+def replica_seed(rank: int) -> int:
+    return 1 + rank
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, m_per_rank: int, seconds: float) -> float:
+    return world * m_per_rank / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -171,7 +194,7 @@ def run_ours(args, rank, world):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = WORKLOADS[args.workload]
-    seed = 1 + rank  # independent replica per GPU; rank 0 is the named workload
+    seed = replica_seed(rank)
     g = gg.rmat(wl["scale"], wl["ef"], seed=seed, device="cuda")
     torch.cuda.synchronize()
     # the library runs on this stream; every timing event is recorded on it
@@ -220,10 +243,7 @@ def run_ours(args, rank, world):
         kt[name] = ctx.kernel_time(name)
     enum_ms = kt["tri_enum"][0]
     enum_launches = max(kt["tri_enum"][1], 1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     hbm, peak_src = peaks()
     cand = {
@@ -317,16 +337,13 @@ def run_ours(args, rank, world):
         nnz_out = e2e_step()
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
     cpu = cpu_baseline(args) if rank == 0 and not args.no_cpu else None
     clk = clocks.summary()
     res = {
         "metric": METRIC,
-        "value": world * m / (ms / 1e3),
+        "value": replica_throughput(world, m, ms / 1e3),
         "unit": "edges/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -353,7 +370,7 @@ def run_ours(args, rank, world):
         "eo_rounds_per_step": st["eo_rounds"] / args.steps,
         "gpu_launches": st["kernel_launches"],
         "clocks": clk,
-        "e2e": {"value": world * m / e2e_s, "unit": "edges/s",
+        "e2e": {"value": replica_throughput(world, m, e2e_s), "unit": "edges/s",
                 "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
                 "d2h_bytes_per_step": 8 * (n + 1) + 4 * int(nnz_out)},
         "rows": rows,
