@@ -380,7 +380,8 @@ void sg_batch_free(sg_batch *b) {
         for (void *p : {(void *)b->u.off, (void *)b->u.col, (void *)b->u.w, (void *)b->vgid, (void *)b->d_params,
                         (void *)b->rm.chunk_row, (void *)b->rm.tile_vlo, (void *)b->o.off, (void *)b->o.col,
                         (void *)b->o.w, (void *)b->o.fwd_bits, (void *)b->o.status, (void *)b->st_final,
-                        (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->off_c,
+                        (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->bt.din,
+                        (void *)b->bt.inl, (void *)b->off_c,
                         (void *)b->out_off, (void *)b->out_col, (void *)b->out_w, (void *)b->d_info})
             if (p) (void)cudaFree(p);
         if (b->h_params) cudaFreeHost(b->h_params);

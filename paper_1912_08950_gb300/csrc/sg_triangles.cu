@@ -1135,14 +1135,16 @@ static sg_status launch_inarcs(Ctx *c, const Oriented &o, const int64_t *offs, u
     return SG_OK;
 }
 
-static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64_t nnz, Plan *pl) {
+// inl_cap: room for in-arc records; nnz - m when E+ holds all m arcs, nnz
+// when it may hold fewer (batches orient only their triangle-kernel graphs).
+static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64_t inl_cap, Plan *pl) {
     if (o.m >= (int64_t)0xFFFFFFFFll)
         return fail(SG_ERR_UNSUPPORTED, "triangle kernels address oriented arcs with 32 bits: m must be < 2^32");
     pl->offs = offs;
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kBuckets);
     if (st == SG_OK) st = dalloc(c, (void **)&pl->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
-    if (st == SG_OK) st = dalloc(c, (void **)&pl->inl, sizeof(uint2) * (size_t)std::max<int64_t>(nnz - o.m, 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&pl->inl, sizeof(uint2) * (size_t)std::max<int64_t>(inl_cap, 1));
     if (st != SG_OK) return st;
     SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, c->stream));
     SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
@@ -1457,7 +1459,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
 
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed, uint8_t *del) {
     Plan pl;
-    sg_status st = make_plan(c, o, g->off, g->nnz, &pl);
+    sg_status st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
     TriArgs a = base_args(c, o);
     a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(seed >> 32);
@@ -1492,7 +1494,7 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
     Plan pl;
     unsigned long long v0[kCtrCount] = {}, v1[kCtrCount] = {};
     sg_status st = read_ctr(c, 0, kCtrCount, v0);
-    if (st == SG_OK) st = make_plan(c, o, g->off, g->nnz, &pl);
+    if (st == SG_OK) st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
     if (st == SG_OK) st = launch_enum<Mode::Count>(c, base_args(c, o), pl);
     if (st == SG_OK) st = read_ctr(c, 0, kCtrCount, v1);
     if (count) *count = (int64_t)(v1[kCtrTriangles] - v0[kCtrTriangles]);
@@ -1506,7 +1508,7 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
 // Triangles through every vertex (device uint64[n], overwritten).
 sg_status tr_vertex_counts(Ctx *c, const Graph *g, const Oriented &o, unsigned long long *vcnt) {
     Plan pl;
-    sg_status st = make_plan(c, o, g->off, g->nnz, &pl);
+    sg_status st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
     if (st == SG_OK && cudaMemsetAsync(vcnt, 0, sizeof(unsigned long long) * (size_t)std::max<int64_t>(o.n, 1),
                                        c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync(vcnt)");
@@ -1522,7 +1524,7 @@ sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *
     Plan pl;
     pl.light_max = bt->light_max;
     pl.light_items = 4 * bt->light_max;
-    sg_status st = make_plan(c, o, u->off, u->nnz, &pl);
+    sg_status st = make_plan(c, o, u->off, u->nnz, &pl);  // an unvalidated member may orient fewer arcs
     if (st == SG_OK) {
         bt->log_slots = pl.log_slots;
         bt->smem = pl.smem;
@@ -1534,8 +1536,11 @@ sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *
     if (st == SG_OK && !bt->buckets)
         st = dalloc(c, (void **)&bt->buckets, sizeof(unsigned long long) * (2 * kBuckets + 1));
     if (st == SG_OK && !bt->din) st = dalloc(c, (void **)&bt->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
+    // Per call only the graphs with a triangle kernel are oriented, so E+ can
+    // hold fewer than nnz/2 arcs and the in-list room off(v) - off+(v) then
+    // reaches up to nnz: size the records for that.
     if (st == SG_OK && !bt->inl)
-        st = dalloc(c, (void **)&bt->inl, sizeof(uint2) * (size_t)std::max<int64_t>(u->nnz - o.m, 1));
+        st = dalloc(c, (void **)&bt->inl, sizeof(uint2) * (size_t)std::max<int64_t>(u->nnz, 1));
     return st;
 }
 

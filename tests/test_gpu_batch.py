@@ -97,3 +97,21 @@ def test_batch_rejects_edge_once(sg, ctx):
             B.compress([kern], [0.5], [1])
         assert e.value.status == sg.SG_ERR_UNSUPPORTED
     B.free()
+
+
+def test_batch_edge_kernel_graphs_before_triangle_graphs(sg, ctx):
+    # Large graphs with edge kernels first, triangle kernels last: those
+    # graphs are not oriented, so the in-arc room of the later vertices sits
+    # beyond nnz/2 -- the in-arc records must cover all nnz.
+    graphs = [gg.rmat(s, 16, seed=40 + i) for i, s in enumerate((14, 13, 14, 12, 13, 12))]
+    kernels = ["uniform", "spectral_avgdeg", "uniform", "tr_random", "tr_p2", "tr_random"]
+    ps = [0.5, 0.5, 0.3, 0.6, 0.5, 0.9]
+    seeds = [3, 4, 5, 6, 7, 8]
+    B, _ = _check_batch(sg, ctx, graphs, kernels, ps, seeds)
+    # and with the order reversed
+    outs = B.compress(kernels[::-1], ps[::-1], seeds[::-1])
+    for i, h in enumerate(outs):
+        off, col, _ = h.download()
+        o_off, o_col, _ = oracle.compress(graphs[i], kernels[::-1][i], ps[::-1][i], seeds[::-1][i])
+        assert np.array_equal(off, o_off) and np.array_equal(col, o_col)
+    B.free()
