@@ -369,7 +369,8 @@ __device__ __forceinline__ void flush_hits(const TriArgs &a, const HitQueue &q, 
 // divergence.  Load <= 1/4.  An insertion that keeps displacing keys for
 // kCuckooIters exchanges leaves its homeless entry in a small stash that
 // lookups then scan; a full stash raises a device error.
-constexpr unsigned long long kSlotEmpty = ~0ull;
+// an empty slot's key is 0xFFFFFFFE: never a vertex (ids stay below 2^32 - 2) and not kEmpty
+constexpr unsigned long long kSlotEmpty = 0xFFFFFFFEFFFFFFFFull;
 constexpr int kCuckooIters = 32;
 constexpr int kStash = 16;
 
@@ -399,17 +400,25 @@ __device__ __forceinline__ void table_insert(const Table &t, int log_slots, uint
     else atomicExch(err, (int)kDevTableFull);
 }
 
-// w in the table?  t receives its position in N+(u)
-__device__ __forceinline__ bool table_find(const Table &tb, int sh, int stash_n, uint32_t w, uint32_t &t) {
+// w in the table's two slots?  t receives its position in N+(u).  kEmpty (a
+// lane past the end of its list) matches neither an empty slot nor a vertex.
+__device__ __forceinline__ bool table_find(const Table &tb, int sh, uint32_t w, uint32_t &t) {
     const unsigned long long a = tb.slot[h1_of(w, sh)];
     const unsigned long long b = tb.slot[h2_of(w, sh)];
-    if ((uint32_t)(a >> 32) == w) { t = (uint32_t)a; return true; }
-    if ((uint32_t)(b >> 32) == w) { t = (uint32_t)b; return true; }
+    t = (uint32_t)a;
+    if ((uint32_t)(a >> 32) == w) return true;
+    t = (uint32_t)b;
+    return (uint32_t)(b >> 32) == w;
+}
+
+// w in the stash (the rare table whose insertion left keys there)?  Returns
+// the slot word (key << 32 | position), or kSlotEmpty.
+__device__ __noinline__ unsigned long long stash_find(const unsigned long long *stash, int stash_n, uint32_t w) {
     for (int k = 0; k < stash_n; ++k) {
-        const unsigned long long c = tb.stash[k];
-        if ((uint32_t)(c >> 32) == w) { t = (uint32_t)c; return true; }
+        const unsigned long long c = stash[k];
+        if ((uint32_t)(c >> 32) == w) return c;
     }
-    return false;
+    return kSlotEmpty;
 }
 
 // First two 32-element slabs of the list colp[ov, ov + dv) (kEmpty past its end).
@@ -443,8 +452,20 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
         if (ja + 64 < dv) na = __ldg(lst + ja + 64);
         if (jb + 64 < dv) nb = __ldg(lst + jb + 64);
         // kEmpty is never a vertex, so out-of-range lanes miss
-        const bool ha = table_find(tb, sh, stash_n, wa, ta) && ja < dv;
-        const bool hb = table_find(tb, sh, stash_n, wb, tb2) && jb < dv;
+        bool ha = table_find(tb, sh, wa, ta);
+        bool hb = table_find(tb, sh, wb, tb2);
+        if (stash_n != 0) {  // warp-uniform and rare
+            if (!ha) {
+                const unsigned long long c = stash_find(tb.stash, stash_n, wa);
+                ha = c != kSlotEmpty;
+                ta = (uint32_t)c;
+            }
+            if (!hb) {
+                const unsigned long long c = stash_find(tb.stash, stash_n, wb);
+                hb = c != kSlotEmpty;
+                tb2 = (uint32_t)c;
+            }
+        }
         const unsigned ma = __ballot_sync(kFull, ha), mb = __ballot_sync(kFull, hb);
         if constexpr (M == Mode::EdgeCount) {
             // each hit closes a triangle through u->w and v->w; u->v is summed once
@@ -1140,6 +1161,8 @@ static sg_status launch_inarcs(Ctx *c, const Oriented &o, const int64_t *offs, u
 static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64_t inl_cap, Plan *pl) {
     if (o.m >= (int64_t)0xFFFFFFFFll)
         return fail(SG_ERR_UNSUPPORTED, "triangle kernels address oriented arcs with 32 bits: m must be < 2^32");
+    if (o.n >= (int64_t)0xFFFFFFFEll)
+        return fail(SG_ERR_UNSUPPORTED, "triangle kernels reserve vertex ids 2^32 - 2 and 2^32 - 1");
     pl->offs = offs;
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kBuckets);
