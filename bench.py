@@ -261,8 +261,11 @@ def run_ours(args, rank, world):
 
     # other rows of the hot path, timed once each (not part of the metric)
     rows = {}
-    for kern, p in (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5), ("tr_p2", 0.5),
-                    ("tr_mincount", 0.5), ("tr_eo_mincount", 0.5)):
+    row_kernels = (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5), ("tr_p2", 0.5),
+                   ("tr_mincount", 0.5), ("tr_eo_mincount", 0.5))
+    if args.no_rows:
+        row_kernels = ()
+    for kern, p in row_kernels:
         for _ in range(2):
             sg.compress(G, kern, p, 1).free()
         torch.cuda.synchronize()
@@ -273,41 +276,42 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         rows[kern] = {"ms": e0.elapsed_time(e1) / 3, "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
-    # the enumeration alone (triangle counting, no decisions) for comparison
-    ctx.reset_profile()
-    ctx.set_profiling(True)
-    sg.tr_work(G)
-    ctx.set_profiling(False)
-    rows["enum_count_only"] = {"ms": ctx.kernel_time("tri_enum")[0], "probes": work["probes"],
-                               "triangles": work["triangles"]}
-    H = sg.compress(G, args.kernel, args.p, 1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    div = sg.divergence(G, H)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    rows["divergence"] = {"ms": e0.elapsed_time(e1), "kl_bits": div["kl_bits"], "cc_g": div["cc_g"],
-                          "cc_h": div["cc_h"]}
-    e0.record(stream)
-    acc = sg.accuracy(G, H)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    rows["accuracy"] = {"ms": e0.elapsed_time(e1), "pr_aren": acc["pr_aren"], "tc_aren": acc["tc_aren"],
-                        "critical_fraction": acc["critical_fraction"], "root": acc["root"]}
-    H.free()
-    for _ in range(2):
-        sg.low_degree(G).free()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(3):
-        L0 = sg.low_degree(G)
-        kept_n = L0.n
-        L0.free()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    rows["low_degree"] = {"ms": e0.elapsed_time(e1) / 3, "kept_vertices": kept_n,
-                          "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
+    if not args.no_rows:
+        # the enumeration alone (triangle counting, no decisions) for comparison
+        ctx.reset_profile()
+        ctx.set_profiling(True)
+        sg.tr_work(G)
+        ctx.set_profiling(False)
+        rows["enum_count_only"] = {"ms": ctx.kernel_time("tri_enum")[0], "probes": work["probes"],
+                                   "triangles": work["triangles"]}
+        H = sg.compress(G, args.kernel, args.p, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        div = sg.divergence(G, H)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows["divergence"] = {"ms": e0.elapsed_time(e1), "kl_bits": div["kl_bits"], "cc_g": div["cc_g"],
+                              "cc_h": div["cc_h"]}
+        e0.record(stream)
+        acc = sg.accuracy(G, H)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows["accuracy"] = {"ms": e0.elapsed_time(e1), "pr_aren": acc["pr_aren"], "tc_aren": acc["tc_aren"],
+                            "critical_fraction": acc["critical_fraction"], "root": acc["root"]}
+        H.free()
+        for _ in range(2):
+            sg.low_degree(G).free()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            L0 = sg.low_degree(G)
+            kept_n = L0.n
+            L0.free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows["low_degree"] = {"ms": e0.elapsed_time(e1) / 3, "kept_vertices": kept_n,
+                              "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
 
     # end to end through the C-ABI with pinned host buffers
     off_h = g.off.cpu().pin_memory()
@@ -578,6 +582,7 @@ def main():
     ap.add_argument("--kernel", default="tr_eo")
     ap.add_argument("--p", type=float, default=0.5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-rows", action="store_true", help="skip the extra per-kernel rows and analytics")
     ap.add_argument("--eo-list-cap", type=int, default=0,
                     help="edge-once triangle list capacity in records (0: automatic, -1: none)")
     ap.add_argument("--mode", choices=["compress", "batch", "serve"], default="compress")

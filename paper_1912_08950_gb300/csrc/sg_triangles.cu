@@ -58,6 +58,13 @@ enum class Mode { Count, EdgeCount, VertexCount, UnionRandom, UnionMaxw, UnionP2
 template <Mode M>
 constexpr bool kEdgeOnce = M == Mode::EoReserve || M == Mode::EoEmit;
 
+// Edge-once "considered" flags: one bit per oriented arc (m/8 bytes, so the
+// flags stay in L2 while the triangle lists stream past them).
+__device__ __forceinline__ bool considered_bit(const uint32_t *c, int64_t e) {
+    return (__ldg(c + (e >> 5)) >> (e & 31)) & 1u;
+}
+__device__ __forceinline__ void set_considered(uint32_t *c, int64_t e) { atomicOr(c + (e >> 5), 1u << (e & 31)); }
+
 struct TriArgs {
     const int64_t *offp;
     const uint32_t *colp;
@@ -69,7 +76,7 @@ struct TriArgs {
     uint32_t k0, k1;
     unsigned long long tp;
     uint8_t *del;
-    const uint8_t *considered;
+    const uint32_t *considered;  // edge-once flag bits (see considered_bit)
     unsigned long long *resv;
     uint32_t *tcnt;               // triangles of G through each arc of E+ (EdgeCount adds, min-count reads)
     unsigned long long *vcnt;     // triangles through each vertex (VertexCount adds)
@@ -288,7 +295,8 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                     if (w12 > bw || (w12 == bw && (x1 > bl || (x1 == bl && x2 > bh)))) { best = e12; }
                     a.del[best] = 1;
                 } else if constexpr (M == Mode::EoReserve) {
-                    if (a.considered == nullptr || !(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
+                    if (a.considered == nullptr || !(considered_bit(a.considered, e01) | considered_bit(a.considered, e02) |
+                                                     considered_bit(a.considered, e12))) {
                         // the round's prefix of the (r2, a, b, c) order bids for its edges
                         if ((unsigned long long)r.z < a.eo_theta) {
                             const unsigned long long hi = (unsigned long long)r.z << 32;
@@ -299,7 +307,8 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                         ++live;
                     }
                 } else {  // EoEmit: list the live selected triangle, bid later
-                    if (a.considered == nullptr || !(a.considered[e01] | a.considered[e02] | a.considered[e12])) {
+                    if (a.considered == nullptr || !(considered_bit(a.considered, e01) | considered_bit(a.considered, e02) |
+                                                     considered_bit(a.considered, e12))) {
                         ++live;
                         emit = true;
                         rec_r2 = r.z;
@@ -538,7 +547,7 @@ __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &t
         se = it.y;
         const int64_t b0 = __ldg(a.offp + sv);
         so = (uint32_t)b0;
-        sd = (kEdgeOnce<M> && a.considered != nullptr && a.considered[se])
+        sd = (kEdgeOnce<M> && a.considered != nullptr && considered_bit(a.considered, se))
                  ? 0 : (int)(__ldg(a.offp + sv + 1) - b0);
     }
     // the next list's first slabs load while the current one is probed
@@ -630,7 +639,8 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                 for (int k = threadIdx.x; k < cn; k += blockDim.x) {
                     const int i = c0 + k;
                     const uint32_t v = __ldg(a.colp + ou + i);
-                    const bool dead = kEdgeOnce<M> && a.considered != nullptr && a.considered[ou + i];
+                    const bool dead = kEdgeOnce<M> && a.considered != nullptr &&
+                                      considered_bit(a.considered, (int64_t)ou + i);
                     if (staged) {
                         const int64_t ov = __ldg(a.offp + v);
                         const int dv = (int)(__ldg(a.offp + v + 1) - ov);
@@ -668,7 +678,7 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                         const int64_t o64 = __ldg(a.offp + v);
                         ov = (uint32_t)o64;
                         dv = (int)(__ldg(a.offp + v + 1) - o64);
-                        if (dv > d || (kEdgeOnce<M> && a.considered != nullptr && a.considered[e])) dv = 0;
+                        if (dv > d || (kEdgeOnce<M> && a.considered != nullptr && considered_bit(a.considered, e))) dv = 0;
                     }
                     // algorithmic probes: a chunked N+(u) re-reads the lists, which is not counted
                     if (lane == 0 && c0 == 0) probes += (unsigned)dv;
@@ -722,7 +732,7 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                     const int64_t b0 = __ldg(a.offp + n0);
                     o0 = (uint32_t)b0;
                     d0 = (int)(__ldg(a.offp + n0 + 1) - b0);
-                    live0 = !kEdgeOnce<M> || a.considered == nullptr || !a.considered[ou + lane];
+                    live0 = !kEdgeOnce<M> || a.considered == nullptr || !considered_bit(a.considered, (int64_t)ou + lane);
                     if (live0) table_insert(tb, log_slots, n0, lane, a.err);
                     if (!live0 || d0 > d) d0 = 0;  // streamed from n0's side when d+(n0) > d+(u)
                 }
@@ -731,7 +741,8 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                     const int64_t b1 = __ldg(a.offp + n1);
                     o1 = (uint32_t)b1;
                     d1 = (int)(__ldg(a.offp + n1 + 1) - b1);
-                    live1 = !kEdgeOnce<M> || a.considered == nullptr || !a.considered[ou + lane + 32];
+                    live1 = !kEdgeOnce<M> || a.considered == nullptr ||
+                            !considered_bit(a.considered, (int64_t)ou + lane + 32);
                     if (live1) table_insert(tb, log_slots, n1, lane + 32, a.err);
                     if (!live1 || d1 > d) d1 = 0;
                 }
@@ -898,7 +909,7 @@ __device__ __forceinline__ int64_t arc_between(const int64_t *off, const int64_t
 enum Choice { kChoiceRandom = 0, kChoiceMaxw = 1, kChoiceMinCount = 2 };
 
 template <int CH>
-__global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uint8_t *considered) {
+__global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uint32_t *considered) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < a.n; u += nw) {
@@ -914,7 +925,7 @@ __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uin
             const int64_t f2 = arc_between(off, a.offp, a.colp, y, z);
             if (f1 < 0 || f2 < 0) continue;
             if (a.resv[f1] != (hi | y) || a.resv[f2] != (hi | (uint32_t)u)) continue;
-            considered[e] = 1;
+            set_considered(considered, e);
             // which edge of the accepted triangle goes
             uint32_t x0 = (uint32_t)u, x1 = y, x2 = z;
             int64_t e01 = e, e02 = f1, e12 = f2;
@@ -946,7 +957,7 @@ __global__ void eo_accept_kernel(TriArgs a, const int64_t *__restrict__ off, uin
 // accepted; accepted triangles are edge-disjoint, so their stores never race.
 template <int CH>
 __global__ void eo_list_accept_kernel(const TriRec *__restrict__ L, int64_t len,
-                                      const unsigned long long *__restrict__ resv, uint8_t *considered,
+                                      const unsigned long long *__restrict__ resv, uint32_t *considered,
                                       uint8_t *del, const float *__restrict__ wp, const uint32_t *__restrict__ tcnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
@@ -954,9 +965,9 @@ __global__ void eo_list_accept_kernel(const TriRec *__restrict__ L, int64_t len,
         if (r.x0 == kSentinel) continue;
         const unsigned long long hi = (unsigned long long)r.r2 << 32;
         if (resv[r.e01] != (hi | r.x2) || resv[r.e02] != (hi | r.x1) || resv[r.e12] != (hi | r.x0)) continue;
-        considered[r.e01] = 1;
-        considered[r.e02] = 1;
-        considered[r.e12] = 1;
+        set_considered(considered, (int64_t)r.e01);
+        set_considered(considered, (int64_t)r.e02);
+        set_considered(considered, (int64_t)r.e12);
         uint32_t chosen;
         if constexpr (CH == kChoiceMinCount) {
             chosen = mincount_arc(tcnt, r.e01, r.e02, r.e12);
@@ -982,7 +993,7 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
                                                               TriRec *__restrict__ out,
                                                               unsigned long long *out_len,
                                                               unsigned long long *resv,
-                                                              const uint8_t *__restrict__ considered,
+                                                              const uint32_t *__restrict__ considered,
                                                               unsigned long long theta) {
     __shared__ int s_cnt[8];
     __shared__ unsigned long long s_base;
@@ -994,7 +1005,8 @@ __global__ void __launch_bounds__(256) eo_list_reserve_kernel(const TriRec *__re
         TriRec r{kSentinel, 0, 0, 0, 0, 0, 0, 0};
         if (i < len) {
             r = L[i];
-            if (r.x0 != kSentinel && !(considered[r.e01] | considered[r.e02] | considered[r.e12])) {
+            if (r.x0 != kSentinel && !(considered_bit(considered, r.e01) | considered_bit(considered, r.e02) |
+                                       considered_bit(considered, r.e12))) {
                 keep = true;
                 if ((unsigned long long)r.r2 < theta) {
                     const unsigned long long hi = (unsigned long long)r.r2 << 32;
@@ -1032,7 +1044,7 @@ constexpr int kFreshPer = 4;
 __global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__restrict__ F, int64_t len,
                                                                TriRec *__restrict__ out, unsigned long long *out_len,
                                                                unsigned long long *resv,
-                                                               const uint8_t *__restrict__ considered,
+                                                               const uint32_t *__restrict__ considered,
                                                                unsigned long long theta,
                                                                const uint32_t *__restrict__ colp, uint32_t k0,
                                                                uint32_t k1) {
@@ -1050,7 +1062,8 @@ __global__ void __launch_bounds__(256) eo_fresh_reserve_kernel(const uint4 *__re
         }
 #pragma unroll
         for (int r = 0; r < kFreshPer; ++r)
-            keep[r] = f[r].x != kSentinel && !(considered[f[r].y] | considered[f[r].z] | considered[f[r].w]);
+            keep[r] = f[r].x != kSentinel && !(considered_bit(considered, f[r].y) | considered_bit(considered, f[r].z) |
+                                               considered_bit(considered, f[r].w));
         int cnt = 0;
 #pragma unroll
         for (int r = 0; r < kFreshPer; ++r) cnt += keep[r];
@@ -1283,7 +1296,8 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
 static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
     const size_t m = (size_t)std::max<int64_t>(o.m, 1);
     const int choice = k == SG_TR_EO_MAXW ? kChoiceMaxw : (k == SG_TR_EO_MINCOUNT ? kChoiceMinCount : kChoiceRandom);
-    uint8_t *considered = nullptr;
+    uint32_t *considered = nullptr;
+    const size_t cwords = (m + 31) / 32;
     unsigned long long *resv = nullptr, *lctr = nullptr;  // lctr: [kEoBuckets] bucket fills, then an out length
     int *lovf = nullptr;
     uint4 *L = nullptr;    // bucketed list written by the enumeration
@@ -1294,12 +1308,13 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     bool listed = false;
     const bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
     bool try_list = use_list;
-    sg_status st = dalloc(c, (void **)&considered, m);
+    sg_status st = dalloc(c, (void **)&considered, cwords * sizeof(uint32_t));
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
     if (st == SG_OK) st = dalloc(c, (void **)&lctr, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int));
     if (st == SG_OK) {
         lovf = reinterpret_cast<int *>(lctr + kEoBuckets + 1);
-        if (cudaMemsetAsync(considered, 0, m, c->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+        if (cudaMemsetAsync(considered, 0, cwords * sizeof(uint32_t), c->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "memset");
     }
     a.considered = considered;
     a.resv = resv;
