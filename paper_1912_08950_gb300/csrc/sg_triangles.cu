@@ -223,7 +223,8 @@ __device__ __forceinline__ I mincount_arc(const uint32_t *tcnt, I e01, I e02, I 
 // triangle pass valid = false.
 template <Mode M>
 __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u, uint32_t v, uint32_t w,
-                                       uint32_t iuv, uint32_t iuw, uint32_t ivw, unsigned &live, Emitter &em) {
+                                       uint32_t iuv, uint32_t iuw, uint32_t ivw, unsigned &live, Emitter &em,
+                                       uint32_t head_uv = 0) {
     if constexpr (M == Mode::Count || M == Mode::EdgeCount || M == Mode::VertexCount) {
         return;
     } else {
@@ -313,7 +314,7 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                         emit = true;
                         rec_r2 = r.z;
                         // w is last in the degree order; of u and v the head of iuv is the later one
-                        const bool u_first = __ldg(a.colp + iuv) == v;
+                        const bool u_first = head_uv == v;
                         rec = make_uint4(u_first ? u : v, iuv, u_first ? iuw : ivw, u_first ? ivw : iuw);
                     }
                 }
@@ -329,7 +330,10 @@ __device__ __forceinline__ void drain32_body(const TriArgs &a, const HitQueue &q
                                              unsigned &live, Emitter &em) {
     const int k = (head + (threadIdx.x & 31)) & (kQ - 1);
     const uint32_t iuw = q.iuw[k];
-    decide<M>(a, true, u, q.v[k], __ldg(a.colp + iuw), q.iuv[k], iuw, q.ivw[k], live, em);
+    const uint32_t iuv = q.iuv[k];
+    // the listing pass needs the head of u-v too: load it with w, before the draw
+    const uint32_t huv = M == Mode::EoEmit ? __ldg(a.colp + iuv) : 0u;
+    decide<M>(a, true, u, q.v[k], __ldg(a.colp + iuw), iuv, iuw, q.ivw[k], live, em, huv);
     __syncwarp();
 }
 template <Mode M>
@@ -363,8 +367,10 @@ __device__ __forceinline__ void flush_hits(const TriArgs &a, const HitQueue &q, 
         const bool valid = lane < qs.n;
         const int k = (qs.head + lane) & (kQ - 1);
         const uint32_t iuw = valid ? q.iuw[k] : 0u;
-        decide<M>(a, valid, u, valid ? q.v[k] : 0u, valid ? __ldg(a.colp + iuw) : 0u, valid ? q.iuv[k] : 0u, iuw,
-                  valid ? q.ivw[k] : 0u, live, em);
+        const uint32_t iuv = valid ? q.iuv[k] : 0u;
+        const uint32_t huv = (M == Mode::EoEmit && valid) ? __ldg(a.colp + iuv) : 0u;
+        decide<M>(a, valid, u, valid ? q.v[k] : 0u, valid ? __ldg(a.colp + iuw) : 0u, iuv, iuw,
+                  valid ? q.ivw[k] : 0u, live, em, huv);
         __syncwarp();
     }
     qs.head = 0;
