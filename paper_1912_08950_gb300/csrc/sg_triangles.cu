@@ -665,6 +665,10 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                     if (lane == 0) i = atomicAdd(&s_next, 1);
                     i = __shfl_sync(kFull, i, 0);
                     if (i >= items) break;
+                    {  // hand out the in-arc groups (the larger units) first, then the out-arcs
+                        const int ng = items - d;
+                        i = i < ng ? d + i : i - ng;
+                    }
                     if (i >= d) {  // 32 in-arcs v->u with d+(v) < d+(u): stream each N+(v)
                         const int g0 = (i - d) * 32;
                         stream_in_group<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)c0, ib, g0, min(32, nin - g0),
