@@ -307,9 +307,15 @@ __device__ __forceinline__ void decide(const TriArgs &a, bool valid, uint32_t u,
                         }
                         ++live;
                     }
-                } else {  // EoEmit: list the live selected triangle, bid later
+                } else {  // EoEmit: list the live selected triangle (and bid, in case the list overflows)
                     if (a.considered == nullptr || !(considered_bit(a.considered, e01) | considered_bit(a.considered, e02) |
                                                      considered_bit(a.considered, e12))) {
+                        if ((unsigned long long)r.z < a.eo_theta) {
+                            const unsigned long long hi = (unsigned long long)r.z << 32;
+                            atomicMin(a.resv + e01, hi | x2);
+                            atomicMin(a.resv + e02, hi | x1);
+                            atomicMin(a.resv + e12, hi | x0);
+                        }
                         ++live;
                         emit = true;
                         rec_r2 = r.z;
@@ -1299,9 +1305,10 @@ static TriArgs base_args(Ctx *c, const Oriented &o) {
 // the round in which it first bids.  Each later round works on lists alone:
 // the survivors of the last round plus this round's bucket are filtered
 // (triangles that lost an edge are dropped), bid and are compacted into the
-// next active list, so a listed triangle is read once before it bids.  If the
-// list does not fit, the round enumerates again and bids directly, accepting
-// from the edges' side; a later round retries the list once the live
+// next active list, so a listed triangle is read once before it bids.  The
+// listing pass also bids for its round's prefix, so if the list does not fit,
+// the round still completes from those bids, accepting from the edges' side;
+// later rounds enumerate and bid directly and retry the list once the live
 // triangles fit.
 static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, const Plan &pl, TriArgs a) {
     const size_t m = (size_t)std::max<int64_t>(o.m, 1);
@@ -1318,6 +1325,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     bool listed = false;
     const bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
     bool try_list = use_list;
+    bool bids_done = false;  // this round's bids came from a listing pass whose list overflowed
     sg_status st = dalloc(c, (void **)&considered, cwords * sizeof(uint32_t));
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
     if (st == SG_OK) st = dalloc(c, (void **)&lctr, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int));
@@ -1391,9 +1399,11 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                 live = fill[kEoBuckets];
                 if (live == 0) break;  // no live selected triangle is left
                 if (ovf) {
+                    // the pass bid like EoReserve: finish this round from the edges' side
                     dfree(c, L);
                     L = nullptr;
                     try_list = false;
+                    bids_done = true;
                 } else {
                     listed = true;
                     c->eo_listed += live;
@@ -1409,13 +1419,16 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         }
         if (!listed) {
             // ---- enumeration round that bids directly; acceptance from the edges' side
-            SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
-            a.considered = round == 0 ? nullptr : considered;
-            st = launch_enum<Mode::EoReserve>(c, a, pl);
-            a.considered = considered;
-            if (st != SG_OK) break;
-            st = read_ctr(c, kCtrLive, 1, &live);
-            if (st != SG_OK || live == 0) break;
+            if (!bids_done) {
+                SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+                a.considered = round == 0 ? nullptr : considered;
+                st = launch_enum<Mode::EoReserve>(c, a, pl);
+                a.considered = considered;
+                if (st != SG_OK) break;
+                st = read_ctr(c, kCtrLive, 1, &live);
+                if (st != SG_OK || live == 0) break;
+            }
+            bids_done = false;
             // retry the list next round once the live triangles fit it
             try_list = use_list && (double)live * 1.25 <= (double)list_capacity();
             ++c->eo_rounds;
