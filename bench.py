@@ -47,8 +47,8 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than sca
 # figure no longer describes the kernel and the JSON line reports null.
 MEASURED_TRAFFIC = {
     # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
-    # profiles/tri_enum_rmat22_tr_eo.md: 48.61 GB read + 17.09 GB written
-    ("rmat22", "tr_eo"): (65705235000, "2de0ec6f4e218802819d83c83b4dd1e34c5cd15d09e1e7340847a4238aba459d"),
+    # profiles/tri_enum_rmat22_tr_eo.md: 53.60 GB read + 18.83 GB written
+    ("rmat22", "tr_eo"): (72431613000, "26d5e27935b7b9ee64b4f1c0f64570ed1228807fa962a1af6b747b28a0097328"),
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 
