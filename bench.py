@@ -372,6 +372,8 @@ def run_ours(args, rank, world):
                      "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "eo_rounds_per_step": st["eo_rounds"] / args.steps,
+        "eo_passes_per_step": st["eo_passes"] / args.steps,
+        "eo_list_passes_per_step": st["eo_list_passes"] / args.steps,
         "gpu_launches": st["kernel_launches"],
         "clocks": clk,
         "e2e": {"value": replica_throughput(world, m, e2e_s), "unit": "edges/s",

@@ -121,6 +121,8 @@ typedef struct sg_stats {
     uint64_t triangles;       /* triangles found by triangle kernels */
     uint64_t eo_rounds;       /* Edge-Once reservation rounds run */
     uint64_t eo_listed;       /* triangles written to Edge-Once lists (16 bytes each) */
+    uint64_t eo_passes;       /* Edge-Once enumeration passes (each bids for its round) */
+    uint64_t eo_list_passes;  /* ... of them that listed triangles for later rounds */
 } sg_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -142,12 +144,16 @@ sg_status sg_ctx_stats(sg_ctx *ctx, sg_stats *out, int reset);
 sg_status sg_ctx_set_profiling(sg_ctx *ctx, int on);
 sg_status sg_ctx_kernel_time(sg_ctx *ctx, const char *prefix, double *ms, int64_t *launches);
 sg_status sg_ctx_reset_profile(sg_ctx *ctx);
-/* Memory bound of the Edge-Once kernels.  They keep the live selected
- * triangles in a device list (32 bytes per triangle) once it fits, so that
- * later reservation rounds need no new enumeration.  records > 0 caps the list
- * at that many triangles, 0 (default) sizes it at a quarter of free device
- * memory, -1 disables it (every round then enumerates the triangles again).
- * The result is the same in every setting; only time and memory change. */
+/* Memory bound of the Edge-Once kernels.  An enumeration lists the live
+ * selected triangles (16 bytes each, 32 once they bid), grouped by the round
+ * of the prefix schedule in which they first bid, so that later reservation
+ * rounds need no new enumeration.  When they do not all fit, the list keeps
+ * the earliest groups that do (a window of the schedule); once every triangle
+ * in the window is decided, one more enumeration lists the live ones above
+ * it.  records > 0 caps the list at that many triangles, 0 (default) sizes it
+ * at a quarter of free device memory, -1 disables it (every round then
+ * enumerates the triangles again).  The result is the same in every setting;
+ * only time and memory change. */
 sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records);
 
 /* ----------------------------------------------------------------- graphs */

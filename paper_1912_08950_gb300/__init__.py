@@ -58,7 +58,8 @@ class AccuracyResult(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("probes", C.c_uint64), ("triangles", C.c_uint64),
-                ("eo_rounds", C.c_uint64), ("eo_listed", C.c_uint64)]
+                ("eo_rounds", C.c_uint64), ("eo_listed", C.c_uint64), ("eo_passes", C.c_uint64),
+                ("eo_list_passes", C.c_uint64)]
 
 
 _vp, _i64, _u64, _int, _dbl, _flt = C.c_void_p, C.c_int64, C.c_uint64, C.c_int, C.c_double, C.c_float

@@ -226,10 +226,14 @@ sg_status sg_ctx_stats(sg_ctx *ctx, sg_stats *out, int reset) {
     out->triangles = v[kCtrTriangles];
     out->eo_rounds = c->eo_rounds;
     out->eo_listed = c->eo_listed;
+    out->eo_passes = c->eo_passes;
+    out->eo_list_passes = c->eo_list_passes;
     if (reset) {
         c->launches = 0;
         c->eo_rounds = 0;
         c->eo_listed = 0;
+        c->eo_passes = 0;
+        c->eo_list_passes = 0;
         SG_CUDA(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * 2, c->stream));
         SG_CUDA(cudaStreamSynchronize(c->stream));
     }

@@ -45,6 +45,8 @@ struct Ctx {
     uint64_t launches = 0;
     uint64_t eo_rounds = 0;
     uint64_t eo_listed = 0;                // triangles written to edge-once lists
+    uint64_t eo_passes = 0;                // edge-once enumeration passes
+    uint64_t eo_list_passes = 0;           // ... that listed triangles
     int64_t eo_list_cap = 0;               // 0 auto, -1 off, > 0 records
     bool profiling = false;
     std::vector<ProfRec> prof;             // events of launches since reset

@@ -98,9 +98,11 @@ struct TriArgs {
     // buckets by the round in which each first bids
     uint4 *list;
     unsigned long long *list_ctr;  // [kEoBuckets] slots handed out per bucket
+    unsigned long long *list_dem;  // [kEoBuckets] triangles that belong in each bucket, listed or not
     unsigned long long list_base[kEoBuckets], list_cap[kEoBuckets];
     int eo_round;                  // this enumeration's round: earlier buckets fold into it
-    int *list_overflow;
+    int eo_hi;                     // buckets from this one on are not listed (counted only)
+    int *list_overflow;            // bit b: bucket b ran out of room
 };
 
 // One live selected triangle of an active list: sorted original ids
@@ -125,10 +127,13 @@ __host__ __device__ constexpr int eo_chunk(int b) { return b <= 1 ? 64 : (32 << 
 // Per-warp list writer: per bucket it claims chunks of slots, fills them in
 // order and seals the unused tail of a chunk with sentinels.  The cursors
 // live in registers spread over the lanes: lane b holds the next free slot of
-// bucket b and lane 8 + b the end of its chunk.
+// bucket b, lane 8 + b the end of its chunk and lane 16 + b how many
+// triangles belong in bucket b.  Buckets from hi on are counted but not
+// written: those the caller left out, and any that ran out of room (the
+// lower buckets stay complete, so the caller can still use them).
 struct Emitter {
-    unsigned long long cur = 0;  // this lane's cursor (see above)
-    bool dead = false;
+    unsigned long long cur = 0;  // this lane's cursor or count (see above)
+    int hi = 0;                  // warp-uniform
 };
 
 __device__ __forceinline__ void emit_seal(const TriArgs &a, unsigned long long cur, unsigned long long end) {
@@ -137,21 +142,21 @@ __device__ __forceinline__ void emit_seal(const TriArgs &a, unsigned long long c
 }
 
 __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool want, const uint4 &rec, uint32_t r2) {
-    if (em.dead) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
     const int mb = want ? max(eo_bucket(r2), min(a.eo_round, kEoBuckets - 1)) : -1;
     if (!__any_sync(kFull, want)) return;
-    // lanes of my bucket, and (in lane b) the count of bucket b
+    // lanes of my bucket, and (in lanes b and 16 + b) the count of bucket b
     unsigned mine = 0, cnt_b = 0;
 #pragma unroll
     for (int b = 0; b < kEoBuckets; ++b) {
         const unsigned bm = __ballot_sync(kFull, mb == b);
         if (mb == b) mine = bm;
-        if (lane == b) cnt_b = (unsigned)__popc(bm);
+        if ((lane & 15) == b) cnt_b = (unsigned)__popc(bm);
     }
+    if (lane >= 16) em.cur += cnt_b;  // zero outside lanes 16 .. 16 + kEoBuckets - 1
     // a bucket whose chunk is too short for this group claims a new chunk (rare)
     const unsigned long long end_b = __shfl_down_sync(kFull, em.cur, 8);  // lane b: end of bucket b
-    unsigned need = __ballot_sync(kFull, lane < kEoBuckets && end_b - em.cur < cnt_b);
+    unsigned need = __ballot_sync(kFull, lane < em.hi && end_b - em.cur < cnt_b);
     while (need) {
         const int b = __ffs(need) - 1;
         need &= need - 1;
@@ -163,16 +168,17 @@ __device__ __forceinline__ void emit_push(const TriArgs &a, Emitter &em, bool wa
         if (lane == 0) base = atomicAdd(a.list_ctr + b, chunk);
         base = __shfl_sync(kFull, base, 0);
         if (base + chunk > a.list_cap[b]) {
-            if (lane == 0) atomicExch(a.list_overflow, 1);
-            em.dead = true;
-            return;
+            // out of room: bucket b and the ones above it are no longer written
+            if (lane == 0) atomicOr(a.list_overflow, 1 << b);
+            em.hi = b;
+            break;
         }
         if (lane == b) em.cur = a.list_base[b] + base;
         if (lane == 8 + b) em.cur = a.list_base[b] + base + chunk;
     }
     const unsigned long long cur = __shfl_sync(kFull, em.cur, mb < 0 ? 0 : mb);
-    if (want) a.list[cur + __popc(mine & lanemask_lt())] = rec;
-    if (lane < kEoBuckets) em.cur += cnt_b;
+    if (want && mb < em.hi) a.list[cur + __popc(mine & lanemask_lt())] = rec;
+    if (lane < em.hi) em.cur += cnt_b;
 }
 
 // Per-warp ring of found triangles, waiting to be decided 32 at a time.  The
@@ -581,9 +587,10 @@ template <Mode M>
 __device__ __forceinline__ void finish(const TriArgs &a, unsigned live, unsigned long long probes,
                                        unsigned long long tris, Emitter &em) {
     if constexpr (M == Mode::EoEmit) {
-        if (!em.dead)
-            for (int b = 0; b < kEoBuckets; ++b)
-                emit_seal(a, __shfl_sync(kFull, em.cur, b), __shfl_sync(kFull, em.cur, 8 + b));
+        for (int b = 0; b < em.hi; ++b)
+            emit_seal(a, __shfl_sync(kFull, em.cur, b), __shfl_sync(kFull, em.cur, 8 + b));
+        const int lane = threadIdx.x & 31;
+        if (lane >= 16 && lane < 16 + kEoBuckets && em.cur != 0) atomicAdd(a.list_dem + (lane - 16), em.cur);
     }
     const unsigned long long P = warp_sum(probes), T = warp_sum(tris);
     const unsigned L = warp_sum(live);
@@ -617,6 +624,7 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
     unsigned live = 0;
     unsigned long long probes = 0, tris = 0;
     Emitter em;
+    em.hi = a.eo_hi;
     const int64_t n_heavy = a.n_heavy_dev ? (int64_t)*a.n_heavy_dev : a.n_heavy;
 
     // ---- phase 1: heavy vertices
@@ -1315,22 +1323,29 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     const int choice = k == SG_TR_EO_MAXW ? kChoiceMaxw : (k == SG_TR_EO_MINCOUNT ? kChoiceMinCount : kChoiceRandom);
     uint32_t *considered = nullptr;
     const size_t cwords = (m + 31) / 32;
-    unsigned long long *resv = nullptr, *lctr = nullptr;  // lctr: [kEoBuckets] bucket fills, then an out length
+    // lctr: [kEoBuckets] bucket fills, [kEoBuckets] bucket counts, an out length, then the overflow bits
+    unsigned long long *resv = nullptr, *lctr = nullptr;
+    const size_t lctr_bytes = (2 * kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int);
     int *lovf = nullptr;
     uint4 *L = nullptr;    // bucketed list written by the enumeration
     TriRec *A = nullptr;   // active list: this round's bidders
     int64_t lenA = 0;
     int64_t ubase[kEoBuckets] = {}, used[kEoBuckets] = {};
+    // live selected triangles per bucket at the last listing pass: a bound on them now
+    unsigned long long dem[kEoBuckets] = {};
+    bool have_dem = false;
     int next_bucket = kEoBuckets;  // next bucket to merge into the active list
+    int top = kEoBuckets;          // the list holds every live triangle of the buckets below this one
+    int sched = 0;                 // step of the prefix schedule: bids come from r2 below the top of bucket sched
     bool listed = false;
-    const bool use_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
-    bool try_list = use_list;
-    bool bids_done = false;  // this round's bids came from a listing pass whose list overflowed
+    bool try_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
+    // warps of one enumeration launch, at most: each may leave a chunk per bucket part filled
+    const int64_t emit_warps = (int64_t)c->num_sms * 8 * kTW;
     sg_status st = dalloc(c, (void **)&considered, cwords * sizeof(uint32_t));
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
-    if (st == SG_OK) st = dalloc(c, (void **)&lctr, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int));
+    if (st == SG_OK) st = dalloc(c, (void **)&lctr, lctr_bytes);
     if (st == SG_OK) {
-        lovf = reinterpret_cast<int *>(lctr + kEoBuckets + 1);
+        lovf = reinterpret_cast<int *>(lctr + 2 * kEoBuckets + 1);
         if (cudaMemsetAsync(considered, 0, cwords * sizeof(uint32_t), c->stream) != cudaSuccess)
             st = cuda_fail(cudaGetLastError(), "memset");
     }
@@ -1347,108 +1362,138 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
         return cap;
     };
-    for (int round = 0; st == SG_OK; ++round) {
+    for (int round = 0; st == SG_OK; ++round, ++sched) {
         if (round > 100000) { st = fail(SG_ERR_TIMEOUT, "edge-once rounds did not converge"); break; }
-        const unsigned long long theta = round >= 5 ? (1ull << 32) : (1ull << (27 + round));
+        const int rb = std::min(sched, kEoBuckets - 1);
+        unsigned long long theta = 1ull << (27 + rb);
+        if (listed && top < kEoBuckets) theta = std::min(theta, 1ull << (26 + top));  // the list's window
         a.eo_theta = theta;
         unsigned long long live = 0;
-        if (!listed && try_list) {
-            // ---- enumerate and list the live selected triangles, no bids
-            const int64_t cap = list_capacity();
-            // bucket shares of the draws r2: 1,1,2,4,8,16 of 32; earlier buckets fold into this round's
-            const int rb = std::min(round, kEoBuckets - 1);
-            double w[kEoBuckets], wsum = 0.0;
-            for (int b = 0; b < kEoBuckets; ++b) w[b] = b < rb ? 0.0 : (b <= 1 ? 1.0 : (double)(1 << (b - 1)));
-            for (int b = 0; b < rb; ++b) w[rb] += b <= 1 ? 1.0 : (double)(1 << (b - 1));
-            for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
-            int64_t run = 0;
-            bool big = true;
-            for (int b = 0; b < kEoBuckets; ++b) {
-                const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
-                a.list_base[b] = (unsigned long long)run;
-                a.list_cap[b] = (unsigned long long)cb;
-                ubase[b] = run;
-                run += cb;
-                if (w[b] > 0.0 && cb < 4 * eo_chunk(b)) big = false;
+        if (!listed) {
+            bool bids_done = false;
+            int hi = 0;  // buckets [rb, hi) get room in the list
+            if (try_list) {
+                // ---- one enumeration bids for this round and lists the live selected
+                // triangles of as many buckets, from rb on, as the room allows
+                const int64_t cap = list_capacity();
+                hi = kEoBuckets;
+                int64_t run = 0;
+                for (int b = 0; b < kEoBuckets; ++b) a.list_base[b] = a.list_cap[b] = 0;
+                auto give = [&](int b, int64_t cb) {
+                    a.list_base[b] = (unsigned long long)run;
+                    a.list_cap[b] = (unsigned long long)cb;
+                    ubase[b] = run;
+                    run += cb;
+                };
+                if (!have_dem) {
+                    // no counts yet: the shares of the draws r2, 1,1,2,4,8,16 of 32 (earlier buckets fold into rb)
+                    double w[kEoBuckets], wsum = 0.0;
+                    for (int b = 0; b < kEoBuckets; ++b) w[b] = b <= 1 ? 1.0 : (double)(1 << (b - 1));
+                    for (int b = 0; b < rb; ++b) { w[rb] += w[b]; w[b] = 0.0; }
+                    for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
+                    for (int b = rb; b < kEoBuckets; ++b) {
+                        const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
+                        if (cb < 4 * eo_chunk(b)) { hi = b; break; }
+                        give(b, cb);
+                    }
+                } else {
+                    // the last pass's counts bound each bucket; add room for sealed chunk tails
+                    unsigned long long fold = 0;
+                    for (int b = 0; b <= rb; ++b) fold += dem[b];
+                    for (int b = rb; b < kEoBuckets; ++b) {
+                        const double d = (double)(b == rb ? fold : dem[b]);
+                        const int64_t want = (int64_t)(d * (1.0 + 16.0 / eo_chunk(b))) + emit_warps * eo_chunk(b);
+                        const int64_t cb = std::min<int64_t>(want, cap - run);
+                        if (cb < 4 * eo_chunk(b)) { hi = b; break; }
+                        give(b, cb);
+                        if (cb < want) { hi = b + 1; break; }  // may still fit: the bound is loose
+                    }
+                }
+                if (hi <= rb) hi = 0;  // nothing to list: the pass only bids and counts
+                if (hi > 0 && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(uint4)) != SG_OK) {
+                    L = nullptr;
+                    set_error("");
+                    try_list = false;
+                }
             }
-            if (big && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(uint4)) == SG_OK) {
+            if (try_list) {
                 a.list = L;
                 a.list_ctr = lctr;
+                a.list_dem = lctr + kEoBuckets;
                 a.list_overflow = lovf;
-                a.eo_round = round;
-                SG_CUDA(cudaMemsetAsync(lctr, 0, (kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int),
-                                        c->stream));
+                a.eo_round = rb;
+                a.eo_hi = L != nullptr ? hi : 0;
+                SG_CUDA(cudaMemsetAsync(lctr, 0, lctr_bytes, c->stream));
                 SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
                 // nothing is considered before the first acceptance: skip the flag reads
                 a.considered = round == 0 ? nullptr : considered;
                 st = launch_enum<Mode::EoEmit>(c, a, pl);
+                ++c->eo_passes;
                 a.considered = considered;
                 a.list = nullptr;
                 if (st != SG_OK) break;
-                unsigned long long fill[kEoBuckets + 1];
+                unsigned long long fill[2 * kEoBuckets + 1];
                 int ovf = 0;
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, kEoBuckets * sizeof(unsigned long long),
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned, lctr, 2 * kEoBuckets * sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, c->stream));
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned + kEoBuckets, c->d_ctr + kCtrLive, sizeof(unsigned long long),
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned + 2 * kEoBuckets, c->d_ctr + kCtrLive, sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, c->stream));
-                SG_CUDA(cudaMemcpyAsync(c->h_pinned + kEoBuckets + 1, lovf, sizeof(int), cudaMemcpyDeviceToHost,
+                SG_CUDA(cudaMemcpyAsync(c->h_pinned + 2 * kEoBuckets + 1, lovf, sizeof(int), cudaMemcpyDeviceToHost,
                                         c->stream));
                 SG_CUDA(cudaStreamSynchronize(c->stream));
                 std::memcpy(fill, c->h_pinned, sizeof(fill));
-                std::memcpy(&ovf, c->h_pinned + kEoBuckets + 1, sizeof(int));
-                live = fill[kEoBuckets];
+                std::memcpy(&ovf, c->h_pinned + 2 * kEoBuckets + 1, sizeof(int));
+                live = fill[2 * kEoBuckets];
+                for (int b = 0; b < kEoBuckets; ++b) dem[b] = fill[kEoBuckets + b];
+                have_dem = true;
                 if (live == 0) break;  // no live selected triangle is left
-                if (ovf) {
-                    // the pass bid like EoReserve: finish this round from the edges' side
-                    dfree(c, L);
-                    L = nullptr;
-                    try_list = false;
-                    bids_done = true;
-                } else {
+                // the buckets below the first one that ran out of room are complete
+                const int wtop = a.eo_hi > 0 ? std::min(a.eo_hi, ovf ? __builtin_ctz((unsigned)ovf) : kEoBuckets) : 0;
+                if (wtop > rb) {
                     listed = true;
-                    c->eo_listed += live;
-                    for (int b = 0; b < kEoBuckets; ++b)
-                        used[b] = (int64_t)std::min<unsigned long long>(fill[b], a.list_cap[b]);
+                    top = wtop;
+                    for (int b = 0; b < kEoBuckets; ++b) used[b] = b >= rb && b < top ? (int64_t)fill[b] : 0;
+                    for (int b = rb; b < top; ++b) c->eo_listed += dem[b];
+                    ++c->eo_list_passes;
                     next_bucket = rb;
+                } else {
+                    dfree(c, L);  // this round's bids are in: finish it from the edges' side
+                    L = nullptr;
+                    bids_done = true;
                 }
-            } else {
-                L = nullptr;
-                set_error("");
-                try_list = false;
             }
-        }
-        if (!listed) {
-            // ---- enumeration round that bids directly; acceptance from the edges' side
-            if (!bids_done) {
-                SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
-                a.considered = round == 0 ? nullptr : considered;
-                st = launch_enum<Mode::EoReserve>(c, a, pl);
-                a.considered = considered;
-                if (st != SG_OK) break;
-                st = read_ctr(c, kCtrLive, 1, &live);
-                if (st != SG_OK || live == 0) break;
+            if (!listed) {
+                // ---- enumeration round that bids directly; acceptance from the edges' side
+                if (!bids_done) {
+                    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrLive, 0, sizeof(unsigned long long), c->stream));
+                    a.considered = round == 0 ? nullptr : considered;
+                    st = launch_enum<Mode::EoReserve>(c, a, pl);
+                    ++c->eo_passes;
+                    a.considered = considered;
+                    if (st != SG_OK) break;
+                    st = read_ctr(c, kCtrLive, 1, &live);
+                    if (st != SG_OK || live == 0) break;
+                }
+                ++c->eo_rounds;
+                SG_LAUNCH(c, "tri_eo_accept");
+                if (choice == kChoiceMaxw)
+                    eo_accept_kernel<kChoiceMaxw><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+                else if (choice == kChoiceMinCount)
+                    eo_accept_kernel<kChoiceMinCount><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off,
+                                                                                                  considered);
+                else
+                    eo_accept_kernel<kChoiceRandom><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
+                SG_CUDA(cudaGetLastError());
+                SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
+                continue;
             }
-            bids_done = false;
-            // retry the list next round once the live triangles fit it
-            try_list = use_list && (double)live * 1.25 <= (double)list_capacity();
-            ++c->eo_rounds;
-            SG_LAUNCH(c, "tri_eo_accept");
-            if (choice == kChoiceMaxw)
-                eo_accept_kernel<kChoiceMaxw><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
-            else if (choice == kChoiceMinCount)
-                eo_accept_kernel<kChoiceMinCount><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
-            else
-                eo_accept_kernel<kChoiceRandom><<<(unsigned)acc_blocks, 256, 0, c->stream>>>(a, g->off, considered);
-            SG_CUDA(cudaGetLastError());
-            SG_CUDA(cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream));
-            continue;
         }
         // ---- list round: last round's survivors plus this round's bucket
-        const int64_t fresh = next_bucket < kEoBuckets ? used[next_bucket] : 0;
+        const int64_t fresh = next_bucket < top ? used[next_bucket] : 0;
         TriRec *B = nullptr;
         st = dalloc(c, (void **)&B, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec));
         if (st != SG_OK) break;
-        unsigned long long *out_len = lctr + kEoBuckets;
+        unsigned long long *out_len = lctr + 2 * kEoBuckets;
         SG_CUDA(cudaMemsetAsync(out_len, 0, sizeof(unsigned long long), c->stream));
         if (lenA > 0) {
             SG_LAUNCH(c, "tri_eo_list_reserve");
@@ -1461,7 +1506,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                                       c->stream>>>(
                 L + ubase[next_bucket], fresh, B, out_len, resv, considered, theta, a.colp, a.k0, a.k1);
         }
-        if (next_bucket < kEoBuckets) ++next_bucket;
+        if (next_bucket < top) ++next_bucket;
         SG_CUDA(cudaGetLastError());
         SG_CUDA(cudaMemcpyAsync(c->h_pinned, out_len, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
         SG_CUDA(cudaStreamSynchronize(c->stream));
@@ -1470,8 +1515,15 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         A = B;
         lenA = (int64_t)live;
         if (live == 0) {
-            if (next_bucket >= kEoBuckets) break;  // no triangle left anywhere
-            continue;                              // nothing bid this round
+            if (next_bucket < top) continue;  // nothing bid this round
+            if (top >= kEoBuckets) break;     // no triangle left anywhere
+            // every triangle of the list's window is decided: list the live ones
+            // above it, starting the schedule at its first bucket
+            dfree(c, L);
+            L = nullptr;
+            listed = false;
+            sched = top - 1;
+            continue;
         }
         ++c->eo_rounds;
         // ---- accept: triangles holding all three reservations.  Judging from

@@ -132,17 +132,44 @@ def test_triangle_count(sg, ctx, rmat14):
         G.free()
 
 
-@pytest.mark.parametrize("cap", [-1, 4096, 60000, 0])
-@pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw", "tr_eo_mincount"])
-def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
-    # -1: enumerate every round; small caps overflow and fall back to the edge
-    # pass, then retry the list in a later round; 0: automatic
-    g = gg.attach_weights(gg.rmat(13, 16, seed=8), seed=8)
+def _eo_run(sg, ctx, g, kern, p, seed, cap):
     ctx.set_eo_list_capacity(cap)
     try:
-        _same(sg, ctx, g, kern, 0.7, 4)
+        ctx.stats(reset=True)
+        _same(sg, ctx, g, kern, p, seed)
+        return ctx.stats(reset=True)
     finally:
         ctx.set_eo_list_capacity(0)
+
+
+@pytest.mark.parametrize("cap", [-1, 4096, 60000, 250000, 0])
+@pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw", "tr_eo_mincount"])
+def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
+    # -1: enumerate every round.  Small caps: a listing pass that runs out of
+    # room in its first bucket only bids, and later passes list the buckets
+    # that fit (a window of the schedule), list again above the window once
+    # it is decided, and so on.  0: automatic (everything fits)
+    g = gg.attach_weights(gg.rmat(13, 16, seed=8), seed=8)
+    st = _eo_run(sg, ctx, g, kern, 0.7, 4, cap)
+    # every pass but a last one that finds nothing live ends in a round
+    assert 1 <= st["eo_passes"] <= st["eo_rounds"] + 1
+    if cap == 0:
+        assert st["eo_passes"] == 1 and st["eo_list_passes"] == 1
+    if cap == -1:
+        assert st["eo_listed"] == 0 and st["eo_list_passes"] == 0
+        assert st["eo_passes"] == st["eo_rounds"] + 1
+
+
+def test_eo_list_windows(sg, ctx):
+    # caps between the first bucket and the whole list: some pass lists a
+    # window of the schedule and a later pass lists the triangles above it
+    g = gg.rmat(14, 16, seed=5)
+    relisted = 0
+    for cap in (30000, 100000, 300000, 1000000):
+        st = _eo_run(sg, ctx, g, "tr_eo", 0.6, 9, cap)
+        assert st["eo_list_passes"] <= st["eo_passes"] <= st["eo_rounds"] + 1
+        relisted += st["eo_list_passes"] >= 2
+    assert relisted > 0
 
 
 def test_deterministic_repeats(sg, ctx, rmat14):
