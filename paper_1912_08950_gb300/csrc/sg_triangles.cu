@@ -44,7 +44,7 @@ constexpr int kLightMax = 64;     // largest out-degree processed by one warp
 constexpr int kLightItems = 256;  // ... with at most this many lists to stream
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
-constexpr int kHeavyCap = 512;   // largest phase-1 table (entries)
+constexpr int kHeavyCap = 1024;  // largest phase-1 table (entries; 26 KB of shared memory)
 constexpr int kQ = 128;           // per-warp hit ring (<= 31 left over + 2 slabs of hits fit)
 constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
 
@@ -391,61 +391,84 @@ __device__ __forceinline__ void flush_hits(const TriArgs &a, const HitQueue &q, 
 
 // Shared-memory cuckoo table of N+(u) (Pagh & Rodler's cuckoo hashing; the
 // concurrent exchange-based insertion follows Alcantara et al.'s GPU tables):
-// a slot holds (vertex << 32 | position in N+(u)); every key lives in one of
-// two slots, so a lookup reads exactly two slots with no probe loop and no
-// divergence.  Load <= 1/4.  An insertion that keeps displacing keys for
-// kCuckooIters exchanges leaves its homeless entry in a small stash that
-// lookups then scan; a full stash raises a device error.
-// an empty slot's key is 0xFFFFFFFE: never a vertex (ids stay below 2^32 - 2) and not kEmpty
-constexpr unsigned long long kSlotEmpty = 0xFFFFFFFEFFFFFFFFull;
+// every key lives in one of two slots, so a lookup reads exactly two slots
+// with no probe loop and no divergence.  Load <= 1/4.  An insertion that
+// keeps displacing keys for kCuckooIters exchanges leaves its homeless entry
+// in a small stash that lookups then scan; a full stash raises a device error.
+//
+// A table of 2^L slots puts key w in slot h_j(w) = (w * K_j) >> (32 - L),
+// j = 1 or 2.  The slot's 32-bit word keeps the low 32 - L bits of w * K_j
+// (the slot number holds the high L bits, and multiplying by an odd K_j is a
+// bijection, so word and slot give w back), which hash placed it, and w's
+// position in N+(u) (< 2^(L-2) at load 1/4):
+//   bits [L, 32): low bits of w * K_j;  bit L-1: j - 1;  bit L-2: 0;  bits [0, L-2): position
+// An empty slot is all ones (bit L-2 set), so it matches no key, and since
+// the word and slot pin down w, kEmpty (past a list's end) matches none either.
+constexpr uint32_t kSlotEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kH1 = 0x9E3779B1u, kH2 = 0x85EBCA77u;
+// inverse of an odd k modulo 2^32 (Newton's iteration doubles the correct low bits)
+constexpr uint32_t inv_mod32(uint32_t k) {
+    uint32_t x = k;  // k * k == 1 mod 8
+    for (int i = 0; i < 5; ++i) x *= 2u - k * x;
+    return x;
+}
+constexpr uint32_t kH1Inv = inv_mod32(kH1), kH2Inv = inv_mod32(kH2);
+static_assert(kH1 * kH1Inv == 1u && kH2 * kH2Inv == 1u, "hash multipliers must be invertible");
+// a stash entry is (vertex << 32 | position); this marks "not in the stash"
+constexpr unsigned long long kStashNone = 0xFFFFFFFEFFFFFFFFull;
 constexpr int kCuckooIters = 32;
 constexpr int kStash = 16;
 
 struct Table {
-    unsigned long long *slot;
+    uint32_t *slot;
     unsigned long long *stash;
     int *stash_n;
 };
 
-__device__ __forceinline__ uint32_t h1_of(uint32_t w, int sh) { return (w * 0x9E3779B1u) >> sh; }
-__device__ __forceinline__ uint32_t h2_of(uint32_t w, int sh) { return (w * 0x85EBCA77u) >> sh; }
-
 __device__ __forceinline__ void table_insert(const Table &t, int log_slots, uint32_t w, int i, int *err) {
-    const int sh = 32 - log_slots;
-    unsigned long long cur = ((unsigned long long)w << 32) | (uint32_t)i;
-    uint32_t pos = h1_of(w, sh);
+    const int L = log_slots, sh = 32 - L;
+    const uint32_t pmask = (1u << (L - 2)) - 1u;
+    uint32_t x = w * kH1;
+    uint32_t pos = x >> sh;
+    uint32_t cur = (x << L) | (uint32_t)i;
     for (int it = 0; it < kCuckooIters; ++it) {
-        const unsigned long long old = atomicExch(t.slot + pos, cur);
+        const uint32_t old = atomicExch(t.slot + pos, cur);
         if (old == kSlotEmpty) return;
-        cur = old;
-        const uint32_t k = (uint32_t)(old >> 32);
-        const uint32_t p1 = h1_of(k, sh);
-        pos = (pos == p1) ? h2_of(k, sh) : p1;
+        // the evicted key moves to its other slot
+        const bool by2 = (old >> (L - 1)) & 1u;
+        const uint32_t wo = ((pos << sh) | (old >> L)) * (by2 ? kH2Inv : kH1Inv);
+        x = wo * (by2 ? kH1 : kH2);
+        pos = x >> sh;
+        cur = (x << L) | ((by2 ? 0u : 1u) << (L - 1)) | (old & pmask);
     }
+    const bool by2 = (cur >> (L - 1)) & 1u;
+    const uint32_t wo = ((pos << sh) | (cur >> L)) * (by2 ? kH2Inv : kH1Inv);
     const int s = atomicAdd(t.stash_n, 1);
-    if (s < kStash) t.stash[s] = cur;
+    if (s < kStash) t.stash[s] = ((unsigned long long)wo << 32) | (cur & pmask);
     else atomicExch(err, (int)kDevTableFull);
 }
 
-// w in the table's two slots?  t receives its position in N+(u).  kEmpty (a
-// lane past the end of its list) matches neither an empty slot nor a vertex.
+// w in the table's two slots?  t receives its position in N+(u).
 __device__ __forceinline__ bool table_find(const Table &tb, int sh, uint32_t w, uint32_t &t) {
-    const unsigned long long a = tb.slot[h1_of(w, sh)];
-    const unsigned long long b = tb.slot[h2_of(w, sh)];
-    t = (uint32_t)a;
-    if ((uint32_t)(a >> 32) == w) return true;
-    t = (uint32_t)b;
-    return (uint32_t)(b >> 32) == w;
+    const int L = 32 - sh;
+    const uint32_t lim = 1u << (L - 2);
+    const uint32_t x1 = w * kH1, x2 = w * kH2;
+    const uint32_t a = tb.slot[x1 >> sh];
+    const uint32_t b = tb.slot[x2 >> sh];
+    const bool ha = (a ^ (x1 << L)) < lim;
+    const bool hb = (b ^ ((x2 << L) | (lim << 1))) < lim;
+    t = (ha ? a : b) & (lim - 1u);
+    return ha | hb;
 }
 
 // w in the stash (the rare table whose insertion left keys there)?  Returns
-// the slot word (key << 32 | position), or kSlotEmpty.
+// the stash entry (vertex << 32 | position), or kStashNone.
 __device__ __noinline__ unsigned long long stash_find(const unsigned long long *stash, int stash_n, uint32_t w) {
     for (int k = 0; k < stash_n; ++k) {
         const unsigned long long c = stash[k];
         if ((uint32_t)(c >> 32) == w) return c;
     }
-    return kSlotEmpty;
+    return kStashNone;
 }
 
 // First two 32-element slabs of the list colp[ov, ov + dv) (kEmpty past its end).
@@ -484,12 +507,12 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
         if (stash_n != 0) {  // warp-uniform and rare
             if (!ha) {
                 const unsigned long long c = stash_find(tb.stash, stash_n, wa);
-                ha = c != kSlotEmpty;
+                ha = c != kStashNone;
                 ta = (uint32_t)c;
             }
             if (!hb) {
                 const unsigned long long c = stash_find(tb.stash, stash_n, wb);
-                hb = c != kSlotEmpty;
+                hb = c != kStashNone;
                 tb2 = (uint32_t)c;
             }
         }
@@ -607,10 +630,14 @@ __device__ __forceinline__ void finish(const TriArgs &a, unsigned live, unsigned
 // out-neighbour's list bounds) and its warps claim out-arcs one at a time and
 // in-arcs 32 at a time.  Phase 2: light vertices, a warp per vertex with its
 // own small table; warps claim 32 vertex ids at a time.  Probe and triangle
-// totals are counted per list and per found triangle.  The listing pass keeps
-// more registers per thread (4 CTAs per SM): its record assembly spills at 48.
+// totals are counted per list and per found triangle.  The counting passes
+// run 5 CTAs per SM at 48 registers; the passes that decide triangles keep 64
+// (4 CTAs per SM): at 48 their queue drain and record assembly spill.
 template <Mode M>
-__global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_kernel(TriArgs a) {
+constexpr int kEnumCtasPerSm = (M == Mode::Count || M == Mode::EdgeCount || M == Mode::VertexCount) ? 5 : 4;
+
+template <Mode M>
+__global__ void __launch_bounds__(kTW * 32, kEnumCtasPerSm<M>) tri_enum_kernel(TriArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next;
     __shared__ long long s_h;
@@ -631,10 +658,10 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
     {
         const int cap = a.heavy_cap;  // table capacity: larger N+(u) is processed in chunks
         const int slots = 4 * cap;
-        Table tb{reinterpret_cast<unsigned long long *>(tbl), s_stash[kTW], &s_stash_n[kTW]};
-        uint32_t *vv = reinterpret_cast<uint32_t *>(tb.slot + slots);  // v, off+(v), d+(v) of N+(u)
+        Table tb{reinterpret_cast<uint32_t *>(tbl), s_stash[kTW], &s_stash_n[kTW]};
+        uint32_t *vv = tb.slot + slots;  // v, off+(v), d+(v) of N+(u)
         uint32_t *vo = vv + cap;
-        int *vd = reinterpret_cast<int *>(vo + cap);
+        unsigned short *vd = reinterpret_cast<unsigned short *>(vo + cap);  // d+(v) <= d+(u) <= cap, else 0
         for (;;) {
             if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.work, 1ull);
             __syncthreads();
@@ -668,7 +695,7 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
                         vo[i] = (uint32_t)ov;
                         // a considered arc u->v closes no live triangle; an arc
                         // with d+(v) > d+(u) is streamed from v's side
-                        vd[i] = (dead || dv > d) ? 0 : dv;
+                        vd[i] = (unsigned short)((dead || dv > d) ? 0 : dv);
                     }
                     if (!dead) table_insert(tb, log_slots, v, k, a.err);
                 }
@@ -719,7 +746,7 @@ __global__ void __launch_bounds__(kTW * 32, M == Mode::EoEmit ? 4 : 5) tri_enum_
 
     // ---- phase 2: light vertices
     {
-        Table tb{reinterpret_cast<unsigned long long *>(tbl) + warp * kLightSlots, s_stash[warp], &s_stash_n[warp]};
+        Table tb{reinterpret_cast<uint32_t *>(tbl) + warp * kLightSlots, s_stash[warp], &s_stash_n[warp]};
         for (;;) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(a.work + 1, 32ull);
@@ -1237,12 +1264,12 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
     // shared memory: hit queues + the larger of the heavy table (4 slots per
     // entry, load <= 1/4, with the list bounds of N+(u)) and the light tables
     const size_t queue_bytes = sizeof(HitQueue) * kTW;
-    const size_t light_bytes = (size_t)kTW * kLightSlots * 8;
+    const size_t light_bytes = (size_t)kTW * kLightSlots * sizeof(uint32_t);
     int cap = 8;
     while (cap < pl->max_deg && cap < kHeavyCap) cap *= 2;
     pl->heavy_cap = cap;
     pl->log_slots = ceil_log2_host(4 * cap);
-    const size_t heavy_bytes = (size_t)cap * (4 * 8 + 12);
+    const size_t heavy_bytes = (size_t)cap * (4 * sizeof(uint32_t) + 2 * sizeof(uint32_t) + sizeof(unsigned short));
     pl->smem = queue_bytes + std::max(light_bytes, heavy_bytes);
     return SG_OK;
 }
