@@ -337,6 +337,18 @@ def from_edge_list(n: int, edges) -> CSR:
     return csr_from_edges(n, e[:, 0], e[:, 1])
 
 
+def biclique_matched(k: int) -> CSR:
+    """K_{k,k} (left ids 0..k-1, right ids k..2k-1) plus a perfect matching of
+    the left side (k even).  The left vertices get degree k + 1, so in the
+    degree order every right vertex has all k left vertices above it
+    (out-degree k), and each matching edge closes a triangle with every right
+    vertex: k/2 * k triangles over k*k + k/2 edges."""
+    left = torch.arange(k, dtype=torch.int64).repeat_interleave(k)
+    right = k + torch.arange(k, dtype=torch.int64).repeat(k)
+    ml = torch.arange(0, k - 1, 2, dtype=torch.int64)
+    return csr_from_edges(2 * k, torch.cat([left, ml]), torch.cat([right, ml + 1]))
+
+
 def complete(k: int) -> CSR:
     return from_edge_list(k, [(i, j) for i in range(k) for j in range(i + 1, k)])
 

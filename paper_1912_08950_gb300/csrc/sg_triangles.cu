@@ -45,6 +45,8 @@ constexpr int kLightItems = 256;  // ... with at most this many lists to stream
 constexpr int kLightSlots = 256;  // hash slots per warp (>= 4 * kLightMax)
 constexpr int kTW = 8;            // warps per CTA
 constexpr int kHeavyCap = 1024;  // largest phase-1 table (entries; 26 KB of shared memory)
+constexpr int kHubTW = 32;        // warps per CTA of the hub launch (one CTA per SM)
+constexpr int kHubCap = 4096;     // largest hub table (entries; 104 KB of shared memory)
 constexpr int kQ = 128;           // per-warp hit ring (<= 31 left over + 2 slabs of hits fit)
 constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
 
@@ -633,18 +635,23 @@ __device__ __forceinline__ void finish(const TriArgs &a, unsigned live, unsigned
 // totals are counted per list and per found triangle.  The counting passes
 // run 5 CTAs per SM at 48 registers; the passes that decide triangles keep 64
 // (4 CTAs per SM): at 48 their queue drain and record assembly spill.
+//
+// The hub launch (TW = kHubTW) runs phase 1 alone, before the main launch,
+// over the vertices whose N+(u) is too long for the main launch's table: one
+// CTA of 32 warps per SM shares a table of up to kHubCap entries, so those
+// lists are streamed once instead of once per table chunk.
 template <Mode M>
 constexpr int kEnumCtasPerSm = (M == Mode::Count || M == Mode::EdgeCount || M == Mode::VertexCount) ? 5 : 4;
 
-template <Mode M>
-__global__ void __launch_bounds__(kTW * 32, kEnumCtasPerSm<M>) tri_enum_kernel(TriArgs a) {
+template <Mode M, int TW>
+__global__ void __launch_bounds__(TW * 32, TW == kTW ? kEnumCtasPerSm<M> : 1) tri_enum_kernel(TriArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next;
     __shared__ long long s_h;
-    __shared__ int s_stash_n[kTW + 1];
-    __shared__ unsigned long long s_stash[kTW + 1][kStash];
+    __shared__ int s_stash_n[TW + 1];
+    __shared__ unsigned long long s_stash[TW + 1][kStash];
     HitQueue *qs = reinterpret_cast<HitQueue *>(smem);
-    unsigned char *tbl = smem + sizeof(HitQueue) * kTW;
+    unsigned char *tbl = smem + sizeof(HitQueue) * TW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     HitQueue &q = qs[warp];
     QState qst;
@@ -658,7 +665,7 @@ __global__ void __launch_bounds__(kTW * 32, kEnumCtasPerSm<M>) tri_enum_kernel(T
     {
         const int cap = a.heavy_cap;  // table capacity: larger N+(u) is processed in chunks
         const int slots = 4 * cap;
-        Table tb{reinterpret_cast<uint32_t *>(tbl), s_stash[kTW], &s_stash_n[kTW]};
+        Table tb{reinterpret_cast<uint32_t *>(tbl), s_stash[TW], &s_stash_n[TW]};
         uint32_t *vv = tb.slot + slots;  // v, off+(v), d+(v) of N+(u)
         uint32_t *vo = vv + cap;
         unsigned short *vd = reinterpret_cast<unsigned short *>(vo + cap);  // d+(v) <= d+(u) <= cap, else 0
@@ -745,7 +752,7 @@ __global__ void __launch_bounds__(kTW * 32, kEnumCtasPerSm<M>) tri_enum_kernel(T
     }
 
     // ---- phase 2: light vertices
-    {
+    if constexpr (TW == kTW) {
         Table tb{reinterpret_cast<uint32_t *>(tbl) + warp * kLightSlots, s_stash[warp], &s_stash_n[warp]};
         for (;;) {
             unsigned long long base = 0;
@@ -833,6 +840,8 @@ __global__ void __launch_bounds__(kTW * 32, kEnumCtasPerSm<M>) tri_enum_kernel(T
 // counts the vertices of each bucket (and the maximum out-degree), pass 2
 // scatters them so that larger buckets come first.
 constexpr int kBuckets = 52;  // floor(log2) of the work bound d+ (d+ + in-arcs)
+// sort keys: the bucket, plus kBuckets for a hub (d+ > hub_min), so hubs come first
+constexpr int kKeys = 2 * kBuckets;
 
 __device__ __forceinline__ int bucket_of(unsigned long long d) { return 63 - __clzll(d); }
 
@@ -844,6 +853,9 @@ __device__ __forceinline__ bool is_heavy(int64_t d, int64_t nin, int light_max, 
 }
 __device__ __forceinline__ int heavy_bucket(int64_t d, int64_t nin) {
     return min(bucket_of((unsigned long long)d * (unsigned long long)(d + nin)), kBuckets - 1);
+}
+__device__ __forceinline__ int heavy_key(int64_t d, int64_t nin, int64_t hub_min) {
+    return heavy_bucket(d, nin) + (d > hub_min ? kBuckets : 0);
 }
 
 // In-arcs streamed from the head's side: for every arc u->v of E+ with
@@ -885,10 +897,10 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
 // already flagged by the scatter, can exceed it), so that no later read
 // leaves the in-arc array.
 __global__ void classify_count_kernel(const int64_t *__restrict__ offp, const int64_t *__restrict__ offs,
-                                      uint32_t *din, int64_t n, int light_max, int light_items,
+                                      uint32_t *din, int64_t n, int light_max, int light_items, int64_t hub_min,
                                       unsigned long long *bucket_cnt, unsigned long long *ctr) {
-    __shared__ unsigned int s_cnt[kBuckets];
-    if (threadIdx.x < kBuckets) s_cnt[threadIdx.x] = 0;
+    __shared__ unsigned int s_cnt[kKeys];
+    if (threadIdx.x < kKeys) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned long long dmax = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -903,7 +915,7 @@ __global__ void classify_count_kernel(const int64_t *__restrict__ offp, const in
                 din[u] = (uint32_t)nin;
             }
         }
-        if (is_heavy(d, nin, light_max, light_items)) atomicAdd(&s_cnt[heavy_bucket(d, nin)], 1u);
+        if (is_heavy(d, nin, light_max, light_items)) atomicAdd(&s_cnt[heavy_key(d, nin, hub_min)], 1u);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -912,18 +924,18 @@ __global__ void classify_count_kernel(const int64_t *__restrict__ offp, const in
     }
     if ((threadIdx.x & 31) == 0) atomicMax(ctr + kCtrMaxDeg, dmax);
     __syncthreads();
-    if (threadIdx.x < kBuckets && s_cnt[threadIdx.x]) atomicAdd(bucket_cnt + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+    if (threadIdx.x < kKeys && s_cnt[threadIdx.x]) atomicAdd(bucket_cnt + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
 }
 
 __global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, const uint32_t *__restrict__ din,
-                                        int64_t n, int light_max, int light_items,
+                                        int64_t n, int light_max, int light_items, int64_t hub_min,
                                         const unsigned long long *__restrict__ bucket_cnt,
                                         unsigned long long *bucket_fill, uint32_t *heavy,
                                         unsigned long long *total_out) {
-    __shared__ unsigned long long s_off[kBuckets];
+    __shared__ unsigned long long s_off[kKeys];
     if (threadIdx.x == 0) {
         unsigned long long run = 0;
-        for (int b = kBuckets - 1; b >= 0; --b) {
+        for (int b = kKeys - 1; b >= 0; --b) {
             s_off[b] = run;
             run += bucket_cnt[b];
         }
@@ -935,7 +947,7 @@ __global__ void classify_scatter_kernel(const int64_t *__restrict__ offp, const 
         const int64_t d = offp[u + 1] - offp[u];
         const int64_t nin = din[u];
         if (is_heavy(d, nin, light_max, light_items)) {
-            const int b = heavy_bucket(d, nin);
+            const int b = heavy_key(d, nin, hub_min);
             heavy[s_off[b] + atomicAdd(bucket_fill + b, 1ull)] = (uint32_t)u;
         }
     }
@@ -1174,11 +1186,14 @@ __global__ void eo_list_reset_kernel(const TriRec *__restrict__ L, int64_t len, 
 // -------------------------------------------------------------------- host
 struct Plan {
     uint32_t *heavy = nullptr;
-    unsigned long long *buckets = nullptr;  // counts [kBuckets], fills [kBuckets]
+    unsigned long long *buckets = nullptr;  // counts [kKeys], fills [kKeys]
     uint32_t *din = nullptr;                // in-arcs streamed from the head's side, per vertex
     uint2 *inl = nullptr;                   // their (tail, arc), at offs(v) - offp(v) per vertex
     const int64_t *offs = nullptr;          // symmetric offsets of the graph
     int64_t n_heavy = 0, max_deg = 0;
+    int64_t n_hubs = 0;  // the first n_hubs heavy vertices (d+ > kHeavyCap) go to the hub launch
+    int hub_cap = 0;     // hub table entries
+    size_t hub_smem = 0;
     int light_max = kLightMax;
     int light_items = kLightItems;
     int log_slots = 3;
@@ -1229,11 +1244,11 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
         return fail(SG_ERR_UNSUPPORTED, "triangle kernels reserve vertex ids 2^32 - 2 and 2^32 - 1");
     pl->offs = offs;
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
-    if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kBuckets);
+    if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kKeys);
     if (st == SG_OK) st = dalloc(c, (void **)&pl->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&pl->inl, sizeof(uint2) * (size_t)std::max<int64_t>(inl_cap, 1));
     if (st != SG_OK) return st;
-    SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kBuckets, c->stream));
+    SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kKeys, c->stream));
     SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
     st = launch_inarcs(c, o, offs, pl->din, pl->inl);
     if (st != SG_OK) return st;
@@ -1241,24 +1256,31 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
     if (o.n > 0) {
         SG_LAUNCH(c, "tri_classify");
         classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, offs, pl->din, o.n, pl->light_max,
-                                                                       pl->light_items, pl->buckets, c->d_ctr);
+                                                                       pl->light_items, (int64_t)kHeavyCap,
+                                                                       pl->buckets, c->d_ctr);
     }
     SG_CUDA(cudaGetLastError());
-    SG_CUDA(cudaMemcpyAsync(c->h_pinned, pl->buckets, sizeof(unsigned long long) * kBuckets, cudaMemcpyDeviceToHost,
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, pl->buckets, sizeof(unsigned long long) * kKeys, cudaMemcpyDeviceToHost,
                             c->stream));
-    SG_CUDA(cudaMemcpyAsync(c->h_pinned + kBuckets, c->d_ctr + kCtrMaxDeg, sizeof(unsigned long long),
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned + kKeys, c->d_ctr + kCtrMaxDeg, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(cudaStreamSynchronize(c->stream));
-    unsigned long long cnt[kBuckets + 1];
+    unsigned long long cnt[kKeys + 1];
     std::memcpy(cnt, c->h_pinned, sizeof(cnt));
     pl->n_heavy = 0;
-    for (int b = 0; b < kBuckets; ++b) pl->n_heavy += (int64_t)cnt[b];
-    pl->max_deg = (int64_t)cnt[kBuckets];
+    pl->n_hubs = 0;
+    for (int b = 0; b < kKeys; ++b) pl->n_heavy += (int64_t)cnt[b];
+    for (int b = kBuckets; b < kKeys; ++b) pl->n_hubs += (int64_t)cnt[b];
+    pl->max_deg = (int64_t)cnt[kKeys];
+    // a hub launch with fewer hubs than SMs would leave most SMs idle: the
+    // main launch then takes them first (they lead the list), in chunks
+    if (pl->n_hubs < c->num_sms) pl->n_hubs = 0;
     if (pl->n_heavy > 0) {
         SG_LAUNCH(c, "tri_classify");
         classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, pl->din, o.n, pl->light_max,
-                                                                         pl->light_items, pl->buckets,
-                                                                         pl->buckets + kBuckets, pl->heavy, nullptr);
+                                                                         pl->light_items, (int64_t)kHeavyCap,
+                                                                         pl->buckets, pl->buckets + kKeys,
+                                                                         pl->heavy, nullptr);
     }
     SG_CUDA(cudaGetLastError());
     // shared memory: hit queues + the larger of the heavy table (4 slots per
@@ -1269,23 +1291,29 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
     while (cap < pl->max_deg && cap < kHeavyCap) cap *= 2;
     pl->heavy_cap = cap;
     pl->log_slots = ceil_log2_host(4 * cap);
-    const size_t heavy_bytes = (size_t)cap * (4 * sizeof(uint32_t) + 2 * sizeof(uint32_t) + sizeof(unsigned short));
-    pl->smem = queue_bytes + std::max(light_bytes, heavy_bytes);
+    const size_t entry_bytes = 4 * sizeof(uint32_t) + 2 * sizeof(uint32_t) + sizeof(unsigned short);
+    pl->smem = queue_bytes + std::max(light_bytes, (size_t)cap * entry_bytes);
+    if (pl->n_hubs > 0) {
+        int hc = kHeavyCap;
+        while (hc < pl->max_deg && hc < kHubCap) hc *= 2;
+        pl->hub_cap = hc;
+        pl->hub_smem = sizeof(HitQueue) * kHubTW + (size_t)hc * entry_bytes;
+    }
     return SG_OK;
 }
 
 template <Mode M>
 static sg_status launch_enum_raw(Ctx *c, TriArgs a, size_t smem, int grid_per_sm) {
     SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
-    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M, kTW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M>, kTW * 32, smem));
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M, kTW>, kTW * 32, smem));
     per_sm = std::max(per_sm, 1);
     if (grid_per_sm > 0) per_sm = std::min(per_sm, grid_per_sm);
     const int64_t grid = (int64_t)c->num_sms * per_sm;
     {
         SG_LAUNCH(c, "tri_enum");
-        tri_enum_kernel<M><<<(unsigned)grid, kTW * 32, smem, c->stream>>>(a);
+        tri_enum_kernel<M, kTW><<<(unsigned)grid, kTW * 32, smem, c->stream>>>(a);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -1305,14 +1333,34 @@ static sg_status launch_enum(Ctx *c, const TriArgs &base, const Plan &pl) {
     a.din = pl.din;
     a.inl = pl.inl;
     a.work = c->d_ctr + kCtrAux;
+    if (pl.n_hubs > 0) {
+        // the hubs first, one 32-warp CTA per SM sharing a large table
+        TriArgs h = a;
+        h.n_heavy = pl.n_hubs;
+        h.heavy_cap = pl.hub_cap;
+        SG_CUDA(cudaMemsetAsync(h.work, 0, 2 * sizeof(unsigned long long), c->stream));
+        SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M, kHubTW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pl.hub_smem));
+        int hub_per_sm = 0;
+        SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub_per_sm, tri_enum_kernel<M, kHubTW>, kHubTW * 32,
+                                                              pl.hub_smem));
+        const int64_t hgrid = (int64_t)c->num_sms * std::max(hub_per_sm, 1);
+        {
+            SG_LAUNCH(c, "tri_hubs");
+            tri_enum_kernel<M, kHubTW><<<(unsigned)hgrid, kHubTW * 32, pl.hub_smem, c->stream>>>(h);
+        }
+        SG_CUDA(cudaGetLastError());
+        a.heavy = pl.heavy + pl.n_hubs;
+        a.n_heavy = pl.n_heavy - pl.n_hubs;
+    }
     SG_CUDA(cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned long long), c->stream));
-    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    SG_CUDA(cudaFuncSetAttribute(tri_enum_kernel<M, kTW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
     int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M>, kTW * 32, pl.smem));
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_enum_kernel<M, kTW>, kTW * 32, pl.smem));
     const int64_t grid = (int64_t)c->num_sms * std::max(per_sm, 1);
     {
         SG_LAUNCH(c, "tri_enum");
-        tri_enum_kernel<M><<<(unsigned)grid, kTW * 32, pl.smem, c->stream>>>(a);
+        tri_enum_kernel<M, kTW><<<(unsigned)grid, kTW * 32, pl.smem, c->stream>>>(a);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -1367,7 +1415,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     bool listed = false;
     bool try_list = o.m <= (int64_t)0xFFFFFFFFll && c->eo_list_cap >= 0;
     // warps of one enumeration launch, at most: each may leave a chunk per bucket part filled
-    const int64_t emit_warps = (int64_t)c->num_sms * 8 * kTW;
+    const int64_t emit_warps = (int64_t)c->num_sms * (8 * kTW + kHubTW);
     sg_status st = dalloc(c, (void **)&considered, cwords * sizeof(uint32_t));
     if (st == SG_OK) st = dalloc(c, (void **)&resv, m * sizeof(unsigned long long));
     if (st == SG_OK) st = dalloc(c, (void **)&lctr, lctr_bytes);
@@ -1674,7 +1722,7 @@ sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *
     if (st != SG_OK) return st;
     if (!bt->heavy) st = dalloc(c, (void **)&bt->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK && !bt->buckets)
-        st = dalloc(c, (void **)&bt->buckets, sizeof(unsigned long long) * (2 * kBuckets + 1));
+        st = dalloc(c, (void **)&bt->buckets, sizeof(unsigned long long) * (2 * kKeys + 1));
     if (st == SG_OK && !bt->din) st = dalloc(c, (void **)&bt->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     // Per call only the graphs with a triangle kernel are oriented, so E+ can
     // hold fewer than nnz/2 arcs and the in-list room off(v) - off+(v) then
@@ -1700,28 +1748,29 @@ sg_status batch_tr_mark(Ctx *c, const Graph *u, const Oriented &o, const BatchDe
                         uint8_t *del) {
     if (o.n == 0) return SG_OK;
     const int light_items = 4 * bt.light_max;
-    SG_CUDA(cudaMemsetAsync(bt.buckets, 0, sizeof(unsigned long long) * (2 * kBuckets + 1), c->stream));
+    SG_CUDA(cudaMemsetAsync(bt.buckets, 0, sizeof(unsigned long long) * (2 * kKeys + 1), c->stream));
     sg_status st = launch_inarcs(c, o, u->off, bt.din, bt.inl);
     if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     {
         SG_LAUNCH(c, "tri_classify");
+        // no hub launch in a batch: its graphs are small, and a long N+(u) is chunked
         classify_count_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, u->off, bt.din, o.n, bt.light_max,
-                                                                       light_items, bt.buckets, c->d_ctr);
+                                                                       light_items, INT64_MAX, bt.buckets, c->d_ctr);
     }
     {
         SG_LAUNCH(c, "tri_classify");
         classify_scatter_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(o.off, bt.din, o.n, bt.light_max,
-                                                                         light_items, bt.buckets,
-                                                                         bt.buckets + kBuckets, bt.heavy,
-                                                                         bt.buckets + 2 * kBuckets);
+                                                                         light_items, INT64_MAX, bt.buckets,
+                                                                         bt.buckets + kKeys, bt.heavy,
+                                                                         bt.buckets + 2 * kKeys);
     }
     SG_CUDA(cudaGetLastError());
     TriArgs a = base_args(c, o);
     a.del = del;
     a.heavy = bt.heavy;
     a.n_heavy = 0;
-    a.n_heavy_dev = bt.buckets + 2 * kBuckets;
+    a.n_heavy_dev = bt.buckets + 2 * kKeys;
     a.heavy_log_slots = bt.log_slots;
     a.heavy_cap = bt.max_deg;
     a.light_max = bt.light_max;

@@ -89,6 +89,15 @@ def test_batch_matches_solo_weighted_maxw(sg, ctx):
     B.free()
 
 
+def test_batch_long_out_lists_are_chunked(sg, ctx):
+    # a batch has no hub launch: the biclique's out-degree-1100 vertices are
+    # taken by the main launch's tables in chunks
+    graphs = [gg.rmat(8, 8, seed=3), gg.biclique_matched(1100), gg.complete(30)]
+    kernels = ["tr_random", "tr_random", "tr_p2"]
+    B, _ = _check_batch(sg, ctx, graphs, kernels, [0.5, 0.7, 0.4], [1, 2, 3])
+    B.free()
+
+
 def test_batch_rejects_edge_once(sg, ctx):
     G = [sg.Graph.from_csr(ctx, gg.complete(5))]
     B = sg.Batch(ctx, G)

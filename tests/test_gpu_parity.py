@@ -289,6 +289,51 @@ def test_chunked_heavy_tables(sg, ctx, kern, p):
     G.free()
 
 
+@pytest.mark.parametrize("kern,p", [("tr_random", 0.3), ("tr_eo", 0.5), ("tr_eo", 1.0), ("tr_p2", 0.4),
+                                    ("tr_mincount", 0.6), ("tr_eo_mincount", 1.0), ("tr_maxw", 1.0)])
+def test_hub_tables(sg, ctx, kern, p):
+    # every right vertex of the matched biclique has out-degree 1100: longer
+    # than the main launch's tables, so the hub launch handles them (1100
+    # hubs, more than the SMs)
+    g = gg.attach_weights(gg.biclique_matched(1100), seed=3)
+    _same(sg, ctx, g, kern, p, 5)
+    G = sg.Graph.from_csr(ctx, g)
+    assert sg.triangle_count(G) == 550 * 1100
+    w = sg.tr_work(G)
+    assert w["max_out_degree"] == 1100 and w["triangles"] == 550 * 1100
+    G.free()
+
+
+def test_hub_tables_chunked(sg, ctx):
+    # out-degree 4100 exceeds even the hub table, which then takes N+(u) in
+    # chunks (the oracle needs about a minute for this graph)
+    g = gg.biclique_matched(4100)
+    _same(sg, ctx, g, "tr_random", 0.5, 8)
+    G = sg.Graph.from_csr(ctx, g)
+    assert sg.triangle_count(G) == 2050 * 4100
+    G.free()
+
+
+@pytest.mark.parametrize("kern", ["tr_random", "tr_eo"])
+def test_few_hubs_chunked_in_main_launch(sg, ctx, kern):
+    # 40 hubs of out-degree 1100 are too few for a hub launch: the main
+    # launch takes their N+(u) in two chunks.  Each of the 1100 vertices below
+    # the hubs gets 1100 leaves and a matching partner, so it ranks above them.
+    k, h = 1100, 40
+    mid = torch.arange(k, dtype=torch.int64)
+    hubs = k + torch.arange(h, dtype=torch.int64)
+    leaves = k + h + torch.arange(k * k, dtype=torch.int64)
+    ml = torch.arange(0, k - 1, 2, dtype=torch.int64)
+    src = torch.cat([mid.repeat_interleave(h), mid.repeat_interleave(k), ml])
+    dst = torch.cat([hubs.repeat(k), leaves, ml + 1])
+    g = gg.csr_from_edges(k + h + k * k, src, dst)
+    G = sg.Graph.from_csr(ctx, g)
+    w = sg.tr_work(G)
+    assert w["max_out_degree"] == k and w["triangles"] == (k // 2) * h
+    G.free()
+    _same(sg, ctx, g, kern, 0.6, 2)
+
+
 def test_edge_triangle_counts_through_mincount(sg, ctx):
     # at p = 1 every triangle is selected, so min-count TR deletes exactly the
     # per-triangle minima of the counts -- a wrong count anywhere shows up
