@@ -34,6 +34,7 @@ WORKLOADS = {
     "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat19": dict(scale=19, ef=16, desc="R-MAT scale 19, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
+    "rmat23": dict(scale=23, ef=16, desc="R-MAT scale 23, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat24": dict(scale=24, ef=16, desc="R-MAT scale 24, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
     "rmat14": dict(scale=14, ef=16, desc="R-MAT scale 14, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
 }
@@ -202,6 +203,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(local)
     ctx = sg.Context(local, stream=stream)
     G = sg.Graph.from_csr(ctx, g, copy=True)
+    torch.cuda.empty_cache()  # hand the generator's scratch back before the library sizes its lists
     ctx.set_eo_list_capacity(args.eo_list_cap)
     n, m = G.n, G.m
     work = sg.tr_work(G)

@@ -54,7 +54,7 @@ struct Ctx {
 };
 
 enum CtrIdx { kCtrProbes = 0, kCtrTriangles = 1, kCtrLive = 2, kCtrHeavy = 3, kCtrMaxDeg = 4, kCtrAux = 5,
-              kCtrInArcs = 7, kCtrCount = 8 };  // kCtrAux holds two words
+              kCtrInArcs = 7, kCtrWork = 8, kCtrCount = 9 };  // kCtrAux holds two words
 
 struct Graph {
     Ctx *ctx = nullptr;

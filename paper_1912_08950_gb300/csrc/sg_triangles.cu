@@ -869,13 +869,14 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
                                      unsigned long long *ctr, int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    unsigned long long cnt = 0;
+    unsigned long long cnt = 0, work = 0;  // work: W, the probes of one enumeration pass
     for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n; u += nw) {
         const int64_t ou = __ldg(offp + u), du = __ldg(offp + u + 1) - ou;
         for (int64_t i = lane; i < du; i += 32) {
             const uint32_t v = __ldg(colp + ou + i);
             const int64_t ov = __ldg(offp + v);
             const int64_t dv = __ldg(offp + v + 1) - ov;
+            work += (unsigned long long)(du < dv ? du : dv);
             if (du < dv) {
                 const int64_t sv = __ldg(offs + v);
                 const int64_t room = (__ldg(offs + v + 1) - sv) - dv;
@@ -890,7 +891,9 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
         }
     }
     cnt = warp_sum(cnt);
+    work = warp_sum(work);
     if (lane == 0 && cnt) atomicAdd(ctr + kCtrInArcs, cnt);
+    if (lane == 0 && work) atomicAdd(ctr + kCtrWork, work);
 }
 
 // Also clamps every in-list length to its room (only an asymmetric input,
@@ -1191,6 +1194,7 @@ struct Plan {
     uint2 *inl = nullptr;                   // their (tail, arc), at offs(v) - offp(v) per vertex
     const int64_t *offs = nullptr;          // symmetric offsets of the graph
     int64_t n_heavy = 0, max_deg = 0;
+    int64_t work = 0;    // W = sum over arcs of min(d+(u), d+(v)): the probes of one pass
     int64_t n_hubs = 0;  // the first n_hubs heavy vertices (d+ > kHeavyCap) go to the hub launch
     int hub_cap = 0;     // hub table entries
     size_t hub_smem = 0;
@@ -1250,6 +1254,7 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
     if (st != SG_OK) return st;
     SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kKeys, c->stream));
     SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
+    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrWork, 0, sizeof(unsigned long long), c->stream));
     st = launch_inarcs(c, o, offs, pl->din, pl->inl);
     if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
@@ -1264,9 +1269,12 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
                             c->stream));
     SG_CUDA(cudaMemcpyAsync(c->h_pinned + kKeys, c->d_ctr + kCtrMaxDeg, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned + kKeys + 1, c->d_ctr + kCtrWork, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(cudaStreamSynchronize(c->stream));
-    unsigned long long cnt[kKeys + 1];
+    unsigned long long cnt[kKeys + 2];
     std::memcpy(cnt, c->h_pinned, sizeof(cnt));
+    pl->work = (int64_t)cnt[kKeys + 1];
     pl->n_heavy = 0;
     pl->n_hubs = 0;
     for (int b = 0; b < kKeys; ++b) pl->n_heavy += (int64_t)cnt[b];
@@ -1430,9 +1438,20 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     if (st == SG_OK && cudaMemsetAsync(resv, 0xFF, m * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "memset");
     auto list_blocks = [&](int64_t len) { return std::min<int64_t>((len + 255) / 256, (int64_t)c->num_sms * 8); };
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetMemPool(&pool, c->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        pool = nullptr;
+    }
     auto list_capacity = [&]() -> int64_t {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+        // memory the stream-ordered pool keeps from earlier calls but does not use is free too
+        uint64_t reserved = 0, used = 0;  // the pool attributes are 64-bit counts
+        if (pool && cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            fr += (size_t)(reserved - used);
+        (void)cudaGetLastError();
         int64_t cap = (int64_t)(fr / 4 / sizeof(uint4));
         if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
         return cap;
@@ -1460,35 +1479,63 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                     ubase[b] = run;
                     run += cb;
                 };
-                if (!have_dem) {
-                    // no counts yet: the shares of the draws r2, 1,1,2,4,8,16 of 32 (earlier buckets fold into rb)
-                    double w[kEoBuckets], wsum = 0.0;
-                    for (int b = 0; b < kEoBuckets; ++b) w[b] = b <= 1 ? 1.0 : (double)(1 << (b - 1));
-                    for (int b = 0; b < rb; ++b) { w[rb] += w[b]; w[b] = 0.0; }
-                    for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
+                // the shares of the draws r2 over the buckets: 1,1,2,4,8,16 of 32
+                // (earlier buckets fold into rb)
+                double w[kEoBuckets], wsum = 0.0;
+                for (int b = 0; b < kEoBuckets; ++b) w[b] = b <= 1 ? 1.0 : (double)(1 << (b - 1));
+                for (int b = 0; b < rb; ++b) { w[rb] += w[b]; w[b] = 0.0; }
+                for (int b = 0; b < kEoBuckets; ++b) wsum += w[b];
+                // no counts yet: a triangle is found by one probe, so at most
+                // about p W are selected (W probes per pass)
+                const double sel_max = (double)a.tp / 4294967296.0 * (double)pl.work;
+                if (!have_dem && sel_max <= (double)cap) {
+                    // everything fits: split the room by the shares
                     for (int b = rb; b < kEoBuckets; ++b) {
                         const int64_t cb = (int64_t)((double)cap * w[b] / wsum);
                         if (cb < 4 * eo_chunk(b)) { hi = b; break; }
                         give(b, cb);
                     }
                 } else {
-                    // the last pass's counts bound each bucket; add room for sealed chunk tails
+                    // Each bucket wants its bound: the last pass's count (live
+                    // triangles only die) or, before the first pass, a quarter of p W
+                    // (R-MAT graphs find a triangle in 12-18% of their probes), plus
+                    // room for sealed chunk tails.  The bounds are loose -- deciding a
+                    // window kills most of the triangles above it -- so when they do
+                    // not all fit, this round's bucket gets its bound (up to half the
+                    // room) and the rest is split in proportion to the bounds above:
+                    // a bucket that overflows only narrows the window.
                     unsigned long long fold = 0;
                     for (int b = 0; b <= rb; ++b) fold += dem[b];
+                    int64_t want[kEoBuckets] = {};
+                    double above = 0.0;
                     for (int b = rb; b < kEoBuckets; ++b) {
-                        const double d = (double)(b == rb ? fold : dem[b]);
-                        const int64_t want = (int64_t)(d * (1.0 + 16.0 / eo_chunk(b))) + emit_warps * eo_chunk(b);
-                        const int64_t cb = std::min<int64_t>(want, cap - run);
+                        const double d = have_dem ? (double)(b == rb ? fold : dem[b]) : 0.25 * sel_max * w[b] / wsum;
+                        want[b] = (int64_t)(d * (1.0 + 16.0 / eo_chunk(b))) + emit_warps * eo_chunk(b);
+                        if (b > rb) above += (double)want[b];
+                    }
+                    const int64_t first = std::min<int64_t>(want[rb], cap / 2);
+                    const double rest = (double)(cap - first);
+                    const double scale = above <= rest ? 1.0 : rest / above;
+                    for (int b = rb; b < kEoBuckets; ++b) {
+                        const int64_t cb = b == rb ? first : (int64_t)((double)want[b] * scale);
                         if (cb < 4 * eo_chunk(b)) { hi = b; break; }
                         give(b, cb);
-                        if (cb < want) { hi = b + 1; break; }  // may still fit: the bound is loose
                     }
                 }
                 if (hi <= rb) hi = 0;  // nothing to list: the pass only bids and counts
-                if (hi > 0 && dalloc(c, (void **)&L, (size_t)std::max<int64_t>(run, 1) * sizeof(uint4)) != SG_OK) {
-                    L = nullptr;
-                    set_error("");
-                    try_list = false;
+                if (hi > 0) {
+                    const size_t lbytes = (size_t)std::max<int64_t>(run, 1) * sizeof(uint4);
+                    if (dalloc(c, (void **)&L, lbytes) != SG_OK && pool) {
+                        // the pool's idle memory may be too fragmented: hand it back and retry
+                        (void)cudaStreamSynchronize(c->stream);
+                        (void)cudaMemPoolTrimTo(pool, 0);
+                        (void)cudaGetLastError();
+                        (void)dalloc(c, (void **)&L, lbytes);
+                    }
+                    if (L == nullptr) {
+                        set_error("");
+                        try_list = false;
+                    }
                 }
             }
             if (try_list) {
@@ -1594,6 +1641,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             if (top >= kEoBuckets) break;     // no triangle left anywhere
             // every triangle of the list's window is decided: list the live ones
             // above it, starting the schedule at its first bucket
+            for (int b = 0; b < top; ++b) dem[b] = 0;
             dfree(c, L);
             L = nullptr;
             listed = false;
