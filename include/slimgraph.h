@@ -155,6 +155,11 @@ sg_status sg_ctx_reset_profile(sg_ctx *ctx);
  * enumerates the triangles again).  The result is the same in every setting;
  * only time and memory change. */
 sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records);
+/* The Edge-Once lists live in device workspaces that the context keeps and
+ * reuses across calls (grown when a call needs more).  This frees them, in
+ * stream order; the next Edge-Once call allocates them again.
+ * Errors: SG_ERR_INVALID_ARG (ctx == NULL). */
+sg_status sg_ctx_release_workspace(sg_ctx *ctx);
 
 /* ----------------------------------------------------------------- graphs */
 

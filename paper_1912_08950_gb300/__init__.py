@@ -72,6 +72,7 @@ _SIGS = {
     "sg_ctx_kernel_time": [_vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "sg_ctx_reset_profile": [_vp],
     "sg_ctx_set_eo_list_capacity": [_vp, _i64],
+    "sg_ctx_release_workspace": [_vp],
     "sg_graph_from_device": [_vp, C.POINTER(CsrView), _int, _int, _PP],
     "sg_graph_from_host": [_vp, _i64, _i64, _vp, _vp, _vp, _PP],
     "sg_graph_view": [_vp, C.POINTER(CsrView)],
@@ -183,6 +184,10 @@ class Context:
     def set_eo_list_capacity(self, records: int):
         """0: automatic, -1: no triangle list, > 0: at most that many triangles."""
         _check(_lib.sg_ctx_set_eo_list_capacity(self.handle, int(records)))
+
+    def release_workspace(self):
+        """Free the edge-once list workspaces the context keeps between calls."""
+        _check(_lib.sg_ctx_release_workspace(self.handle))
 
 
 class Graph:

@@ -54,6 +54,21 @@ void dfree(Ctx *c, void *p) {
     if (p) (void)cudaFreeAsync(p, c->stream);
 }
 
+sg_status ws_get(Ctx *c, int slot, size_t bytes, void **p) {
+    if (c->ws[slot] && c->ws_bytes[slot] >= bytes) {
+        *p = c->ws[slot];
+        return SG_OK;
+    }
+    dfree(c, c->ws[slot]);
+    c->ws[slot] = nullptr;
+    c->ws_bytes[slot] = 0;
+    sg_status st = dalloc(c, p, bytes);
+    if (st != SG_OK) return st;
+    c->ws[slot] = *p;
+    c->ws_bytes[slot] = bytes;
+    return SG_OK;
+}
+
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->event_pool.empty()) {
         cudaEvent_t e = c->event_pool.back();
@@ -192,6 +207,7 @@ void sg_ctx_destroy(sg_ctx *ctx) {
         g_live_ctx.erase(c);
     }
     (void)cudaSetDevice(c->device);
+    for (int i = 0; i < 3; ++i) dfree(c, c->ws[i]);
     if (c->stream) (void)cudaStreamSynchronize(c->stream);
     for (auto &r : c->prof) {
         (void)cudaEventDestroy(r.beg);
@@ -249,6 +265,19 @@ sg_status sg_ctx_set_profiling(sg_ctx *ctx, int on) {
 sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records) {
     if (!ctx || records < -1) return fail(SG_ERR_INVALID_ARG, "bad argument");
     C_(ctx)->eo_list_cap = records;
+    return SG_OK;
+}
+
+sg_status sg_ctx_release_workspace(sg_ctx *ctx) {
+    if (!ctx) return fail(SG_ERR_INVALID_ARG, "ctx is NULL");
+    Ctx *c = C_(ctx);
+    sg_status st = set_device(c);
+    if (st != SG_OK) return st;
+    for (int i = 0; i < 3; ++i) {
+        dfree(c, c->ws[i]);
+        c->ws[i] = nullptr;
+        c->ws_bytes[i] = 0;
+    }
     return SG_OK;
 }
 

@@ -49,6 +49,10 @@ struct Ctx {
     uint64_t eo_list_passes = 0;           // ... that listed triangles
     int64_t eo_list_cap = 0;               // 0 auto, -1 off, > 0 records
     bool profiling = false;
+    // grow-only device workspaces kept across calls (edge-once list and active
+    // lists), so that repeated calls do not churn the stream-ordered pool
+    void *ws[3] = {nullptr, nullptr, nullptr};
+    size_t ws_bytes[3] = {0, 0, 0};
     std::vector<ProfRec> prof;             // events of launches since reset
     std::vector<cudaEvent_t> event_pool;   // recycled events
 };
@@ -82,6 +86,8 @@ bool ctx_alive(const Ctx *c);
 
 // stream-ordered device allocation on the context stream
 sg_status dalloc(Ctx *c, void **p, size_t bytes);
+// workspace `slot` of at least `bytes` bytes (contents undefined; owned by the context)
+sg_status ws_get(Ctx *c, int slot, size_t bytes, void **p);
 void dfree(Ctx *c, void *p);
 
 // launch bookkeeping: brackets a launch with events when profiling

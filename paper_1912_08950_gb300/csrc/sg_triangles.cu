@@ -49,6 +49,8 @@ constexpr int kHubTW = 32;        // warps per CTA of the hub launch (one CTA pe
 constexpr int kHubCap = 4096;     // largest hub table (entries; 104 KB of shared memory)
 constexpr int kQ = 128;           // per-warp hit ring (<= 31 left over + 2 slabs of hits fit)
 constexpr int kEoBuckets = 6;     // edge-once list buckets (rounds 0..5 of the prefix schedule)
+// context workspaces of the edge-once rounds: the list and the two active lists
+constexpr int kWsList = 0, kWsActive0 = 1, kWsActive1 = 2;
 
 // Count: totals only.  EdgeCount / VertexCount: add every triangle to the
 // counters of its three edges / vertices.  Union*: the union-semantics TR kernels.  EoReserve: one
@@ -1410,8 +1412,9 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
     unsigned long long *resv = nullptr, *lctr = nullptr;
     const size_t lctr_bytes = (2 * kEoBuckets + 1) * sizeof(unsigned long long) + sizeof(int);
     int *lovf = nullptr;
-    uint4 *L = nullptr;    // bucketed list written by the enumeration
-    TriRec *A = nullptr;   // active list: this round's bidders
+    uint4 *L = nullptr;    // bucketed list written by the enumeration (workspace kWsList)
+    TriRec *A = nullptr;   // active list: this round's bidders (workspace a_slot)
+    int a_slot = kWsActive1;
     int64_t lenA = 0;
     int64_t ubase[kEoBuckets] = {}, used[kEoBuckets] = {};
     // live selected triangles per bucket at the last listing pass: a bound on them now
@@ -1452,6 +1455,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
             fr += (size_t)(reserved - used);
         (void)cudaGetLastError();
+        for (int i = 0; i < 3; ++i) fr += c->ws_bytes[i];  // the context's workspaces are reused
         int64_t cap = (int64_t)(fr / 4 / sizeof(uint4));
         if (c->eo_list_cap > 0) cap = std::min<int64_t>(cap, c->eo_list_cap);
         return cap;
@@ -1525,12 +1529,12 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                 if (hi <= rb) hi = 0;  // nothing to list: the pass only bids and counts
                 if (hi > 0) {
                     const size_t lbytes = (size_t)std::max<int64_t>(run, 1) * sizeof(uint4);
-                    if (dalloc(c, (void **)&L, lbytes) != SG_OK && pool) {
+                    if (ws_get(c, kWsList, lbytes, (void **)&L) != SG_OK && pool) {
                         // the pool's idle memory may be too fragmented: hand it back and retry
                         (void)cudaStreamSynchronize(c->stream);
                         (void)cudaMemPoolTrimTo(pool, 0);
                         (void)cudaGetLastError();
-                        (void)dalloc(c, (void **)&L, lbytes);
+                        if (ws_get(c, kWsList, lbytes, (void **)&L) != SG_OK) L = nullptr;
                     }
                     if (L == nullptr) {
                         set_error("");
@@ -1579,7 +1583,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
                     ++c->eo_list_passes;
                     next_bucket = rb;
                 } else {
-                    dfree(c, L);  // this round's bids are in: finish it from the edges' side
+                    // this round's bids are in: finish it from the edges' side
                     L = nullptr;
                     bids_done = true;
                 }
@@ -1613,7 +1617,8 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         // ---- list round: last round's survivors plus this round's bucket
         const int64_t fresh = next_bucket < top ? used[next_bucket] : 0;
         TriRec *B = nullptr;
-        st = dalloc(c, (void **)&B, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec));
+        const int bslot = a_slot == kWsActive0 ? kWsActive1 : kWsActive0;
+        st = ws_get(c, bslot, (size_t)std::max<int64_t>(lenA + fresh, 1) * sizeof(TriRec), (void **)&B);
         if (st != SG_OK) break;
         unsigned long long *out_len = lctr + 2 * kEoBuckets;
         SG_CUDA(cudaMemsetAsync(out_len, 0, sizeof(unsigned long long), c->stream));
@@ -1633,8 +1638,8 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         SG_CUDA(cudaMemcpyAsync(c->h_pinned, out_len, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
         SG_CUDA(cudaStreamSynchronize(c->stream));
         std::memcpy(&live, c->h_pinned, sizeof(live));
-        dfree(c, A);
         A = B;
+        a_slot = bslot;
         lenA = (int64_t)live;
         if (live == 0) {
             if (next_bucket < top) continue;  // nothing bid this round
@@ -1642,7 +1647,6 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
             // every triangle of the list's window is decided: list the live ones
             // above it, starting the schedule at its first bucket
             for (int b = 0; b < top; ++b) dem[b] = 0;
-            dfree(c, L);
             L = nullptr;
             listed = false;
             sched = top - 1;
@@ -1685,8 +1689,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
         }
         SG_CUDA(cudaGetLastError());
     }
-    dfree(c, A);
-    dfree(c, L);
+
     dfree(c, lctr);
     dfree(c, considered);
     dfree(c, resv);

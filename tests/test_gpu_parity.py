@@ -160,6 +160,18 @@ def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
         assert st["eo_passes"] == st["eo_rounds"] + 1
 
 
+def test_eo_workspace_reuse_and_release(sg, ctx):
+    # repeated calls reuse the context's list workspaces; releasing them in
+    # between changes nothing but the allocations
+    g = gg.rmat(12, 16, seed=4)
+    first = _same(sg, ctx, g, "tr_eo", 0.5, 3)
+    again = _same(sg, ctx, g, "tr_eo", 0.5, 3)
+    ctx.release_workspace()
+    after = _same(sg, ctx, g, "tr_eo", 0.5, 3)
+    for x, y in ((first, again), (first, after)):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
 def test_eo_list_windows(sg, ctx):
     # caps between the first bucket and the whole list: some pass lists a
     # window of the schedule and a later pass lists the triangles above it
