@@ -49,8 +49,11 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than sca
 # figure no longer describes the kernel and the JSON line reports null.
 MEASURED_TRAFFIC = {
     # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
-    # profiles/tri_enum_rmat22_tr_eo.md: 37.70 GB read + 18.76 GB written
-    ("rmat22", "tr_eo"): (56462799000, "9edf0caad05d9cbcc27beb812a30fb639f2426edef1dc7e6164bb6ef8881d266"),
+    # profiles/tri_enum_rmat22_tr_eo.md: 38.01 GB read + 18.83 GB written
+    ("rmat22", "tr_eo"): (56833533000, "ab3ab9f85974aed780212aa4372ec8513a9f43ee5180b4c4250fb8127d3d54e4"),
+    # profiles/tri_enum_rmat26_tr_random.md: hub launch 1417.01 + 144.54 GB, main launch
+    # 514.11 + 12.09 GB (read + written) per union pass
+    ("rmat26", "tr_random"): (2087748801000, "ab3ab9f85974aed780212aa4372ec8513a9f43ee5180b4c4250fb8127d3d54e4"),
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 
