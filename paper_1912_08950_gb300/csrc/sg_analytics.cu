@@ -8,8 +8,15 @@
 // the FP32 vectors.  Connected components use concurrent union-find: roots
 // hook to the smaller root with atomicCAS, then pointer jumping flattens the
 // forest; the count of self-parented vertices is exact whatever the schedule.
+// The edges are taken in the order of Sutton et al.'s Afforest (IPDPS'18):
+// every vertex first links its first kCcSample neighbours, the most frequent
+// root among sampled vertices is taken as the giant component, and then only
+// the rows of vertices outside it link their remaining neighbours (an edge
+// leaving the giant component is seen from its other end).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "sg_internal.cuh"
 
@@ -485,25 +492,56 @@ __device__ __forceinline__ uint32_t cc_find(uint32_t *parent, uint32_t v) {
     return v;
 }
 
-// warp per row; every edge {x < y} hooks the larger root under the smaller
-__global__ void cc_hook_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ col, int64_t n,
-                               uint32_t *parent) {
+constexpr int kCcSample = 2;     // neighbours every vertex links first
+constexpr int kCcProbes = 1024;  // sampled vertices that name the giant component
+
+// join the trees of x and y: the larger root hooks under the smaller
+__device__ __forceinline__ void cc_link(uint32_t *parent, uint32_t x, uint32_t y) {
+    uint32_t rx = cc_find(parent, x), ry = cc_find(parent, y);
+    while (rx != ry) {
+        const uint32_t hi = rx > ry ? rx : ry, lo = rx > ry ? ry : rx;
+        const uint32_t old = atomicCAS(parent + hi, hi, lo);
+        if (old == hi) break;
+        rx = cc_find(parent, hi);
+        ry = cc_find(parent, lo);
+    }
+}
+
+// thread per vertex: link its first kCcSample neighbours
+__global__ void cc_sample_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ col, int64_t n,
+                                 uint32_t *parent) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = __ldg(off + x), e = __ldg(off + x + 1);
+        for (int64_t i = b; i < e && i < b + kCcSample; ++i) cc_link(parent, (uint32_t)x, __ldg(col + i));
+    }
+}
+
+__global__ void cc_compress_kernel(uint32_t *parent, int64_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        parent[v] = cc_find(parent, (uint32_t)v);
+}
+
+// roots of kCcProbes vertices spread over [0, n) by a fixed multiplicative hash
+__global__ void cc_probe_kernel(const uint32_t *parent, int64_t n, uint32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kCcProbes) {
+        const uint64_t v = ((uint64_t)((uint32_t)i * 0x9E3779B1u) * (uint64_t)n) >> 32;
+        out[i] = parent[v];
+    }
+}
+
+// warp per row outside the giant component: link the neighbours after the sampled ones
+__global__ void cc_rest_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ col, int64_t n,
+                               uint32_t *parent, uint32_t giant) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; x < n; x += nw) {
         const int64_t b = __ldg(off + x), e = __ldg(off + x + 1);
-        for (int64_t i = b + lane; i < e; i += 32) {
-            const uint32_t y = __ldg(col + i);
-            if (y <= (uint32_t)x) continue;
-            uint32_t rx = cc_find(parent, (uint32_t)x), ry = cc_find(parent, y);
-            while (rx != ry) {
-                const uint32_t hi = rx > ry ? rx : ry, lo = rx > ry ? ry : rx;
-                const uint32_t old = atomicCAS(parent + hi, hi, lo);
-                if (old == hi) break;
-                rx = cc_find(parent, hi);
-                ry = cc_find(parent, lo);
-            }
-        }
+        if (e - b <= kCcSample) continue;
+        uint32_t r = 0;
+        if (lane == 0) r = cc_find(parent, (uint32_t)x);
+        if (__shfl_sync(0xFFFFFFFFu, r, 0) == giant) continue;
+        for (int64_t i = b + kCcSample + lane; i < e; i += 32) cc_link(parent, (uint32_t)x, __ldg(col + i));
     }
 }
 
@@ -532,7 +570,8 @@ sg_status cc_count(Ctx *c, const Graph *g, int64_t *count, uint32_t *labels) {
     uint32_t *parent = nullptr;
     unsigned long long *roots = nullptr;
     sg_status st = dalloc(c, (void **)&parent, sizeof(uint32_t) * (size_t)n);
-    if (st == SG_OK) st = dalloc(c, (void **)&roots, sizeof(unsigned long long));
+    // roots: the root count, then kCcProbes sampled roots
+    if (st == SG_OK) st = dalloc(c, (void **)&roots, sizeof(unsigned long long) + sizeof(uint32_t) * kCcProbes);
     if (st != SG_OK) {
         dfree(c, parent);
         return st;
@@ -544,9 +583,38 @@ sg_status cc_count(Ctx *c, const Graph *g, int64_t *count, uint32_t *labels) {
         cc_init_kernel<<<blocks, 256, 0, c->stream>>>(parent, n);
     }
     {
-        SG_LAUNCH(c, "cc_hook");
+        SG_LAUNCH(c, "cc_sample");
+        cc_sample_kernel<<<blocks, 256, 0, c->stream>>>(g->off, g->col, n, parent);
+    }
+    {
+        SG_LAUNCH(c, "cc_compress");
+        cc_compress_kernel<<<blocks, 256, 0, c->stream>>>(parent, n);
+    }
+    {
+        SG_LAUNCH(c, "cc_probe");
+        cc_probe_kernel<<<(kCcProbes + 255) / 256, 256, 0, c->stream>>>(parent, n, reinterpret_cast<uint32_t *>(roots + 1));
+    }
+    SG_CUDA(cudaGetLastError());
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, roots + 1, sizeof(uint32_t) * kCcProbes, cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t giant = 0;
+    {
+        // the most frequent root among the probes (ties: the smaller root)
+        std::vector<uint32_t> pr(kCcProbes);
+        std::memcpy(pr.data(), c->h_pinned, sizeof(uint32_t) * kCcProbes);
+        std::sort(pr.begin(), pr.end());
+        int best = 0;
+        for (int i = 0; i < kCcProbes;) {
+            int j = i;
+            while (j < kCcProbes && pr[j] == pr[i]) ++j;
+            if (j - i > best) { best = j - i; giant = pr[i]; }
+            i = j;
+        }
+    }
+    {
+        SG_LAUNCH(c, "cc_rest");
         const int hb = (int)std::min<int64_t>((n + 7) / 8, (int64_t)c->num_sms * 8);
-        cc_hook_kernel<<<hb, 256, 0, c->stream>>>(g->off, g->col, n, parent);
+        cc_rest_kernel<<<hb, 256, 0, c->stream>>>(g->off, g->col, n, parent, giant);
     }
     {
         SG_LAUNCH(c, "cc_finish");

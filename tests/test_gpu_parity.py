@@ -254,6 +254,35 @@ def test_cc_labels(sg, ctx):
     G.free()
 
 
+@pytest.mark.parametrize("shape", ["forest", "no_giant", "giant_plus_specks"])
+def test_cc_sampled_giant(sg, ctx, shape):
+    # the giant-component guess from sampled roots decides only which rows are
+    # skipped: counts and labels must match the oracle whatever the shape
+    rng = np.random.default_rng(7)
+    if shape == "forest":  # 3000 random trees of 1-60 vertices
+        parts, base = [], 0
+        for _ in range(3000):
+            k = int(rng.integers(1, 61))
+            par = base + (rng.integers(0, np.arange(1, k), size=k - 1) if k > 1 else np.zeros(0, np.int64))
+            parts.append(np.stack([base + np.arange(1, k), par], 1) if k > 1 else np.zeros((0, 2), np.int64))
+            base += k
+        e = np.concatenate(parts)
+        g = gg.csr_from_edges(base, torch.from_numpy(e[:, 0]), torch.from_numpy(e[:, 1]))
+    elif shape == "no_giant":  # 20000 disjoint edges and 5000 isolated vertices
+        a_ = torch.arange(0, 40000, 2)
+        g = gg.csr_from_edges(45000, a_, a_ + 1)
+    else:  # a giant R-MAT core, small cliques and isolated vertices
+        core = gg.rmat(14, 8, seed=3)
+        g = gg.disjoint_union(core, *[gg.complete(int(k)) for k in rng.integers(1, 6, size=400)],
+                              gg.from_edge_list(3000, []))
+    G = sg.Graph.from_csr(ctx, g)
+    cnt, lab = sg.cc_count(G, labels=True)
+    n_ref, lab_ref = oracle.cc_count(g, return_labels=True)
+    assert cnt == n_ref
+    assert np.array_equal(lab.cpu().numpy().astype(np.int64), lab_ref)
+    G.free()
+
+
 # --------------------------------------------------------- argument checks
 def test_errors(sg, ctx):
     g = gg.rmat(8, 8, seed=1)
