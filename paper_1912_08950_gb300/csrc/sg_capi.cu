@@ -62,10 +62,17 @@ sg_status ws_get(Ctx *c, int slot, size_t bytes, void **p) {
     dfree(c, c->ws[slot]);
     c->ws[slot] = nullptr;
     c->ws_bytes[slot] = 0;
-    sg_status st = dalloc(c, p, bytes);
-    if (st != SG_OK) return st;
+    // a quarter more than asked: list fills vary a little from call to call
+    // (the order in which warps claim chunks), and each regrowth maps new memory
+    size_t want = bytes + bytes / 4;
+    if (dalloc(c, p, want) != SG_OK) {
+        want = bytes;
+        set_error("");
+        sg_status st = dalloc(c, p, want);
+        if (st != SG_OK) return st;
+    }
     c->ws[slot] = *p;
-    c->ws_bytes[slot] = bytes;
+    c->ws_bytes[slot] = want;
     return SG_OK;
 }
 
