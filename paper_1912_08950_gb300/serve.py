@@ -41,13 +41,24 @@ class Job:
 
     def device_bytes(self) -> int:
         """Peak device memory the job needs: input and output CSR, the
-        orientation, per-arc flags and reservations, and the triangle list
-        budget of the edge-once kernels (kept small by the server)."""
+        orientation, per-arc flags and reservations and, for the edge-once
+        kernels, the triangle list (16 B per listed triangle) and its two
+        active lists (32 B each), with the workspaces' quarter of headroom."""
         base = 8 * (self.n + 1) + 4 * self.nnz
         if self.w is not None:
             base += 4 * self.nnz
         per_arc = 4 + 1 + 1 + 8 + 4  # E+ column, del, considered, reservation, output
-        return 3 * base + per_arc * self.nnz + 64 * (self.n + 1) + (64 << 20)
+        total = 3 * base + per_arc * self.nnz + 64 * (self.n + 1) + (64 << 20)
+        if self.kernel.startswith("tr_eo"):
+            # the list never holds more than EO_LIST_CAP triangles (the executor's
+            # cap), nor, in practice, more than 64 per arc
+            total += int(min(EO_LIST_CAP, 64 * self.nnz) * (16 + 2 * 32) * 5 // 4)
+        return total
+
+
+# triangles an executor's edge-once list may hold (2 GB of list): enough for
+# the largest served graphs to list a window of the schedule per enumeration
+EO_LIST_CAP = 1 << 27
 
 
 @dataclass(order=True)
@@ -169,7 +180,7 @@ class Server:
 class GpuExecutor:
     """Runs one job on its own context/stream: upload, compress, divergence."""
 
-    def __init__(self, device: int = 0, eo_list_cap: int = 1 << 22):
+    def __init__(self, device: int = 0, eo_list_cap: int = EO_LIST_CAP):
         import paper_1912_08950_gb300 as sg
 
         self.sg = sg
@@ -193,6 +204,8 @@ class GpuExecutor:
                 H.free()
         finally:
             G.free()
+            # the job's memory estimate covers its list workspaces only while it runs
+            self.ctx.release_workspace()
         return d
 
     def close(self):
