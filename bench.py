@@ -162,6 +162,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def step_stats(samples):
+    """Median, extremes and a 95% percentile-bootstrap interval of the mean of
+    per-step times (fixed resampling seed)."""
+    import numpy as np
+
+    x = np.asarray(samples, dtype=np.float64)
+    rng = np.random.default_rng(12345)
+    means = x[rng.integers(0, x.size, size=(2000, x.size))].mean(axis=1)
+    return {"median": float(np.median(x)), "min": float(x.min()), "max": float(x.max()),
+            "ci95_mean": [float(np.percentile(means, 2.5)), float(np.percentile(means, 97.5))], "n": int(x.size)}
+
+
 def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0, listed_total=0):
     """Algorithmic bytes of one launch of a named kernel."""
     A = 2 * m
@@ -234,14 +246,18 @@ def run_ours(args, rank, world):
     clocks.start()
     time.sleep(0.3)
     barrier()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev0.record(stream)
-    for _ in range(args.steps):
+    marks[0].record(stream)
+    for i in range(args.steps):
         A_out = step()
+        marks[i + 1].record(stream)
     ev1.record(stream)
     barrier()
     clocks.stop()
     ctx.set_profiling(False)
     ms = ev0.elapsed_time(ev1) / args.steps
+    step_ms = step_stats([marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)])
     st = ctx.stats()
     kt = {}
     for name in ("tri_enum", "tri_hubs", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve", "tri_eo_list_accept",
@@ -352,7 +368,9 @@ def run_ours(args, rank, world):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
-    cpu = cpu_baseline(args) if rank == 0 and not args.no_cpu else None
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu
+    cpu = cpu_baseline(args) if cpu_leg else None
+    cpu_cores = cpu_all_cores(args) if cpu_leg else None
     clk = clocks.summary()
     res = {
         "metric": METRIC,
@@ -362,6 +380,7 @@ def run_ours(args, rank, world):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms,
+        "step_ms": step_ms,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -390,6 +409,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": 8 * (n + 1) + 4 * int(nnz_out)},
         "rows": rows,
         "cpu_baseline": cpu,
+        "cpu_all_cores": cpu_cores,
     }
     if rank == 0:
         print(json.dumps(res), flush=True)
@@ -557,6 +577,41 @@ def cpu_baseline(args):
     return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"R-MAT scale {CPU_SAMPLE_SCALE}, edge factor 16, seed 1 ({m} edges), "
                       f"{args.kernel} p={args.p}; single-threaded C oracle, {dt:.1f} s"}
+
+
+def _oracle_job(job):
+    """One oracle compress of a sample handed over as arrays (in a spawned worker)."""
+    import oracle
+
+    n, off, col, kernel, p, seed = job
+    t0 = time.perf_counter()
+    oracle.compress((n, off, col, None), kernel, p, seed)
+    return time.perf_counter() - t0
+
+
+def cpu_all_cores(args):
+    """The same single-threaded oracle on every host core at once: one sample run
+    per core, in spawned worker processes (the oracle itself is not changed)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import graphgen as gg
+    import oracle
+
+    oracle.build()
+    g = gg.rmat(CPU_SAMPLE_SCALE, 16, seed=1)
+    off, col, _ = g.numpy()
+    cores = os.cpu_count() or 1
+    tiny = (2, np.array([0, 1, 2], dtype=np.int64), np.array([1, 0], dtype=np.uint32), args.kernel, args.p, 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_job, [tiny] * cores, chunksize=1)  # workers up and the library loaded
+        t0 = time.perf_counter()
+        pool.map(_oracle_job, [(g.n, off, col, args.kernel, args.p, 1 + i) for i in range(cores)], chunksize=1)
+        dt = time.perf_counter() - t0
+    return {"value": cores * g.m / dt, "unit": "edges/s", "cores": cores, "kind": "oracle, one sample per core",
+            "sample": f"{cores} runs of the R-MAT scale {CPU_SAMPLE_SCALE} sample ({g.m} edges each), "
+                      f"{args.kernel} p={args.p}, seeds 1..{cores}, in {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
