@@ -49,11 +49,11 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than sca
 # figure no longer describes the kernel and the JSON line reports null.
 MEASURED_TRAFFIC = {
     # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
-    # profiles/tri_enum_rmat22_tr_eo.md: 38.01 GB read + 18.83 GB written
-    ("rmat22", "tr_eo"): (56833533000, "ab3ab9f85974aed780212aa4372ec8513a9f43ee5180b4c4250fb8127d3d54e4"),
-    # profiles/tri_enum_rmat26_tr_random.md: hub launch 1417.01 + 144.54 GB, main launch
-    # 514.11 + 12.09 GB (read + written) per union pass
-    ("rmat26", "tr_random"): (2087748801000, "ab3ab9f85974aed780212aa4372ec8513a9f43ee5180b4c4250fb8127d3d54e4"),
+    # profiles/tri_enum_rmat22_tr_eo.md: 37.92 GB read + 18.83 GB written
+    ("rmat22", "tr_eo"): (56742775000, "dce4cf25f773c3a7d5ef8372fac3c44f7990d873186e6b234c4d94ce0d686a29"),
+    # profiles/tri_enum_rmat26_tr_random.md: hub launch 1417.64 + 144.65 GB, main launch
+    # 513.55 + 12.06 GB (read + written) per union pass
+    ("rmat26", "tr_random"): (2087900042000, "dce4cf25f773c3a7d5ef8372fac3c44f7990d873186e6b234c4d94ce0d686a29"),
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 
@@ -185,6 +185,14 @@ def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0, listed_
         # for edge-once, the 16-byte record of every listed triangle
         per = max(launches, 1)
         return (8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs) + (4.0 * probes_total + 16.0 * listed_total) / per
+    if kernel == "tri_enum_forward":
+        # the enumeration's terms of the listing's byte model: E+ read once
+        # (off+ and N+), one 4-byte read per probe of the plain forward algorithm
+        # (W+ = sum over arcs u->v of d+(v); probes_total holds W+ scaled to the
+        # arcs the passes actually streamed) and, for edge-once, the 16-byte
+        # record of every listed triangle
+        per = max(launches, 1)
+        return (8 * (n + 1) + 4 * m) + (4.0 * probes_total + 16.0 * listed_total) / per
     if kernel == "tri_inarcs":
         # off+ and N+(u) of every vertex, the off+ pair and symmetric offsets of
         # every head, one 8-byte record written per gathered arc
@@ -278,9 +286,20 @@ def run_ours(args, rank, world):
         "compact_trmask": (kt["compact_trmask"][0], kt["compact_trmask"][1],
                            byte_model(n, m, A_out, 0, 1, "compact_trmask")),
     }
+    # the listing's byte model counts the plain forward algorithm's probes W+;
+    # the passes stream the shorter list of each arc instead (W probes), so W+
+    # is scaled by the share of W they streamed (later edge-once passes skip
+    # considered arcs)
+    fwd_total = work["forward_probes"] * st["probes"] / max(work["probes"], 1)
+    enum_fwd_bytes = byte_model(n, m, A_out, fwd_total, enum_launches, "tri_enum_forward", 0, st["eo_listed"])
     dom = max(cand, key=lambda k: cand[k][0])
     d_ms, d_launch, d_bytes = cand[dom]
     per_launch_s = d_ms / max(d_launch, 1) / 1e3
+    streamed = None
+    if dom == "tri_enum":
+        streamed = {"algorithmic_bytes_per_launch": d_bytes,
+                    "achieved": d_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None}
+        d_bytes = enum_fwd_bytes
     achieved = d_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
 
     # other rows of the hot path, timed once each (not part of the metric)
@@ -389,6 +408,7 @@ def run_ours(args, rank, world):
         "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "n": n, "m": m,
                    "eo_list_capacity": args.eo_list_cap,
                    "arcs": 2 * m, "triangles": work["triangles"], "probes_per_pass": work["probes"],
+                   "forward_probes": work["forward_probes"],
                    "head_arcs": work["head_arcs"],
                    "max_out_degree": work["max_out_degree"], "kept_arcs": int(A_out),
                    "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
@@ -397,7 +417,12 @@ def run_ours(args, rank, world):
                      "frac": (achieved / hbm) if achieved else None,
                      "traffic": measured_traffic(args.workload, args.kernel) if dom == "tri_enum" else None,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": d_bytes,
-                     "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch},
+                     "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch,
+                     "byte_model": ("forward listing: 8(n+1) + 4m + 4 W+ (+16 B per listed triangle)"
+                                    if dom == "tri_enum" else dom),
+                     "streamed": None if streamed is None else dict(
+                         streamed, frac=(streamed["achieved"] / hbm) if streamed["achieved"] else None,
+                         byte_model="probes made: 8(n+1) + 4n + 12m + 8H + 4 W (+16 B per listed triangle)")},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "eo_rounds_per_step": st["eo_rounds"] / args.steps,
         "eo_passes_per_step": st["eo_passes"] / args.steps,

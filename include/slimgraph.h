@@ -248,10 +248,13 @@ sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out);
  * d+(u), d+(v) (each arc streams its shorter list through a table of the
  * longer one, ties to d+(v)); the maximum out-degree; the triangle count; and
  * the number of arcs streamed from the head's side (those with
- * d+(u) < d+(v), gathered into per-vertex in-lists of 8 bytes each).  Used
+ * d+(u) < d+(v), gathered into per-vertex in-lists of 8 bytes each); and
+ * W+ = sum over oriented arcs u->v of d+(v), the probes of the plain forward
+ * algorithm that streams N+(v) for every arc (Sec. 4.3's listing cost).  Used
  * to turn kernel times into algorithmic bytes.  Any out pointer may be NULL. */
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out,
-                     int64_t *max_out_degree, int64_t *triangles_out, int64_t *head_arcs_out);
+                     int64_t *max_out_degree, int64_t *triangles_out, int64_t *head_arcs_out,
+                     int64_t *forward_probes_out);
 
 /* ------------------------------------------ accuracy metrics (Sec. 5) */
 

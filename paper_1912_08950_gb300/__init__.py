@@ -90,7 +90,7 @@ _SIGS = {
     "sg_batch_info": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                       C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sg_tr_work": [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "sg_low_degree": [_vp, _vp, _vp, _PP],
     "sg_bfs_levels": [_vp, _vp, _i64, _vp],
     "sg_critical_edges": [_vp, _vp, _i64, C.POINTER(C.c_int64)],
@@ -405,10 +405,11 @@ def triangle_count(g: Graph) -> int:
 
 
 def tr_work(g: Graph) -> dict:
-    m, w, md, t, ha = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
-    _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t), C.byref(ha)))
+    m, w, md, t, ha, wf = (C.c_int64() for _ in range(6))
+    _check(_lib.sg_tr_work(g.ctx.handle, g.handle, C.byref(m), C.byref(w), C.byref(md), C.byref(t), C.byref(ha),
+                           C.byref(wf)))
     return {"m": m.value, "probes": w.value, "max_out_degree": md.value, "triangles": t.value,
-            "head_arcs": ha.value}
+            "head_arcs": ha.value, "forward_probes": wf.value}
 
 
 class Batch:

@@ -644,23 +644,24 @@ sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg
 }
 
 sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *probes_out, int64_t *max_out_degree,
-                     int64_t *triangles_out, int64_t *head_arcs_out) {
+                     int64_t *triangles_out, int64_t *head_arcs_out, int64_t *forward_probes_out) {
     if (!ctx || !g) return fail(SG_ERR_INVALID_ARG, "NULL argument");
     Ctx *c = C_(ctx);
     sg_status st = set_device(c);
     if (st != SG_OK) return st;
     RowMaps rm;
     Oriented o;
-    int64_t t = 0, w = 0, md = 0, ha = 0;
+    int64_t t = 0, w = 0, md = 0, ha = 0, wf = 0;
     st = build_row_maps(c, G_(g), &rm);
     if (st == SG_OK) st = orient(c, G_(g), rm, false, &o);
-    if (st == SG_OK) st = tr_count(c, G_(g), o, &t, &w, &md, &ha);
+    if (st == SG_OK) st = tr_count(c, G_(g), o, &t, &w, &md, &ha, &wf);
     if (st == SG_OK) st = check_device_error(c);
     if (m_out) *m_out = g->nnz / 2;
     if (probes_out) *probes_out = w;
     if (max_out_degree) *max_out_degree = md;
     if (triangles_out) *triangles_out = t;
     if (head_arcs_out) *head_arcs_out = ha;
+    if (forward_probes_out) *forward_probes_out = wf;
     free_oriented(c, &o);
     free_row_maps(c, &rm);
     return st;
@@ -668,7 +669,7 @@ sg_status sg_tr_work(sg_ctx *ctx, const sg_graph *g, int64_t *m_out, int64_t *pr
 
 sg_status sg_triangle_count(sg_ctx *ctx, const sg_graph *g, int64_t *count_out) {
     if (!count_out) return fail(SG_ERR_INVALID_ARG, "NULL argument");
-    return sg_tr_work(ctx, g, nullptr, nullptr, nullptr, count_out, nullptr);
+    return sg_tr_work(ctx, g, nullptr, nullptr, nullptr, count_out, nullptr, nullptr);
 }
 
 }  // extern "C"

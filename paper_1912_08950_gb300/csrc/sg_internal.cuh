@@ -58,7 +58,7 @@ struct Ctx {
 };
 
 enum CtrIdx { kCtrProbes = 0, kCtrTriangles = 1, kCtrLive = 2, kCtrHeavy = 3, kCtrMaxDeg = 4, kCtrAux = 5,
-              kCtrInArcs = 7, kCtrWork = 8, kCtrCount = 9 };  // kCtrAux holds two words
+              kCtrInArcs = 7, kCtrWork = 8, kCtrWorkFwd = 9, kCtrCount = 10 };  // kCtrAux holds two words
 
 struct Graph {
     Ctx *ctx = nullptr;
@@ -218,7 +218,7 @@ sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out);
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed,
                   uint8_t *del);
 sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg,
-                   int64_t *in_arcs);
+                   int64_t *in_arcs, int64_t *fwd_probes);
 // batched union TR, with no host synchronisation (capturable in a CUDA graph)
 struct BatchTri {
     uint32_t *heavy = nullptr;

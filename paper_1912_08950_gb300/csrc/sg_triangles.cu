@@ -871,7 +871,9 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
                                      unsigned long long *ctr, int *err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    unsigned long long cnt = 0, work = 0;  // work: W, the probes of one enumeration pass
+    // work: W, the probes of one enumeration pass; fwd: W+ = sum of d+(v) over arcs u->v,
+    // the probes of the plain forward algorithm (every arc streams N+(v))
+    unsigned long long cnt = 0, work = 0, fwd = 0;
     for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n; u += nw) {
         const int64_t ou = __ldg(offp + u), du = __ldg(offp + u + 1) - ou;
         for (int64_t i = lane; i < du; i += 32) {
@@ -879,6 +881,7 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
             const int64_t ov = __ldg(offp + v);
             const int64_t dv = __ldg(offp + v + 1) - ov;
             work += (unsigned long long)(du < dv ? du : dv);
+            fwd += (unsigned long long)dv;
             if (du < dv) {
                 const int64_t sv = __ldg(offs + v);
                 const int64_t room = (__ldg(offs + v + 1) - sv) - dv;
@@ -894,8 +897,10 @@ __global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uin
     }
     cnt = warp_sum(cnt);
     work = warp_sum(work);
+    fwd = warp_sum(fwd);
     if (lane == 0 && cnt) atomicAdd(ctr + kCtrInArcs, cnt);
     if (lane == 0 && work) atomicAdd(ctr + kCtrWork, work);
+    if (lane == 0 && fwd) atomicAdd(ctr + kCtrWorkFwd, fwd);
 }
 
 // Also clamps every in-list length to its room (only an asymmetric input,
@@ -1729,7 +1734,7 @@ sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double
 }
 
 sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, int64_t *probes, int64_t *maxdeg,
-                   int64_t *in_arcs) {
+                   int64_t *in_arcs, int64_t *fwd_probes) {
     Plan pl;
     unsigned long long v0[kCtrCount] = {}, v1[kCtrCount] = {};
     sg_status st = read_ctr(c, 0, kCtrCount, v0);
@@ -1740,6 +1745,7 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
     if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
     if (maxdeg) *maxdeg = pl.max_deg;
     if (in_arcs) *in_arcs = (int64_t)(v1[kCtrInArcs] - v0[kCtrInArcs]);
+    if (fwd_probes) *fwd_probes = (int64_t)(v1[kCtrWorkFwd] - v0[kCtrWorkFwd]);
     free_plan(c, &pl);
     return st;
 }

@@ -142,6 +142,31 @@ def _eo_run(sg, ctx, g, kern, p, seed, cap):
         ctx.set_eo_list_capacity(0)
 
 
+def test_work_model(sg, ctx):
+    # W (shorter list per arc) and W+ (N+(v) per arc u->v) recounted in numpy
+    # from the degree order (d_u, u) < (d_v, v)
+    g = gg.rmat(12, 16, seed=6)
+    off, col, _ = g.numpy()
+    off = off.astype(np.int64)
+    col = col.astype(np.int64)
+    deg = np.diff(off)
+    src = np.repeat(np.arange(g.n), deg)
+    key = deg * (1 << 32) + np.arange(g.n)
+    fwd = key[src] < key[col]
+    s_, d_ = src[fwd], col[fwd]
+    dp = np.bincount(s_, minlength=g.n)
+    G = sg.Graph.from_csr(ctx, g)
+    w = sg.tr_work(G)
+    G.free()
+    assert w["m"] == fwd.sum()
+    assert w["forward_probes"] == int(dp[d_].sum())
+    # a table owner with d+ < 2 closes no triangle, so its arcs are not streamed
+    owner = np.where(dp[d_] <= dp[s_], s_, d_)
+    shorter = np.minimum(dp[s_], dp[d_])
+    assert w["probes"] == int(shorter[dp[owner] >= 2].sum())
+    assert w["head_arcs"] == int((dp[s_] < dp[d_]).sum())
+
+
 @pytest.mark.parametrize("cap", [-1, 4096, 60000, 250000, 0])
 @pytest.mark.parametrize("kern", ["tr_eo", "tr_eo_maxw", "tr_eo_mincount"])
 def test_eo_list_capacity_does_not_change_result(sg, ctx, kern, cap):
