@@ -349,6 +349,20 @@ def biclique_matched(k: int) -> CSR:
     return csr_from_edges(2 * k, torch.cat([left, ml]), torch.cat([right, ml + 1]))
 
 
+def hubs_over_leaves(k: int, h: int) -> CSR:
+    """h hubs joined to k middle vertices; each middle vertex also has k
+    leaves and a matching partner (k even), so it ranks above the hubs in the
+    degree order: every hub has out-degree k, and the k/2 matching edges close
+    a triangle with every hub (k/2 * h triangles)."""
+    mid = torch.arange(k, dtype=torch.int64)
+    hubs = k + torch.arange(h, dtype=torch.int64)
+    leaves = k + h + torch.arange(k * k, dtype=torch.int64)
+    ml = torch.arange(0, k - 1, 2, dtype=torch.int64)
+    src = torch.cat([mid.repeat_interleave(h), mid.repeat_interleave(k), ml])
+    dst = torch.cat([hubs.repeat(k), leaves, ml + 1])
+    return csr_from_edges(k + h + k * k, src, dst)
+
+
 def complete(k: int) -> CSR:
     return from_edge_list(k, [(i, j) for i in range(k) for j in range(i + 1, k)])
 

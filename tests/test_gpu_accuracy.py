@@ -68,11 +68,26 @@ def test_vertex_triangle_counts(sg, ctx, name):
 
 
 def test_vertex_triangle_counts_chunked_tables(sg, ctx):
-    g = gg.complete(600)  # N+(u) longer than one shared-memory table
+    g = gg.complete(600)  # N+(u) fills most of a 1024-entry table
     G = sg.Graph.from_csr(ctx, g)
     t = sg.vertex_triangle_counts(G).cpu().numpy()
     assert np.all(t == 599 * 598 // 2)
     G.free()
+
+
+@pytest.mark.parametrize("hub_launch", [True, False])
+def test_vertex_triangle_counts_long_out_lists(sg, ctx, hub_launch):
+    # out-degree 1100: 1100 such vertices go to the hub launch; 40 are too few
+    # for it and the main launch takes their N+(u) in two chunks
+    if hub_launch:
+        g, k, h = gg.biclique_matched(1100), 1100, 1100
+    else:
+        g, k, h = gg.hubs_over_leaves(1100, 40), 1100, 40
+    G = sg.Graph.from_csr(ctx, g)
+    t = sg.vertex_triangle_counts(G).cpu().numpy()
+    G.free()
+    assert np.array_equal(t, oracle.vertex_triangle_counts(g))
+    assert int(t.sum()) == 3 * (k // 2) * h
 
 
 @pytest.mark.parametrize("seed", [1, 2])

@@ -346,8 +346,8 @@ def test_errors(sg, ctx):
 @pytest.mark.parametrize("kern,p", [("tr_random", 0.3), ("tr_eo", 0.5), ("tr_eo", 1.0), ("tr_p2", 0.4),
                                     ("tr_mincount", 0.6), ("tr_eo_mincount", 1.0)])
 def test_chunked_heavy_tables(sg, ctx, kern, p):
-    # K600 has out-degrees up to 599: the largest vertices' N+(u) exceeds one
-    # shared-memory table and is processed in chunks
+    # K600: out-degrees up to 599 fill most of a 1024-entry table (the hub
+    # launch and the chunked paths have tests of their own below)
     g = gg.complete(600)
     _same(sg, ctx, g, kern, p, 12)
     G = sg.Graph.from_csr(ctx, g)
@@ -386,13 +386,7 @@ def test_few_hubs_chunked_in_main_launch(sg, ctx, kern):
     # launch takes their N+(u) in two chunks.  Each of the 1100 vertices below
     # the hubs gets 1100 leaves and a matching partner, so it ranks above them.
     k, h = 1100, 40
-    mid = torch.arange(k, dtype=torch.int64)
-    hubs = k + torch.arange(h, dtype=torch.int64)
-    leaves = k + h + torch.arange(k * k, dtype=torch.int64)
-    ml = torch.arange(0, k - 1, 2, dtype=torch.int64)
-    src = torch.cat([mid.repeat_interleave(h), mid.repeat_interleave(k), ml])
-    dst = torch.cat([hubs.repeat(k), leaves, ml + 1])
-    g = gg.csr_from_edges(k + h + k * k, src, dst)
+    g = gg.hubs_over_leaves(k, h)
     G = sg.Graph.from_csr(ctx, g)
     w = sg.tr_work(G)
     assert w["max_out_degree"] == k and w["triangles"] == (k // 2) * h

@@ -74,3 +74,18 @@ def test_rmat_batch_equals_individual_graphs():
         mem = gg.batch_member(u, vbase, i, 1 << s)
         assert torch.equal(mem.off, one.off) and torch.equal(mem.col, one.col), i
         assert abase[i] == int(u.off[vbase[i]])
+
+
+def test_structured_hub_generators():
+    # the matched biclique: k*k + k/2 edges, left degree k + 1, right degree k
+    g = gg.biclique_matched(10)
+    off, col, _ = g.numpy()
+    deg = np.diff(off)
+    assert g.m == 100 + 5 and np.all(deg[:10] == 11) and np.all(deg[10:] == 10)
+    # hubs over leaves: every middle vertex outranks the hubs
+    h = gg.hubs_over_leaves(6, 2)
+    off, col, _ = h.numpy()
+    deg = np.diff(off)
+    assert h.n == 6 + 2 + 36 and h.m == 12 + 36 + 3
+    assert np.all(deg[:6] == 2 + 6 + 1) and np.all(deg[6:8] == 6) and np.all(deg[8:] == 1)
+
