@@ -1,0 +1,32 @@
+"""Host-side helpers of bench.py, on CPU: the byte models, the per-step
+statistics and the guard that drops a measured DRAM figure once the
+enumeration sources change.  No GPU is involved."""
+import bench
+
+
+def test_step_stats():
+    st = bench.step_stats([82.0, 82.5, 83.0, 82.5])
+    assert st["median"] == 82.5 and st["min"] == 82.0 and st["max"] == 83.0 and st["n"] == 4
+    lo, hi = st["ci95_mean"]
+    assert 82.0 <= lo <= 82.5 <= hi <= 83.0
+    assert bench.step_stats([5.0])["ci95_mean"] == [5.0, 5.0]
+
+
+def test_enumeration_byte_models():
+    n, m = 1000, 8000
+    # the listing's model: E+ once, 4 B per forward probe, 16 B per listed triangle
+    assert bench.byte_model(n, m, 0, 10_000, 1, "tri_enum_forward", 0, 0) == 8 * (n + 1) + 4 * m + 40_000
+    assert bench.byte_model(n, m, 0, 20_000, 2, "tri_enum_forward", 0, 100) == 8 * (n + 1) + 4 * m + 40_000 + 800
+    # the probes-made model adds the in-list lengths, staged bounds and in-list records
+    got = bench.byte_model(n, m, 0, 10_000, 1, "tri_enum", 500, 0)
+    assert got == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * 500 + 40_000
+
+
+def test_measured_traffic_guarded_by_source_digest(monkeypatch):
+    d = bench.sources_digest()
+    assert len(d) == 64 and d == bench.sources_digest()
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("wl", "k"), (123, d))
+    assert bench.measured_traffic("wl", "k") == 123
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("wl", "k"), (123, "0" * 64))
+    assert bench.measured_traffic("wl", "k") is None
+    assert bench.measured_traffic("no such workload", "k") is None
