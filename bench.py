@@ -50,10 +50,10 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than sca
 MEASURED_TRAFFIC = {
     # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
     # profiles/tri_enum_rmat22_tr_eo.md: 37.92 GB read + 18.83 GB written
-    ("rmat22", "tr_eo"): (56742775000, "dce4cf25f773c3a7d5ef8372fac3c44f7990d873186e6b234c4d94ce0d686a29"),
+    ("rmat22", "tr_eo"): (56742775000, "94d004d8e9f7af0cd065222fa68884b845cbe2e00ca03967c9c33ca361122db6"),
     # profiles/tri_enum_rmat26_tr_random.md: hub launch 1417.64 + 144.65 GB, main launch
     # 513.55 + 12.06 GB (read + written) per union pass
-    ("rmat26", "tr_random"): (2087900042000, "dce4cf25f773c3a7d5ef8372fac3c44f7990d873186e6b234c4d94ce0d686a29"),
+    ("rmat26", "tr_random"): (2087900042000, "94d004d8e9f7af0cd065222fa68884b845cbe2e00ca03967c9c33ca361122db6"),
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 

@@ -15,7 +15,9 @@
 // sum over arcs of min(d+(u), d+(v)) -- under half of the plain forward
 // algorithm's sum of d+(v) on power-law graphs.  Vertices with a short N+(x)
 // and few in-arcs get one warp each; the others get a whole CTA whose warps
-// split the arcs.
+// split the arcs; those with an N+(x) longer than one CTA's table (when there
+// are at least as many as SMs) go first, to a launch of 32-warp CTAs, one per
+// SM, whose larger table holds their N+(x) whole.
 //
 // Decisions.  A hit (a triangle) is pushed to a per-warp queue; whenever 32
 // hits are queued the warp decides all of them at once with full lanes:
