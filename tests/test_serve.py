@@ -60,6 +60,19 @@ def test_all_jobs_complete_with_their_own_results():
     srv.close()
 
 
+def test_edge_once_jobs_reserve_their_list_workspaces():
+    from paper_1912_08950_gb300.serve import EO_LIST_CAP
+
+    small_u, small_eo = _job(kernel="tr_random"), _job(kernel="tr_eo")
+    # a small edge-once job reserves room for 64 listed triangles per arc
+    # (16 B listed + 2 x 32 B active, a quarter of headroom)
+    assert small_eo.device_bytes() - small_u.device_bytes() == 64 * 400 * 80 * 5 // 4
+    # a large one is bounded by the executor's list cap
+    big = _job(n=10, nnz=1 << 30, kernel="tr_eo_maxw")
+    big_u = _job(n=10, nnz=1 << 30, kernel="tr_maxw")
+    assert big.device_bytes() - big_u.device_bytes() == EO_LIST_CAP * 80 * 5 // 4
+
+
 def test_continuous_batching_overlaps_jobs():
     srv = _server(4, 1 << 40, delay=0.1)
     futs = []
