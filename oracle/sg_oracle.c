@@ -305,11 +305,12 @@ static void union_cb(uint32_t a, uint32_t b, uint32_t c, int64_t eab, int64_t ea
     U->del[e[k]] = 1; /* SG.del is idempotent */
 }
 
-/* Edge-Once: collect the selected triangles, sort, scan greedily. */
+/* Edge-Once: collect the selected triangles, sort, scan greedily.  A record
+ * holds only the sort key (r2, a, b, c): the scan looks the three edges up
+ * again and redraws r1, so that a scale-22 graph's billion selected
+ * triangles fit in host memory (16 bytes each). */
 typedef struct {
     uint32_t r2, a, b, c;
-    int64_t e[3];
-    uint32_t r1;
 } sel_tri;
 
 typedef struct {
@@ -331,10 +332,9 @@ static void eo_collect_cb(uint32_t a, uint32_t b, uint32_t c, int64_t eab, int64
         if (!nv) { E->oom = 1; return; }
         E->v = nv; E->cap = ncap;
     }
+    (void)eab; (void)eac; (void)ebc;
     sel_tri *t = &E->v[E->k++];
     t->r2 = r[2]; t->a = a; t->b = b; t->c = c;
-    t->e[0] = eab; t->e[1] = eac; t->e[2] = ebc;
-    t->r1 = r[1];
 }
 
 static int sel_cmp(const void *x, const void *y)
@@ -430,14 +430,28 @@ int64_t orc_compress(int64_t n, int64_t nnz, const int64_t *off, const uint32_t 
         int64_t *tc = kernel == ORC_TR_EO_MINCOUNT ? edge_triangle_counts(n, nnz, off, col) : NULL;
         if (!considered || (kernel == ORC_TR_EO_MINCOUNT && !tc)) { free(tc); free(considered); free(E.v); free(del); return -3; }
         for (int64_t s = 0; s < E.k; ++s) {
-            sel_tri *t = &E.v[s];
-            if (considered[t->e[0]] || considered[t->e[1]] || considered[t->e[2]]) continue;
-            considered[t->e[0]] = considered[t->e[1]] = considered[t->e[2]] = 1;
+            const sel_tri *t = &E.v[s];
+            /* the canonical ids of {a,b}, {a,c}, {b,c} */
+            int64_t e[3];
+            e[0] = find_arc(off, col, t->a, t->b);
+            if (considered[e[0]]) continue;
+            e[1] = find_arc(off, col, t->a, t->c);
+            if (considered[e[1]]) continue;
+            e[2] = find_arc(off, col, t->b, t->c);
+            if (considered[e[2]]) continue;
+            considered[e[0]] = considered[e[1]] = considered[e[2]] = 1;
             uint32_t lo[3] = {t->a, t->a, t->b}, hi[3] = {t->b, t->c, t->c};
-            int k = (kernel == ORC_TR_EO_MAXW) ? maxw_choice(w, t->e, lo, hi)
-                  : (kernel == ORC_TR_EO_MINCOUNT) ? mincount_choice(tc, t->e, lo, hi)
-                                                   : random_choice(t->r1);
-            del[t->e[k]] = 1;
+            int k;
+            if (kernel == ORC_TR_EO_MAXW) {
+                k = maxw_choice(w, e, lo, hi);
+            } else if (kernel == ORC_TR_EO_MINCOUNT) {
+                k = mincount_choice(tc, e, lo, hi);
+            } else {
+                uint32_t r[4];
+                draw(E.seed, t->a, t->b, t->c, ORC_TAG_TRI, r);
+                k = random_choice(r[1]);
+            }
+            del[e[k]] = 1;
         }
         free(tc);
         if (accepted_out) {
