@@ -161,6 +161,15 @@ sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records);
  * Errors: SG_ERR_INVALID_ARG (ctx == NULL). */
 sg_status sg_ctx_release_workspace(sg_ctx *ctx);
 
+/* Device memory free for new work on CUDA device `device`, in bytes: what
+ * the driver reports free (cudaMemGetInfo) plus what the device's default
+ * stream-ordered pool holds from freed allocations but does not use (this
+ * library keeps freed memory in that pool between calls).  The paper has no
+ * counterpart: serving admits jobs by it.  The caller's current device is
+ * left unchanged.
+ * Errors: SG_ERR_INVALID_ARG (free_out == NULL, no such device), SG_ERR_CUDA. */
+sg_status sg_device_free_memory(int device, uint64_t *free_out);
+
 /* ----------------------------------------------------------------- graphs */
 
 /* Wrap or copy a device CSR.  copy = 0 borrows the caller's buffers (they must
@@ -320,18 +329,31 @@ sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg
  * the output (off_out[n+1], col_out with room for nnz arcs, since the output
  * is a subset of the input); the result equals sg_compress(G, SG_UNIFORM, p,
  * seed) bit for bit and *nnz_out (host) receives its arc count.
+ * The input must be a valid symmetric CSR as defined at the top of this
+ * header; the call checks only that off[0] = 0 and off[n] = nnz
+ * (SG_ERR_INVALID_GRAPH otherwise).
  * Scratch lives in one fixed device array inside the library (about 3 MB per
  * GPU that loads it, held until the process exits), which caps the input at
  * nnz <= 134217728 arcs; larger inputs return SG_ERR_UNSUPPORTED.
- * The first call on a device looks up that array's device address; make the
- * first call before any stream capture.  The call synchronises cuda_stream.
- * All calls share the one array: calls that overlap on the GPU (different
- * streams, threads or processes sharing the library) race and must be
- * serialised by the caller.  No context is needed; errors are reported as by
- * every other entry point (sg_last_error). */
+ * The first call on a device looks up that array's device address and keeps
+ * it for the life of the process (a cudaDeviceReset of that device makes the
+ * kept address stale); make the first call before any stream capture.  The
+ * call synchronises cuda_stream and leaves the caller's current device as it
+ * found it.  All calls share the one array: calls that overlap on the GPU
+ * (different streams, threads or processes sharing the library) race and
+ * must be serialised by the caller.  No context is needed; errors are
+ * reported as by every other entry point (sg_last_error). */
 sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz, const int64_t *off,
                                       const uint32_t *col, double p, uint64_t seed, int64_t *off_out,
                                       uint32_t *col_out, int64_t *nnz_out);
+
+/* Architecture of the library's device code as loaded on `device`
+ * (cudaFuncAttributes.binaryVersion of one of its kernels: 103 for sm_103a).
+ * The paper has no counterpart: it lets a caller check at run time that the
+ * build matches the GPU.  The caller's current device is left unchanged.
+ * Errors: SG_ERR_INVALID_ARG (NULL, no such device), SG_ERR_CUDA (no image
+ * for this device). */
+sg_status sg_kernel_arch(int device, int *binary_version);
 
 /* Message describing the last non-OK status returned on this thread. */
 const char *sg_last_error(void);

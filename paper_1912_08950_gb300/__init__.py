@@ -73,6 +73,8 @@ _SIGS = {
     "sg_ctx_reset_profile": [_vp],
     "sg_ctx_set_eo_list_capacity": [_vp, _i64],
     "sg_ctx_release_workspace": [_vp],
+    "sg_device_free_memory": [_int, C.POINTER(C.c_uint64)],
+    "sg_kernel_arch": [_int, C.POINTER(C.c_int)],
     "sg_graph_from_device": [_vp, C.POINTER(CsrView), _int, _int, _PP],
     "sg_graph_from_host": [_vp, _i64, _i64, _vp, _vp, _vp, _PP],
     "sg_graph_view": [_vp, C.POINTER(CsrView)],
@@ -275,6 +277,13 @@ class Graph:
             self.free()
         except Exception:
             pass
+
+
+def device_free_memory(device: int = 0) -> int:
+    """Bytes of device memory free for new work (driver free + unused pool memory)."""
+    v = C.c_uint64()
+    _check(_lib.sg_device_free_memory(int(device), C.byref(v)))
+    return v.value
 
 
 def compress(g: Graph, kernel, p: float, seed: int, want_weights: bool = False) -> Graph:

@@ -288,6 +288,30 @@ sg_status sg_ctx_release_workspace(sg_ctx *ctx) {
     return SG_OK;
 }
 
+sg_status sg_device_free_memory(int device, uint64_t *free_out) {
+    if (!free_out) return fail(SG_ERR_INVALID_ARG, "free_out is NULL");
+    int ndev = 0, prev = 0;
+    SG_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SG_ERR_INVALID_ARG, "no such device");
+    SG_CUDA(cudaGetDevice(&prev));
+    SG_CUDA(cudaSetDevice(device));
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    uint64_t total = fr;
+    cudaMemPool_t pool;
+    if (e == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        // memory the stream-ordered pool keeps from freed allocations is free too
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            total += reserved - used;
+    }
+    (void)cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    *free_out = total;
+    return SG_OK;
+}
+
 sg_status sg_ctx_kernel_time(sg_ctx *ctx, const char *prefix, double *ms, int64_t *launches) {
     if (!ctx || !prefix || !ms || !launches) return fail(SG_ERR_INVALID_ARG, "NULL argument");
     Ctx *c = C_(ctx);

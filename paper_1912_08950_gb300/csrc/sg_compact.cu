@@ -291,7 +291,9 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
             }
         }
         // new row offsets for the rows whose start lies in this tile
-        const int64_t v0 = __ldg(a.tile_vlo + tile), v1 = __ldg(a.tile_vlo + tile + 1);
+        // (clamped to the offset array: only a malformed CSR could put them outside)
+        const int64_t v0 = max(__ldg(a.tile_vlo + tile), (int64_t)0);
+        const int64_t v1 = min(__ldg(a.tile_vlo + tile + 1), a.n + 1);
         const int64_t tlen = t1 - t0;
         for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
             const int64_t q = __ldg(a.off + v) - t0;
@@ -780,6 +782,23 @@ sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out) 
 
 }  // namespace sg
 
+// ----------------------------------------------------- build information
+extern "C" sg_status sg_kernel_arch(int device, int *binary_version) {
+    using namespace sg;
+    if (!binary_version) return fail(SG_ERR_INVALID_ARG, "binary_version is NULL");
+    int ndev = 0, prev = 0;
+    SG_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SG_ERR_INVALID_ARG, "no such device");
+    SG_CUDA(cudaGetDevice(&prev));
+    SG_CUDA(cudaSetDevice(device));
+    cudaFuncAttributes attr;
+    const cudaError_t e = cudaFuncGetAttributes(&attr, row_maps_kernel);
+    (void)cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    *binary_version = attr.binaryVersion;
+    return SG_OK;
+}
+
 // ------------------------------------------------ no-allocation entry point
 // Uniform edge sampling for callers that must not allocate device memory:
 // the scratch (row maps, tile status words, the tile ticket and an error
@@ -806,7 +825,8 @@ std::mutex g_na_mutex;
 unsigned char *g_na_ptr[kNaMaxDevices] = {};
 
 // Device address of the scratch array on `device` (which must be current).
-// Looked up once per device and cached.
+// Looked up once per device and cached; a cudaDeviceReset of that device
+// would leave the cached address stale.
 cudaError_t na_scratch(int device, unsigned char **out) {
     std::lock_guard<std::mutex> lock(g_na_mutex);
     if (!g_na_ptr[device]) {
@@ -822,10 +842,12 @@ cudaError_t na_scratch(int device, unsigned char **out) {
 }  // namespace
 }  // namespace sg
 
-extern "C" sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz,
-                                                 const int64_t *off, const uint32_t *col, double p, uint64_t seed,
-                                                 int64_t *off_out, uint32_t *col_out, int64_t *nnz_out) {
-    using namespace sg;
+namespace sg {
+namespace {
+
+sg_status noalloc_uniform(int device, void *cuda_stream, int64_t n, int64_t nnz, const int64_t *off,
+                          const uint32_t *col, double p, uint64_t seed, int64_t *off_out, uint32_t *col_out,
+                          int64_t *nnz_out) {
     if (!off || !off_out || !nnz_out || (nnz > 0 && (!col || !col_out)))
         return fail(SG_ERR_INVALID_ARG, "NULL argument");
     if (n < 0 || nnz < 0) return fail(SG_ERR_INVALID_ARG, "negative size");
@@ -840,11 +862,18 @@ extern "C" sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, 
     if (device < 0 || device >= ndev || device >= kNaMaxDevices) return fail(SG_ERR_INVALID_ARG, "no such device");
     SG_CUDA(cudaSetDevice(device));
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    *nnz_out = 0;
+    // the CSR's ends must match its sizes: the row maps cover [off[0], off[n]]
+    int64_t ends[2] = {0, 0};
+    SG_CUDA(cudaMemcpyAsync(&ends[0], off, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    SG_CUDA(cudaMemcpyAsync(&ends[1], off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    SG_CUDA(cudaStreamSynchronize(stream));
+    if (ends[0] != 0 || ends[1] != nnz)
+        return fail(SG_ERR_INVALID_GRAPH, "off[0] must be 0 and off[n] must equal nnz");
     unsigned char *base = nullptr;
     SG_CUDA(na_scratch(device, &base));
     int *err = reinterpret_cast<int *>(base + kNaErrOff);
     SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), stream));
-    *nnz_out = 0;
     if (nnz == 0) {
         SG_CUDA(cudaMemsetAsync(off_out, 0, sizeof(int64_t) * (size_t)(n + 1), stream));
         SG_CUDA(cudaStreamSynchronize(stream));
@@ -893,5 +922,23 @@ extern "C" sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, 
     if (code != kDevOk) return fail(SG_ERR_TIMEOUT, "a device-side wait of the prefix scan gave up; outputs are invalid");
     *nnz_out = count;
     return SG_OK;
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz,
+                                                 const int64_t *off, const uint32_t *col, double p, uint64_t seed,
+                                                 int64_t *off_out, uint32_t *col_out, int64_t *nnz_out) {
+    // the caller's current device is put back whatever happens
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        prev = -1;
+    }
+    const sg_status st = sg::noalloc_uniform(device, cuda_stream, n, nnz, off, col, p, seed, off_out, col_out,
+                                             nnz_out);
+    if (prev >= 0) (void)cudaSetDevice(prev);
+    return st;
 }
 

@@ -4,8 +4,9 @@ Some callers cannot let a library call cudaMalloc (their own allocator owns
 the GPU's memory, or the memory was reserved up front), so the library offers
 sg_compress_uniform_noalloc, which keeps its scratch in a fixed device array.
 Its output must equal the regular sg_compress(SG_UNIFORM) output bit for bit,
-on two calls in a row, because every call reuses the same scratch array.
-This file is collected last so that a failure here cannot hide other tests.
+and the oracle's, on calls in a row, because every call reuses the same
+scratch array.  This file is collected last so that a failure here cannot
+hide other tests.
 """
 import ctypes
 
@@ -14,6 +15,7 @@ import pytest
 import torch
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +42,7 @@ def _regular(sg, ctx, g, p, seed):
     return off, col
 
 
-def test_noalloc_matches_regular_entry_point_twice_in_a_row():
+def test_noalloc_matches_regular_entry_point_and_oracle_twice_in_a_row():
     import paper_1912_08950_gb300 as sg
 
     ctx = sg.Context(0)
@@ -50,13 +52,24 @@ def test_noalloc_matches_regular_entry_point_twice_in_a_row():
     # a larger call first, then a smaller one: stale scratch must not leak
     for g, p, seed in ((big, 0.5, 11), (small, 0.3, 12), (small, 0.3, 12)):
         got = _noalloc(sg, g, p, seed, stream)
-        want = _regular(sg, ctx, g.to("cpu"), p, seed)
-        assert np.array_equal(got[0], want[0])
-        assert np.array_equal(got[1], want[1])
+        host = g.to("cpu")
+        want = _regular(sg, ctx, host, p, seed)
+        o_off, o_col, _ = oracle.compress(host, "uniform", p, seed)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        assert np.array_equal(got[0], o_off) and np.array_equal(got[1], o_col)
     ctx.close()
 
 
-def test_noalloc_rejects_oversized_input():
+def test_noalloc_keeps_the_callers_current_device():
+    import paper_1912_08950_gb300 as sg
+
+    g = gg.rmat(10, 8, seed=5).to("cuda")
+    before = torch.cuda.current_device()
+    _noalloc(sg, g, 0.5, 1, torch.cuda.Stream())
+    assert torch.cuda.current_device() == before
+
+
+def test_noalloc_rejects_oversized_and_malformed_input():
     import paper_1912_08950_gb300 as sg
 
     cnt = ctypes.c_int64()
@@ -65,3 +78,12 @@ def test_noalloc_rejects_oversized_input():
                                               dummy.data_ptr(), dummy.data_ptr(), ctypes.byref(cnt))
     assert st == sg.SG_ERR_UNSUPPORTED
     assert b"134217728" in sg.lib().sg_last_error()
+    # offsets whose last entry disagrees with nnz are refused before any launch
+    off = torch.tensor([0, 1, 5], dtype=torch.int64, device="cuda")
+    col = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
+    out_off = torch.empty(3, dtype=torch.int64, device="cuda")
+    out_col = torch.empty(2, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    st = sg.lib().sg_compress_uniform_noalloc(0, None, 2, 2, off.data_ptr(), col.data_ptr(), 0.5, 1,
+                                              out_off.data_ptr(), out_col.data_ptr(), ctypes.byref(cnt))
+    assert st == sg.SG_ERR_INVALID_GRAPH
