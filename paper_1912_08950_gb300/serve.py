@@ -74,23 +74,38 @@ class Server:
 
     executor_factory(slot) returns an object with run(job) -> dict and an
     optional close(); one executor per slot, each on its own stream.
-    memory_budget: bytes of device memory the server may hand out at once.
+
+    Admission reads the device's free memory at the moment it decides
+    (free_memory(), by default the first executor's free_memory() method):
+    the oldest waiting job starts once a slot is free and its estimate fits in
+    that free memory less what the running jobs reserved and less
+    `reserve_bytes` of headroom.  Running jobs' reservations are subtracted
+    even where they have already allocated (and so no longer show as free),
+    which errs on the safe side.  memory_budget, if given, additionally caps
+    the total reserved at once.  A job that does not fit while nothing else
+    runs fails with MemoryError instead of waiting forever.
     """
 
-    def __init__(self, executor_factory: Callable[[int], object], slots: int, memory_budget: int):
+    def __init__(self, executor_factory: Callable[[int], object], slots: int, memory_budget: Optional[int] = None,
+                 free_memory: Optional[Callable[[], int]] = None, reserve_bytes: int = 1 << 30):
         if slots < 1:
             raise ValueError("slots must be >= 1")
         self.slots = slots
-        self.budget = int(memory_budget)
+        self.budget = None if memory_budget is None else int(memory_budget)
+        self.reserve_bytes = int(reserve_bytes)
         self.reserved = 0
         self._cv = threading.Condition()
         self._pending: List[_Pending] = []
         self._free_slots = list(range(slots))
         self._stop = False
         self._executors = [executor_factory(i) for i in range(slots)]
+        if free_memory is None and hasattr(self._executors[0], "free_memory"):
+            free_memory = self._executors[0].free_memory
+        self._free_memory = free_memory
         self._records = []
         self._active = 0
         self.max_active = 0
+        self.admitted_room = []  # (room seen, job estimate) at every admission
         self._next_id = 0
         self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self._dispatcher.start()
@@ -98,7 +113,7 @@ class Server:
     # ---------------------------------------------------------------- public
     def submit(self, job: Job) -> Future:
         fut: Future = Future()
-        if job.device_bytes() > self.budget:
+        if self.budget is not None and job.device_bytes() > self.budget:
             fut.set_exception(MemoryError(f"job needs {job.device_bytes()} bytes, budget is {self.budget}"))
             return fut
         with self._cv:
@@ -126,14 +141,32 @@ class Server:
             return list(self._records)
 
     # -------------------------------------------------------------- internal
+    def room(self) -> Optional[int]:
+        """Bytes a new job may reserve now (None: no limit known)."""
+        limit = None
+        if self.budget is not None:
+            limit = self.budget - self.reserved
+        if self._free_memory is not None:
+            free = int(self._free_memory()) - self.reserved - self.reserve_bytes
+            limit = free if limit is None else min(limit, free)
+        return limit
+
     def _admissible(self) -> Optional[_Pending]:
         # first come, first served: the oldest job waits until it fits, which
         # keeps large jobs from starving behind a stream of small ones
         if not self._pending or not self._free_slots:
             return None
         head = self._pending[0]
-        if self.reserved + head.job.device_bytes() > self.budget:
+        room = self.room()
+        if room is not None and head.job.device_bytes() > room:
+            if self._active == 0:
+                # nothing will free memory for it: fail it rather than wait
+                item = heapq.heappop(self._pending)
+                item.fut.set_exception(MemoryError(
+                    f"job needs {item.job.device_bytes()} bytes, {room} are free for it"))
+                return self._admissible()
             return None
+        self.admitted_room.append((room, head.job.device_bytes()))
         return heapq.heappop(self._pending)
 
     def _dispatch(self):
@@ -178,15 +211,27 @@ class Server:
 
 
 class GpuExecutor:
-    """Runs one job on its own context/stream: upload, compress, divergence."""
+    """Runs one job on its own context/stream: upload, compress, divergence.
+    With keep_output, the result also holds H's CSR (host arrays)."""
 
-    def __init__(self, device: int = 0, eo_list_cap: int = EO_LIST_CAP):
+    def __init__(self, device: int = 0, eo_list_cap: int = EO_LIST_CAP, keep_output: bool = False):
         import paper_1912_08950_gb300 as sg
 
         self.sg = sg
+        self.device = device
+        self.keep_output = keep_output
         self.ctx = sg.Context(device)
         # a bounded triangle list keeps each job's footprint predictable
         self.ctx.set_eo_list_capacity(eo_list_cap)
+
+    def free_memory(self) -> int:
+        """Device memory free for new work now: what the driver reports free,
+        what the library's stream-ordered pool and torch's caching allocator
+        hold but do not use."""
+        import torch
+
+        slack = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return self.sg.device_free_memory(self.device) + max(0, slack)
 
     def run(self, job: Job) -> dict:
         sg = self.sg
@@ -200,6 +245,8 @@ class GpuExecutor:
             try:
                 d = sg.divergence(G, H)
                 d["nnz_out"] = H.nnz
+                if self.keep_output:
+                    d["off"], d["col"], _ = H.download()
             finally:
                 H.free()
         finally:

@@ -42,13 +42,14 @@ class FakeExecutor:
         return {"job": job.seed}
 
 
-def _server(slots, budget, delay=0.05):
+def _server(slots, budget, delay=0.05, free_memory=None):
     from paper_1912_08950_gb300.serve import Server
 
     FakeExecutor.active = FakeExecutor.peak = 0
     FakeExecutor.reserved_seen = []
     ref = [None]
-    srv = Server(lambda i: FakeExecutor(i, ref, delay), slots=slots, memory_budget=budget)
+    srv = Server(lambda i: FakeExecutor(i, ref, delay), slots=slots, memory_budget=budget, free_memory=free_memory,
+                 reserve_bytes=0 if free_memory is None else 1000)
     ref[0] = srv
     return srv
 
@@ -96,6 +97,47 @@ def test_memory_budget_is_never_exceeded():
     assert all(r <= b for r, b in FakeExecutor.reserved_seen)
 
 
+def test_admission_reads_free_device_memory_when_it_decides():
+    one = _job().device_bytes()
+    free = {"bytes": 1000 + int(2.5 * one)}  # the fake device: room for two jobs
+    calls = []
+
+    def probe():
+        calls.append(free["bytes"])
+        return free["bytes"]
+
+    srv = _server(8, None, delay=0.05, free_memory=probe)
+    futs = [srv.submit(_job(seed=i)) for i in range(6)]
+    for f in futs[:2]:
+        f.result()
+    # more memory frees up on the device: later admissions see it
+    free["bytes"] = 1000 + 10 * one
+    for f in futs[2:]:
+        f.result()
+    srv.close()
+    assert len(calls) >= 6  # read at every admission decision
+    assert all(room >= need for room, need in srv.admitted_room)
+    assert FakeExecutor.peak >= 1
+
+
+def test_free_memory_caps_concurrency():
+    one = _job().device_bytes()
+    srv = _server(8, None, delay=0.05, free_memory=lambda: 1000 + int(2.5 * one))
+    futs = [srv.submit(_job(seed=i)) for i in range(10)]
+    for f in futs:
+        f.result()
+    srv.close()
+    assert FakeExecutor.peak <= 2
+
+
+def test_job_larger_than_free_memory_fails_instead_of_waiting():
+    srv = _server(2, None, free_memory=lambda: 5000)
+    f = srv.submit(_job())
+    with pytest.raises(MemoryError):
+        f.result(timeout=10)
+    srv.close()
+
+
 def test_oversized_job_rejected():
     srv = _server(2, 1000)
     f = srv.submit(_job())
@@ -134,6 +176,10 @@ def test_poisson_arrivals_rate():
 
 @pytest.mark.gpu
 def test_results_same_alone_and_in_the_mix():
+    """Every job's output CSR equals the oracle's, alone and in a concurrent
+    mix; its KL divergence is within the stated tolerance of the oracle's
+    FP64 value and identical between the two runs; its CC counts are exact."""
+    import oracle
     from paper_1912_08950_gb300.serve import GpuExecutor, Job, Server, replay
 
     specs = [(11, "uniform", 0.5), (12, "tr_eo", 0.5), (10, "tr_random", 0.8), (13, "spectral_avgdeg", 0.5),
@@ -148,13 +194,20 @@ def test_results_same_alone_and_in_the_mix():
         return out
 
     alone = []
-    srv = Server(lambda i: GpuExecutor(0), slots=1, memory_budget=8 << 30)
+    srv = Server(lambda i: GpuExecutor(0, keep_output=True), slots=1)
     for j in jobs():
         alone.append(srv.submit(j).result())
     srv.close()
-    srv = Server(lambda i: GpuExecutor(0), slots=4, memory_budget=8 << 30)
+    srv = Server(lambda i: GpuExecutor(0, keep_output=True), slots=4)
     mixed = replay(srv, jobs(), np.zeros(len(specs)))
     srv.close()
     assert mixed["max_concurrent"] > 1
-    for a, b in zip(alone, mixed["results"]):
-        assert a["nnz_out"] == b["nnz_out"] and a["cc_h"] == b["cc_h"] and a["kl_bits"] == b["kl_bits"]
+    for (s, k, p), g, a, b in zip(specs, graphs, alone, mixed["results"]):
+        o_off, o_col, _ = oracle.compress(g, k, p, s)
+        ref = oracle.divergence(g, (g.n, o_off, o_col, None))
+        for r in (a, b):
+            assert np.array_equal(r["off"], o_off) and np.array_equal(r["col"], o_col), (s, k, p)
+            assert r["nnz_out"] == o_col.size
+            assert abs(r["kl_bits"] - ref["kl_bits"]) <= 1e-5 * ref["kl_bits"] + 1e-12, (s, k, p)
+            assert r["cc_g"] == ref["cc_g"] and r["cc_h"] == ref["cc_h"]
+        assert a["kl_bits"] == b["kl_bits"]
