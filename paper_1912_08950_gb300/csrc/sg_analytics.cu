@@ -411,16 +411,18 @@ __global__ void __launch_bounds__(kPrThreads) sum2_kernel(const float *__restric
     }
 }
 
+// Per-vertex terms in FP32, summed in FP64.  With p_i = P_i / S_P and
+// q_i = Q_i / S_Q (S the FP64 sums), sum_i p_i log2(p_i / q_i)
+//   = (sum_i P_i log2(P_i / Q_i)) / S_P + log2(S_Q / S_P),
+// so a term is the FP32 product P_i * log2f(P_i / Q_i) of the raw values and
+// the normalisation enters once, in FP64, after the sum.
 __global__ void __launch_bounds__(kPrThreads) kl_terms_kernel(const float *__restrict__ P, const float *__restrict__ Q,
-                                                              int64_t n, const double *__restrict__ sums,
-                                                              double *__restrict__ parts) {
+                                                              int64_t n, double *__restrict__ parts) {
     __shared__ double s[kPrThreads];
-    const double sp = sums[0], sq = sums[1];
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kPrThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPrThreads) {
-        const double p = (double)P[i] / sp;
-        const double q = (double)Q[i] / sq;
-        if (p > 0.0) acc += p * log2(p / q);
+        const float p = P[i];
+        if (p > 0.f) acc += (double)(p * log2f(p / Q[i]));
     }
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -461,16 +463,22 @@ sg_status kl_divergence(Ctx *c, int64_t n, const float *P, const float *Q, doubl
     }
     {
         SG_LAUNCH(c, "kl_terms");
-        kl_terms_kernel<<<blocks, kPrThreads, 0, c->stream>>>(P, Q, n, sums, terms);
+        kl_terms_kernel<<<blocks, kPrThreads, 0, c->stream>>>(P, Q, n, terms);
     }
     {
         SG_LAUNCH(c, "kl_reduce");
         reduce_parts_kernel<double><<<1, kPrThreads, 0, c->stream>>>(terms, blocks, tot);
     }
     SG_CUDA(cudaGetLastError());
-    SG_CUDA(cudaMemcpyAsync(c->h_pinned, tot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    // sums (S_P, S_Q) and the term total are adjacent: one copy
+    static_assert(sizeof(double) == sizeof(int64_t), "pinned scratch holds doubles");
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned, sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(cudaMemcpyAsync(c->h_pinned + 2, tot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(cudaStreamSynchronize(c->stream));
-    std::memcpy(kl, c->h_pinned, sizeof(double));
+    double h[3];
+    std::memcpy(h, c->h_pinned, sizeof(h));
+    // FP64: the sum of the FP32 terms, normalised (see kl_terms_kernel)
+    *kl = (h[0] > 0.0 && h[1] > 0.0) ? h[2] / h[0] + std::log2(h[1] / h[0]) : 0.0;
     dfree(c, buf);
     return SG_OK;
 }

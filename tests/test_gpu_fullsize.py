@@ -114,8 +114,10 @@ def test_analytics_full_size(sg, big):
     H = sg.compress(G, "tr_eo", 0.5, 1)
     d = sg.divergence(G, H)
     off, col, _ = H.download()
-    P, _ = oracle.pagerank(g)
-    Q, _ = oracle.pagerank((g.n, off, col, None))
+    P, rp = oracle.pagerank(g)
+    Q, rq = oracle.pagerank((g.n, off, col, None))
+    # FP64 residuals of the FP32 iterates: within 2e-5 sum(x) of the oracle's
+    assert abs(d["pr_residual_g"] - rp) <= 2e-5 and abs(d["pr_residual_h"] - rq) <= 2e-5
     x, _ = sg.pagerank(G)
     rel = np.abs(x.cpu().numpy().astype(np.float64) - P) / P
     assert rel.max() <= 1e-5, rel.max()

@@ -230,6 +230,24 @@ def _pr_check(sg, ctx, g):
     x = x.cpu().numpy().astype(np.float64)
     rel = np.abs(x - ref) / ref
     assert rel.max() <= 1e-5, rel.max()
+    # the residual ||x50 - x49||_1 in FP64: both FP32 iterates lie within
+    # 1e-5 relative of the FP64 ones, so it is within 2e-5 sum(x) = 2e-5
+    assert abs(r - rr) <= 2e-5, (r, rr)
+    G.free()
+
+
+def test_pagerank_residual_star_two_iterations(sg, ctx):
+    # the hand-worked two-update star (see the oracle's pin): FP32 values, FP64 residual
+    k, d = 5, 0.85
+    n = k + 1
+    b = (1 - d) / n
+    c1, l1 = b + d * k / n, b + d / (n * k)
+    c2, l2 = b + d * k * l1, b + d * c1 / k
+    want = abs(c2 - c1) + k * abs(l2 - l1)
+    G = sg.Graph.from_csr(ctx, gg.star(k))
+    x, r = sg.pagerank(G, d, 2)
+    _, rr = oracle.pagerank(gg.star(k), d, 2)
+    assert abs(r - want) <= 1e-5 * want and abs(r - rr) <= 1e-5 * rr
     G.free()
 
 
@@ -259,6 +277,8 @@ def test_divergence_rmat14(sg, ctx, rmat14, kern, p):
     assert abs(d["kl_bits"] - ref["kl_bits"]) <= 1e-5 * ref["kl_bits"] + 1e-12, (d["kl_bits"], ref["kl_bits"])
     assert d["cc_g"] == ref["cc_g"] and d["cc_h"] == ref["cc_h"]
     assert d["m_g"] == rmat14.m and d["m_h"] == col.size // 2
+    assert abs(d["pr_residual_g"] - ref["pr_residual_g"]) <= 2e-5
+    assert abs(d["pr_residual_h"] - ref["pr_residual_h"]) <= 2e-5
     H.free()
     G.free()
 

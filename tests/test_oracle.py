@@ -424,6 +424,38 @@ def test_pagerank_star_closed_form():
     assert np.allclose(x[1:], xl, rtol=1e-12)
 
 
+def test_pagerank_residual_zero_on_power_of_two_cycle():
+    # n and every degree powers of two: 1/n, the shares x/d and their sums are
+    # exact in binary, and (1 - d)/n + d/n rounds to 1/n, so no update moves x
+    x, r = oracle.pagerank(gg.cycle(16), 0.85, 50)
+    assert np.all(x == 1.0 / 16) and r == 0.0
+
+
+def test_pagerank_residual_star_two_iterations():
+    # hand-worked: from x0 = 1/n, one update gives the centre
+    # (1-d)/n + d k/n and each leaf (1-d)/n + d/(n k); the second update uses
+    # those; the residual is the L1 norm of the second update's change
+    k, d = 5, 0.85
+    n = k + 1
+    b = (1 - d) / n
+    c1, l1 = b + d * k / n, b + d / (n * k)
+    c2, l2 = b + d * k * l1, b + d * c1 / k
+    want = abs(c2 - c1) + k * abs(l2 - l1)
+    x, r = oracle.pagerank(gg.star(k), d, 2)
+    assert x[0] == pytest.approx(c2, rel=1e-14) and np.allclose(x[1:], l2, rtol=1e-14)
+    assert r == pytest.approx(want, rel=1e-12)
+    # one update: the change from the uniform start
+    _, r1 = oracle.pagerank(gg.star(k), d, 1)
+    assert r1 == pytest.approx(abs(c1 - 1 / n) + k * abs(l1 - 1 / n), rel=1e-12)
+
+
+def test_pagerank_residual_shrinks_by_damping():
+    # the update is a contraction with factor d in L1: r_{t+1} <= d r_t
+    g = gg.rmat(8, 8, seed=2)
+    rs = [oracle.pagerank(g, 0.85, t)[1] for t in range(1, 12)]
+    assert all(b <= 0.85 * a * (1 + 1e-9) for a, b in zip(rs, rs[1:]))
+
+
 def test_pagerank_is_distribution_with_dangling():
     g = gg.rmat(12, 8, seed=4)  # has isolated vertices
     x, r = oracle.pagerank(g)
