@@ -1,16 +1,24 @@
 #!/usr/bin/env python3
 """Throughput of Slim Graph Triangle p-1-Reduction + CSR rebuild on GB300.
 
-Workload (default): R-MAT scale 22, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
-seed 1, symmetrised uint32 CSR with int64 offsets; one step = one
-compress(G, edge-once TR, p = 0.5) -> H: degree-ordered orientation, triangle
-enumeration with the edge-once reservation rounds, mask resolution and the
+Headline workload (default): R-MAT scale 26, edge factor 16,
+(a,b,c,d) = (.57,.19,.19,.05), seed 1, symmetrised uint32 CSR with int64
+offsets; one step = one compress(G, Triangle p-1-Reduction with a random edge
+per selected triangle, p = 0.5) -> H: degree-ordered orientation, triangle
+enumeration with the decisions fused in, mask resolution and the
 stream-compacted CSR rebuild.  Metric: input (undirected) edges per second.
+The headline is timed with per-launch events off; a second, shorter timed
+region with per-launch events on gives the per-kernel split and the roofline.
 
-The JSON line also carries: the roofline of the dominant kernel (measured live
-with CUDA events on the library's stream), the end-to-end number through the
-C-ABI with host buffers, the oracle timed on the host cores, SM clocks sampled
-during the timed region, and per-row timings of the other kernels.
+The JSON line also carries: the roofline of the dominant kernel (the triangle
+enumeration pass, measured with CUDA events on the library's stream) and of
+the whole step, both on the TR byte model (8(n+1) + 4m + 4 W+ for the
+enumeration, W+ = sum over oriented arcs u->v of d+(v)); the end-to-end number
+through the C-ABI with host buffers; the oracle timed on the host cores; SM
+clocks sampled during the timed region; and rows for the other kernels and
+workloads: Edge-Once TR on the same graph, the R-MAT scale-22 kernels and
+analytics, a batch of 4096 graphs against the plain per-graph loop, and a
+Poisson-arrival serving run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -29,31 +37,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOADS = {
-    "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat19": dict(scale=19, ef=16, desc="R-MAT scale 19, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat23": dict(scale=23, ef=16, desc="R-MAT scale 23, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat24": dict(scale=24, ef=16, desc="R-MAT scale 24, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-    "rmat14": dict(scale=14, ef=16, desc="R-MAT scale 14, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"),
-}
+
+def _rmat_desc(s):
+    return f"R-MAT scale {s}, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1"
+
+
+WORKLOADS = {f"rmat{s}": dict(scale=s, ef=16, desc=_rmat_desc(s)) for s in (14, 19, 20, 22, 23, 24, 26)}
 METRIC = "input edges/s compressed (TR + CSR rebuild)"
-CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 64x fewer edges than scale 22
+CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 1024x fewer edges than scale 26
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel, from one ncu capture of this benchmark's own command
-# (the summaries under profiles/ give the command).  Each entry records the
-# digest of the enumeration sources it was taken on; once they change, the
-# figure no longer describes the kernel and the JSON line reports null.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one enumeration
+# pass, from an ncu capture.  Each entry records the digest of the enumeration
+# sources it was taken on; once they change, the figure no longer describes
+# the kernel and the JSON line reports null.
 MEASURED_TRAFFIC = {
-    # (workload, kernel): (bytes per launch, sha256 of the enumeration sources)
-    # profiles/tri_enum_rmat22_tr_eo.md: 37.92 GB read + 18.83 GB written
-    ("rmat22", "tr_eo"): (56742775000, "94d004d8e9f7af0cd065222fa68884b845cbe2e00ca03967c9c33ca361122db6"),
-    # profiles/tri_enum_rmat26_tr_random.md: hub launch 1417.64 + 144.65 GB, main launch
-    # 513.55 + 12.06 GB (read + written) per union pass
-    ("rmat26", "tr_random"): (2087900042000, "94d004d8e9f7af0cd065222fa68884b845cbe2e00ca03967c9c33ca361122db6"),
+    # (workload, kernel): (bytes per pass, sha256 of the enumeration sources)
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 
@@ -174,34 +173,82 @@ def step_stats(samples):
             "ci95_mean": [float(np.percentile(means, 2.5)), float(np.percentile(means, 97.5))], "n": int(x.size)}
 
 
-def byte_model(n, m, A_out, probes_total, launches, kernel, head_arcs=0, listed_total=0):
-    """Algorithmic bytes of one launch of a named kernel."""
+# ------------------------------------------------------------ byte models
+def tr_step_bytes(n, m, A_out, fwd_probes):
+    """Algorithmic bytes of one TR compression (the method's whole step):
+    read the symmetric CSR (8n + 4A), the degree of every arc's head (4A),
+    write and read E+ (2 x (8n + 4m)), one 4-byte read per probe of the
+    forward algorithm (4 W+), the deletion flags (2m: write + read), re-read
+    the symmetric CSR for the mask (4A) and write the output CSR
+    (8n + 4A_out)."""
     A = 2 * m
-    if kernel == "tri_enum":
-        # off+ and the in-list length of every vertex (8 + 4 B), N+(x) staged in
-        # the tables (4 B/arc), the off+ pair of every streamed list (8 B/arc),
-        # the in-list records (8 B per arc streamed from the head's side), one
-        # 4-byte read per probe (W = sum over arcs of min(d+(u), d+(v))) and,
-        # for edge-once, the 16-byte record of every listed triangle
-        per = max(launches, 1)
-        return (8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs) + (4.0 * probes_total + 16.0 * listed_total) / per
-    if kernel == "tri_enum_forward":
-        # the enumeration's terms of the listing's byte model: E+ read once
-        # (off+ and N+), one 4-byte read per probe of the plain forward algorithm
-        # (W+ = sum over arcs u->v of d+(v); probes_total holds W+ scaled to the
-        # arcs the passes actually streamed) and, for edge-once, the 16-byte
-        # record of every listed triangle
-        per = max(launches, 1)
-        return (8 * (n + 1) + 4 * m) + (4.0 * probes_total + 16.0 * listed_total) / per
-    if kernel == "tri_inarcs":
-        # off+ and N+(u) of every vertex, the off+ pair and symmetric offsets of
-        # every head, one 8-byte record written per gathered arc
-        return 8 * (n + 1) + 4 * m + 8 * m + 16 * head_arcs + 8 * head_arcs
+    return ((8 * n + 4 * A) + 4 * A + 2 * (8 * n + 4 * m) + 4 * fwd_probes + 2 * m + 4 * A
+            + (8 * n + 4 * A_out))
+
+
+def enum_pass_bytes(n, m, fwd_probes):
+    """Algorithmic bytes of one enumeration pass: E+ read once (off+ and N+)
+    and one 4-byte read per probe of the forward algorithm (W+)."""
+    return 8 * (n + 1) + 4 * m + 4 * fwd_probes
+
+
+def enum_streamed_bytes(n, m, head_arcs, probes):
+    """Bytes the enumeration actually reads per pass: off+ and the in-list
+    length of every vertex (8 + 4 B), N+(x) staged in the tables (4 B/arc), the
+    off+ pair of every streamed list (8 B/arc), the in-list records (8 B per
+    arc streamed from the head's side) and one 4-byte read per probe made
+    (W = sum over arcs of min(d+(u), d+(v)))."""
+    return 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs + 4 * probes
+
+
+def byte_model(n, m, A_out, kernel):
+    """Algorithmic bytes of one launch of a streaming kernel."""
+    A = 2 * m
     if kernel == "compact_orient":
         return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * m + A / 8
     if kernel == "compact_trmask":
         return 8 * (n + 1) + 4 * A + A / 8 + 4 * m + A + 8 * (n + 1) + 4 * A_out
+    if kernel in ("compact_uniform",):
+        return 8 * (n + 1) + 4 * A + 8 * (n + 1) + 4 * A_out
+    if kernel in ("compact_spectral",):
+        return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * A_out
     return None
+
+
+KERNEL_NAMES = ("tri_enum", "tri_hubs", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve",
+                "tri_eo_list_accept", "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient",
+                "compact_trmask", "row_maps")
+
+
+def _timed(stream, fn, reps):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _kernel_row(sg, ctx, stream, G, kern, p, reps, warm=1, names=()):
+    """Time compress(G, kern, p) end of enqueue to done, plus per-kernel times."""
+    for _ in range(warm):
+        sg.compress(G, kern, p, 1).free()
+    ms = _timed(stream, lambda: sg.compress(G, kern, p, 1).free(), reps)
+    row = {"ms": ms, "edges_per_s": G.m / (ms / 1e3)}
+    if names:
+        ctx.reset_profile()
+        ctx.set_profiling(True)
+        H = sg.compress(G, kern, p, 1)
+        ctx.synchronize()
+        ctx.set_profiling(False)
+        row["kept_arcs"] = H.nnz
+        H.free()
+        row["kernel_ms"] = {k: ctx.kernel_time(k)[0] for k in names}
+    return row
 
 
 def run_ours(args, rank, world):
@@ -226,6 +273,9 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(local)
     ctx = sg.Context(local, stream=stream)
     G = sg.Graph.from_csr(ctx, g, copy=True)
+    off_h = g.off.cpu().pin_memory()
+    col_h = g.col.cpu().pin_memory()
+    del g
     torch.cuda.empty_cache()  # hand the generator's scratch back before the library sizes its lists
     ctx.set_eo_list_capacity(args.eo_list_cap)
     n, m = G.n, G.m
@@ -246,120 +296,69 @@ def run_ours(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- headline: K steps, per-launch events off
     clocks = ClockSampler(local)
     ctx.stats(reset=True)
-    ctx.reset_profile()
-    ctx.set_profiling(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_profiling(False)
     clocks.start()
     time.sleep(0.3)
     barrier()
     marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev0.record(stream)
     marks[0].record(stream)
     for i in range(args.steps):
         A_out = step()
         marks[i + 1].record(stream)
-    ev1.record(stream)
     barrier()
     clocks.stop()
-    ctx.set_profiling(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = marks[0].elapsed_time(marks[-1]) / args.steps
     step_ms = step_stats([marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)])
     st = ctx.stats()
-    kt = {}
-    for name in ("tri_enum", "tri_hubs", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve", "tri_eo_list_accept",
-                 "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient", "compact_trmask", "row_maps"):
-        kt[name] = ctx.kernel_time(name)
+    ms = max_over_ranks(ms, dist, "cuda")
+
+    # ---- per-kernel split: a second timed region with per-launch events on
+    psteps = max(1, min(args.steps, args.profile_steps))
+    ctx.stats(reset=True)
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(psteps):
+        step()
+    e1.record(stream)
+    barrier()
+    ctx.set_profiling(False)
+    prof_ms = e0.elapsed_time(e1) / psteps
+    pst = ctx.stats()
+    kt = {name: ctx.kernel_time(name) for name in KERNEL_NAMES}
+
+    hbm, peak_src = peaks()
     # one enumeration pass = the hub launch (vertices with long out-lists, when
     # there are any) + the main launch; the pass is the roofline's unit
     enum_ms = kt["tri_enum"][0] + kt["tri_hubs"][0]
-    enum_launches = max(kt["tri_enum"][1], 1)
-    ms = max_over_ranks(ms, dist, "cuda")
-
-    hbm, peak_src = peaks()
-    cand = {
-        "tri_enum": (enum_ms, enum_launches, byte_model(n, m, A_out, st["probes"], enum_launches, "tri_enum",
-                                                        work["head_arcs"], st["eo_listed"])),
-        "compact_orient": (kt["compact_orient"][0], kt["compact_orient"][1],
-                           byte_model(n, m, A_out, 0, 1, "compact_orient")),
-        "compact_trmask": (kt["compact_trmask"][0], kt["compact_trmask"][1],
-                           byte_model(n, m, A_out, 0, 1, "compact_trmask")),
-    }
-    # the listing's byte model counts the plain forward algorithm's probes W+;
-    # the passes stream the shorter list of each arc instead (W probes), so W+
-    # is scaled by the share of W they streamed (later edge-once passes skip
+    passes = max(kt["tri_enum"][1], 1)
+    # the passes stream the shorter list of each arc (W probes in all); W+ is
+    # scaled by the share of W they streamed (later edge-once passes skip
     # considered arcs)
-    fwd_total = work["forward_probes"] * st["probes"] / max(work["probes"], 1)
-    enum_fwd_bytes = byte_model(n, m, A_out, fwd_total, enum_launches, "tri_enum_forward", 0, st["eo_listed"])
-    dom = max(cand, key=lambda k: cand[k][0])
-    d_ms, d_launch, d_bytes = cand[dom]
-    per_launch_s = d_ms / max(d_launch, 1) / 1e3
-    streamed = None
-    if dom == "tri_enum":
-        streamed = {"algorithmic_bytes_per_launch": d_bytes,
-                    "achieved": d_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None}
-        d_bytes = enum_fwd_bytes
-    achieved = d_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+    fwd_total = work["forward_probes"] * pst["probes"] / max(work["probes"], 1)
+    enum_bytes = enum_pass_bytes(n, m, fwd_total / passes)
+    pass_s = enum_ms / passes / 1e3
+    enum_achieved = enum_bytes / pass_s / 1e9 if pass_s > 0 else None
+    streamed_bytes = enum_streamed_bytes(n, m, work["head_arcs"], pst["probes"] / passes)
+    streams = {}
+    for name in ("compact_orient", "compact_trmask"):
+        t, launches = kt[name]
+        if launches:
+            b = byte_model(n, m, A_out, name)
+            streams[name] = {"ms": t / launches, "algorithmic_bytes": b, "achieved": b / (t / launches) / 1e6,
+                             "frac": b / (t / launches) / 1e6 / hbm}
+    step_bytes = tr_step_bytes(n, m, A_out, work["forward_probes"])
 
-    # other rows of the hot path, timed once each (not part of the metric)
+    # ---- other rows of the hot path (not part of the metric)
     rows = {}
-    row_kernels = (("uniform", 0.5), ("spectral_avgdeg", 0.5), ("tr_random", 0.5), ("tr_p2", 0.5),
-                   ("tr_mincount", 0.5), ("tr_eo_mincount", 0.5))
-    if args.no_rows:
-        row_kernels = ()
-    for kern, p in row_kernels:
-        for _ in range(2):
-            sg.compress(G, kern, p, 1).free()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(3):
-            sg.compress(G, kern, p, 1).free()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rows[kern] = {"ms": e0.elapsed_time(e1) / 3, "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
-    if not args.no_rows:
-        # the enumeration alone (triangle counting, no decisions) for comparison
-        ctx.reset_profile()
-        ctx.set_profiling(True)
-        sg.tr_work(G)
-        ctx.set_profiling(False)
-        rows["enum_count_only"] = {"ms": ctx.kernel_time("tri_enum")[0] + ctx.kernel_time("tri_hubs")[0],
-                                   "probes": work["probes"],
-                                   "triangles": work["triangles"]}
-        H = sg.compress(G, args.kernel, args.p, 1)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        div = sg.divergence(G, H)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rows["divergence"] = {"ms": e0.elapsed_time(e1), "kl_bits": div["kl_bits"], "cc_g": div["cc_g"],
-                              "cc_h": div["cc_h"]}
-        e0.record(stream)
-        acc = sg.accuracy(G, H)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rows["accuracy"] = {"ms": e0.elapsed_time(e1), "pr_aren": acc["pr_aren"], "tc_aren": acc["tc_aren"],
-                            "critical_fraction": acc["critical_fraction"], "root": acc["root"]}
-        H.free()
-        for _ in range(2):
-            sg.low_degree(G).free()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(3):
-            L0 = sg.low_degree(G)
-            kept_n = L0.n
-            L0.free()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rows["low_degree"] = {"ms": e0.elapsed_time(e1) / 3, "kept_vertices": kept_n,
-                              "edges_per_s": m / (e0.elapsed_time(e1) / 3e3)}
-
-    # end to end through the C-ABI with pinned host buffers
-    off_h = g.off.cpu().pin_memory()
-    col_h = g.col.cpu().pin_memory()
+    if not args.no_rows and world == 1:
+        rows.update(rows_same_graph(args, sg, ctx, stream, G))
+    # ---- end to end through the C-ABI with pinned host buffers
     out_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
     out_col = torch.empty(max(2 * m, 1), dtype=torch.int32).pin_memory()
     L = sg.lib()
@@ -386,6 +385,18 @@ def run_ours(args, rank, world):
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    G.free()
+    del off_h, col_h, out_off, out_col
+    torch.cuda.empty_cache()
+
+    if not args.no_rows and world == 1:
+        rows.update(rows_rmat22(args, sg, ctx, stream))
+        ctx.release_workspace()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        rows["batch"] = batch_row(args, ctx, stream)
+        torch.cuda.empty_cache()
+        rows["serve"] = serve_row(args)
 
     cpu_leg = rank == 0 and world == 1 and not args.no_cpu
     cpu = cpu_baseline(args) if cpu_leg else None
@@ -405,7 +416,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "n": n, "m": m,
+        "config": {"workload": wl["desc"], "kernel": args.kernel, "p": args.p, "seed": 1, "n": n, "m": m,
                    "eo_list_capacity": args.eo_list_cap,
                    "arcs": 2 * m, "triangles": work["triangles"], "probes_per_pass": work["probes"],
                    "forward_probes": work["forward_probes"],
@@ -413,20 +424,28 @@ def run_ours(args, rank, world):
                    "max_out_degree": work["max_out_degree"], "kept_arcs": int(A_out),
                    "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * (n + 1) + 8 * m) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None,
-                     "traffic": measured_traffic(args.workload, args.kernel) if dom == "tri_enum" else None,
-                     "peak_source": peak_src, "algorithmic_bytes_per_launch": d_bytes,
-                     "launch_ms": d_ms / max(d_launch, 1), "launches": d_launch,
-                     "byte_model": ("forward listing: 8(n+1) + 4m + 4 W+ (+16 B per listed triangle)"
-                                    if dom == "tri_enum" else dom),
-                     "streamed": None if streamed is None else dict(
-                         streamed, frac=(streamed["achieved"] / hbm) if streamed["achieved"] else None,
-                         byte_model="probes made: 8(n+1) + 4n + 12m + 8H + 4 W (+16 B per listed triangle)")},
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
-        "eo_rounds_per_step": st["eo_rounds"] / args.steps,
-        "eo_passes_per_step": st["eo_passes"] / args.steps,
-        "eo_list_passes_per_step": st["eo_list_passes"] / args.steps,
+        "roofline": {"bound": "hbm", "kernel": "tri_enum pass (hub launch + main launch)",
+                     "achieved": enum_achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (enum_achieved / hbm) if enum_achieved else None,
+                     "traffic": measured_traffic(args.workload, args.kernel),
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": enum_bytes,
+                     "launch_ms": enum_ms / passes, "launches": passes / psteps,
+                     "byte_model": "8(n+1) + 4m + 4 W+ per enumeration pass",
+                     "launch_split_ms": {"tri_hubs": kt["tri_hubs"][0] / passes, "tri_enum": kt["tri_enum"][0] / passes},
+                     "streamed": {"algorithmic_bytes_per_launch": streamed_bytes,
+                                  "achieved": streamed_bytes / pass_s / 1e9 if pass_s > 0 else None,
+                                  "frac": streamed_bytes / pass_s / 1e9 / hbm if pass_s > 0 else None,
+                                  "byte_model": "probes made: 8(n+1) + 4n + 12m + 8H + 4 W"},
+                     "eo_list_bytes_per_step": 16 * pst["eo_listed"] / psteps},
+        "step_roofline": {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms / 1e3) / 1e9,
+                          "frac": step_bytes / (ms / 1e3) / 1e9 / hbm, "unit": "GB/s",
+                          "byte_model": "TR step: (8n+4A) + 4A + 2(8n+4m) + 4 W+ + 2m + 4A + (8n+4A')"},
+        "streaming_kernels": streams,
+        "profiled_ms_per_step": prof_ms,
+        "kernel_ms_per_step": {k: v[0] / psteps for k, v in kt.items()},
+        "eo_rounds_per_step": pst["eo_rounds"] / psteps,
+        "eo_passes_per_step": pst["eo_passes"] / psteps,
+        "eo_list_passes_per_step": pst["eo_list_passes"] / psteps,
         "gpu_launches": st["kernel_launches"],
         "clocks": clk,
         "e2e": {"value": replica_throughput(world, m, e2e_s), "unit": "edges/s",
@@ -438,10 +457,63 @@ def run_ours(args, rank, world):
     }
     if rank == 0:
         print(json.dumps(res), flush=True)
-    G.free()
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def rows_same_graph(args, sg, ctx, stream, G):
+    """Other kernels on the headline graph: Edge-Once TR (p = 0.5) and the
+    edge kernels, with kernel-only times."""
+    rows = {}
+    key = args.workload
+    if args.kernel != "tr_eo":
+        rows[f"{key}.tr_eo"] = _kernel_row(sg, ctx, stream, G, "tr_eo", 0.5, 2, 1,
+                                           names=("tri_enum", "tri_hubs", "tri_eo", "compact_trmask"))
+    for kern, name in (("uniform", "compact_uniform"), ("spectral_avgdeg", "compact_spectral")):
+        r = _kernel_row(sg, ctx, stream, G, kern, 0.5, 3, 2, names=(name, "row_maps"))
+        t = r["kernel_ms"][name]
+        b = byte_model(G.n, G.m, r["kept_arcs"], name)
+        r["kernel_roofline"] = {"kernel": name, "ms": t, "algorithmic_bytes": b, "achieved": b / t / 1e6,
+                                "frac": b / t / 1e6 / peaks()[0]}
+        rows[f"{key}.{kern}"] = r
+    return rows
+
+
+def rows_rmat22(args, sg, ctx, stream):
+    """The R-MAT scale-22 kernels and analytics (edge-once TR at three p,
+    spectral, uniform, the other TR variants, divergence, accuracy)."""
+    import torch
+
+    import graphgen as gg
+
+    rows = {}
+    g = gg.rmat(22, 16, seed=1, device="cuda")
+    torch.cuda.synchronize()
+    G = sg.Graph.from_csr(ctx, g, copy=True)
+    del g
+    torch.cuda.empty_cache()
+    for kern, p in (("tr_eo", 0.2), ("tr_eo", 0.5), ("tr_eo", 0.8), ("tr_random", 0.5), ("uniform", 0.5),
+                    ("spectral_avgdeg", 0.5), ("spectral_logn", 0.5), ("tr_p2", 0.5), ("tr_mincount", 0.5),
+                    ("tr_eo_mincount", 0.5)):
+        rows[f"rmat22.{kern}.p{p}"] = _kernel_row(sg, ctx, stream, G, kern, p, 3, 2)
+    H = sg.compress(G, "tr_eo", 0.5, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    div = sg.divergence(G, H)
+    ms = (time.perf_counter() - t0) * 1e3
+    rows["rmat22.divergence"] = {"ms": ms, "kl_bits": div["kl_bits"], "cc_g": div["cc_g"], "cc_h": div["cc_h"],
+                                 "pr_residual_g": div["pr_residual_g"], "pr_residual_h": div["pr_residual_h"]}
+    t0 = time.perf_counter()
+    acc = sg.accuracy(G, H)
+    rows["rmat22.accuracy"] = {"ms": (time.perf_counter() - t0) * 1e3, "pr_aren": acc["pr_aren"],
+                               "tc_aren": acc["tc_aren"], "critical_fraction": acc["critical_fraction"]}
+    H.free()
+    for _ in range(2):
+        sg.low_degree(G).free()
+    rows["rmat22.low_degree"] = {"ms": _timed(stream, lambda: sg.low_degree(G).free(), 3)}
+    G.free()
+    return rows
 
 
 def _digest(graphs, sync_stream):
@@ -459,99 +531,97 @@ def _digest(graphs, sync_stream):
     return int(acc.item())
 
 
-def run_batch(args):
-    """Batched compression of many R-MAT graphs vs the plain one-call-per-graph loop."""
+def batch_row(args, ctx, stream):
+    """Batched compression of many R-MAT graphs (one captured CUDA-graph replay)
+    against the plain loop of one compress call per graph, at identical outputs."""
     import numpy as np
     import torch
 
     import graphgen as gg
     import paper_1912_08950_gb300 as sg
 
-    torch.cuda.set_device(0)
-    G = args.batch_graphs
+    count = args.batch_graphs
     rng = np.random.default_rng(7)
-    scales = [int(round(8 + 8 * u)) for u in rng.random(G)]
-    efs = [int(e) for e in rng.integers(8, 33, size=G)]
-    seeds = [i + 1 for i in range(G)]
-    ps = [float(x) for x in rng.choice([0.2, 0.5, 0.8], size=G)]
-    kernels = [("uniform", "spectral_avgdeg", "tr_random")[i % 3] for i in range(G)]
+    scales = [int(round(8 + 8 * u)) for u in rng.random(count)]
+    efs = [int(e) for e in rng.integers(8, 33, size=count)]
+    seeds = [i + 1 for i in range(count)]
+    ps = [float(x) for x in rng.choice([0.2, 0.5, 0.8], size=count)]
+    kernels = [("uniform", "spectral_avgdeg", "tr_random")[i % 3] for i in range(count)]
     t0 = time.perf_counter()
     u, vbase, _ = gg.rmat_batch(scales, efs, seeds, device="cuda")
     gen_s = time.perf_counter() - t0
-    stream = torch.cuda.Stream()
-    ctx = sg.Context(0, stream=stream)
-    graphs = [sg.Graph.from_csr(ctx, gg.batch_member(u, vbase, i, 1 << scales[i]), copy=True) for i in range(G)]
+    graphs = [sg.Graph.from_csr(ctx, gg.batch_member(u, vbase, i, 1 << scales[i]), copy=True) for i in range(count)]
     del u
+    torch.cuda.empty_cache()
     m_total = sum(g.m for g in graphs)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    reps = max(1, min(args.steps, args.batch_steps))
 
     def plain():
-        return [sg.compress(graphs[i], kernels[i], ps[i], seeds[i]) for i in range(G)]
+        return [sg.compress(graphs[i], kernels[i], ps[i], seeds[i]) for i in range(count)]
 
-    for _ in range(max(1, args.warmup // 2)):
-        for h in plain():
-            h.free()
-    torch.cuda.synchronize()
+    for h in plain():
+        h.free()
     ctx.stats(reset=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
     ev[0].record(stream)
-    reps = max(1, args.steps // 2)
-    for _ in range(reps):
+    for r in range(reps):
         outs = plain()
-        if _ < reps - 1:
+        if r < reps - 1:
             for h in outs:
                 h.free()
     ev[1].record(stream)
     torch.cuda.synchronize()
     plain_ms = ev[0].elapsed_time(ev[1]) / reps
     plain_launches = ctx.stats(reset=True)["kernel_launches"] / reps
-    d_plain = _digest(outs, stream)
+    d_plain = _digest(outs, stream)  # one compress call per graph: the solo outputs
     for h in outs:
         h.free()
     B = sg.Batch(ctx, graphs)
     t0 = time.perf_counter()
-    outs_b = B.compress(kernels, ps, seeds)  # first call: autotune + capture
+    B.compress(kernels, ps, seeds)  # first call: autotune + capture
     tune_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
-        outs_b = B.compress(kernels, ps, seeds)
+    B.compress(kernels, ps, seeds)
     torch.cuda.synchronize()
     ctx.stats(reset=True)
     ev[2].record(stream)
-    for _ in range(args.steps):
+    for _ in range(reps):
         outs_b = B.compress(kernels, ps, seeds)
     ev[3].record(stream)
     torch.cuda.synchronize()
-    batch_ms = ev[2].elapsed_time(ev[3]) / args.steps
-    batch_launches = ctx.stats(reset=True)["kernel_launches"] / args.steps
+    batch_ms = ev[2].elapsed_time(ev[3]) / reps
+    batch_launches = ctx.stats(reset=True)["kernel_launches"] / reps
     d_batch = _digest(outs_b, stream)
     info = B.info()
-    print(json.dumps({
-        "mode": "batch", "metric": METRIC + ", batched vs plain", "unit": "edges/s",
-        "value": m_total / (batch_ms / 1e3), "plain_value": m_total / (plain_ms / 1e3),
-        "speedup": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
-        "identical_outputs": d_plain == d_batch, "graphs": G, "m_total": m_total,
-        "gpu_launches_per_call": {"batch": batch_launches, "plain": plain_launches},
-        "autotune": info, "autotune_s": tune_s, "generation_s": gen_s, "steps": args.steps,
-        "config": {"workload": f"{G} R-MAT graphs, scale round(8+8u) u~U[0,1), ef~U{{8..32}}, seed i+1, "
-                               "p~U{0.2,0.5,0.8}, kernel round-robin uniform/spectral_avgdeg/tr_random"},
-    }), flush=True)
     B.free()
-    ctx.close()
+    for g in graphs:
+        g.free()
+    return {"metric": METRIC + ", batched vs plain", "unit": "edges/s",
+            "value": m_total / (batch_ms / 1e3), "plain_value": m_total / (plain_ms / 1e3),
+            "speedup": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms, "reps": reps,
+            "identical_outputs": d_plain == d_batch, "graphs": count, "m_total": m_total,
+            "gpu_launches_per_call": {"batch": batch_launches, "plain": plain_launches},
+            "autotune": info, "autotune_s": tune_s, "generation_s": gen_s,
+            "workload": f"{count} R-MAT graphs, scale round(8+8u) u~U[0,1), ef~U{{8..32}}, seed i+1, "
+                        "p~U{0.2,0.5,0.8}, kernel round-robin uniform/spectral_avgdeg/tr_random"}
 
 
-def run_serve(args):
-    """Continuous-batching serving of compress + divergence jobs with Poisson arrivals."""
+def serve_row(args):
+    """Continuous-batching serving of compress + divergence jobs with Poisson
+    arrivals: at the offered rate, then at 70% of the capacity that run showed."""
     import numpy as np
     import torch
 
     import graphgen as gg
     from paper_1912_08950_gb300.serve import GpuExecutor, Job, Server, poisson_arrivals, replay
 
-    rng = np.random.default_rng(5)
     pool = {}
     for s in range(args.serve_min_scale, args.serve_max_scale + 1):
         g = gg.rmat(s, 16, seed=s, device="cuda")
         off, col, _ = g.numpy()
         pool[s] = (g.n, np.ascontiguousarray(off), np.ascontiguousarray(col))
+    del g
+    torch.cuda.empty_cache()
     kern = ["uniform", "spectral_avgdeg", "tr_random", "tr_eo"]
 
     def make_jobs(count, seed):
@@ -564,29 +634,25 @@ def run_serve(args):
                             p=float(r.choice([0.2, 0.5, 0.8])), seed=i + 1))
         return jobs
 
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(free * 0.6)
-    slots = args.serve_slots
     res = {}
     for label, rate in (("offered", args.serve_rate), ("capacity70", None)):
         if rate is None:
             rate = 0.7 * res["offered"]["jobs_per_s"]
-        srv = Server(lambda i: GpuExecutor(0), slots=slots, memory_budget=budget)
+        srv = Server(lambda i: GpuExecutor(0), slots=args.serve_slots)
         jobs = make_jobs(args.serve_jobs, 11)
         out = replay(srv, jobs, poisson_arrivals(rate, len(jobs), seed=3))
         srv.close()
         out.pop("results")
         out["rate"] = rate
         res[label] = out
-    print(json.dumps({"mode": "serve", "slots": slots, "memory_budget": budget, **res,
-                      "config": {"workload": f"Poisson arrivals; jobs = compress + KL/CC on R-MAT scale "
-                                             f"U{{{args.serve_min_scale}..{args.serve_max_scale}}} ef 16; "
-                                             "kernels uniform/spectral_avgdeg/tr_random/tr_eo, p~U{0.2,0.5,0.8}"}}),
-          flush=True)
+    return {"slots": args.serve_slots, **res,
+            "workload": f"Poisson arrivals; jobs = compress + KL/CC on R-MAT scale "
+                        f"U{{{args.serve_min_scale}..{args.serve_max_scale}}} ef 16; "
+                        "kernels uniform/spectral_avgdeg/tr_random/tr_eo, p~U{0.2,0.5,0.8}; admitted by free HBM"}
 
 
 def _oracle_sample(kernel, p):
-    """One bounded oracle run: the same generator at scale 16 (a 64x smaller sample)."""
+    """One bounded oracle run: the same generator at scale 16."""
     import graphgen as gg
     import oracle
 
@@ -669,25 +735,22 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22")
-    ap.add_argument("--kernel", default="tr_eo")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat26")
+    ap.add_argument("--kernel", default="tr_random")
     ap.add_argument("--p", type=float, default=0.5)
+    ap.add_argument("--profile-steps", type=int, default=3, help="steps of the per-kernel timing region")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--no-rows", action="store_true", help="skip the extra per-kernel rows and analytics")
+    ap.add_argument("--no-rows", action="store_true", help="skip the extra rows (other kernels, batch, serve)")
     ap.add_argument("--eo-list-cap", type=int, default=0,
                     help="edge-once triangle list capacity in records (0: automatic, -1: none)")
-    ap.add_argument("--mode", choices=["compress", "batch", "serve"], default="compress")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-jobs", type=int, default=300)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-min-scale", type=int, default=10)
     ap.add_argument("--serve-max-scale", type=int, default=22)
     args = ap.parse_args()
-    if args.mode == "batch":
-        return run_batch(args)
-    if args.mode == "serve":
-        return run_serve(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", 0))

@@ -14,12 +14,26 @@ def test_step_stats():
 
 def test_enumeration_byte_models():
     n, m = 1000, 8000
-    # the listing's model: E+ once, 4 B per forward probe, 16 B per listed triangle
-    assert bench.byte_model(n, m, 0, 10_000, 1, "tri_enum_forward", 0, 0) == 8 * (n + 1) + 4 * m + 40_000
-    assert bench.byte_model(n, m, 0, 20_000, 2, "tri_enum_forward", 0, 100) == 8 * (n + 1) + 4 * m + 40_000 + 800
+    # the enumeration pass: E+ once, 4 B per probe of the forward algorithm
+    assert bench.enum_pass_bytes(n, m, 10_000) == 8 * (n + 1) + 4 * m + 40_000
     # the probes-made model adds the in-list lengths, staged bounds and in-list records
-    got = bench.byte_model(n, m, 0, 10_000, 1, "tri_enum", 500, 0)
-    assert got == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * 500 + 40_000
+    assert bench.enum_streamed_bytes(n, m, 500, 10_000) == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * 500 + 40_000
+
+
+def test_tr_step_byte_model():
+    n, m, a_out, wf = 1000, 8000, 9000, 50_000
+    A = 2 * m
+    # read CSR, head degrees, write + read E+, forward probes, del flags, mask re-read, output
+    want = (8 * n + 4 * A) + 4 * A + 2 * (8 * n + 4 * m) + 4 * wf + 2 * m + 4 * A + (8 * n + 4 * a_out)
+    assert bench.tr_step_bytes(n, m, a_out, wf) == want
+
+
+def test_streaming_byte_models():
+    n, m, a_out = 1000, 8000, 9000
+    A = 2 * m
+    assert bench.byte_model(n, m, a_out, "compact_uniform") == 16 * (n + 1) + 4 * A + 4 * a_out
+    assert bench.byte_model(n, m, a_out, "compact_spectral") == 16 * (n + 1) + 8 * A + 4 * a_out
+    assert bench.byte_model(n, m, a_out, "nothing") is None
 
 
 def test_measured_traffic_guarded_by_source_digest(monkeypatch):
