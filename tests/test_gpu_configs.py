@@ -4,17 +4,25 @@ under max-weight TR at p = 1, and a 3-D random geometric graph with 2^24
 points (mean degree 48, triangle-dense) under the TR kernels.
 
 At these sizes the oracle answers sampled edges one by one (the union kernels'
-deletion of an edge depends only on the triangles through it).  The MST weight
-is checked through the cycle property: every deleted edge must be the heaviest
-edge, under (weight, lo, hi), of a triangle of G -- such an edge is in no
-minimum spanning forest, so removing it leaves the MST weight unchanged.
+deletion of an edge depends only on the triangles through it).  For the
+Chung-Lu graph the oracle's Kruskal MST weight and component count of H are
+compared exactly with the values it computed for G (stored by
+tests/golden/make_golden.py chung_lu26_mst): max-weight TR keeps both
+(Sec. 6, Others).  The cycle property is also checked on sampled deleted
+edges: each must be the heaviest edge, under (weight, lo, hi), of a triangle
+of G.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
 
 import graphgen as gg
 import oracle
+from tests.digest import csr_digest, read_golden
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 pytestmark = pytest.mark.gpu
 
@@ -88,10 +96,15 @@ def test_chung_lu_26_maxw(sg, ctx):
     del g
     torch.cuda.empty_cache()
     n, off, col, w = host
+    gold = read_golden(os.path.join(GOLDEN, "chung_lu26_mst.txt"))
+    assert gold["graph"] == [str(n), str(col.size), csr_digest(off, col, w)], "generator output changed"
     H, hoff, hcol, hw = _union_parity(sg, G, host, "tr_maxw", 1.0, 3, 2000)
-    # H is a subgraph with the same components
+    # H is a subgraph with G's components and G's MST weight, both from the oracle
     assert np.all(np.diff(hoff) <= np.diff(off))
-    assert sg.cc_count(H) == sg.cc_count(G)
+    h_host = (n, hoff, hcol, hw)
+    assert oracle.cc_count(h_host) == int(gold["cc"][0])
+    assert oracle.mst_weight_units(h_host) == int(gold["mst_units"][0])
+    assert sg.cc_count(H) == int(gold["cc"][0]) and sg.cc_count(G) == int(gold["cc"][0])
     # sampled deleted edges are triangle maxima (cycle property => MST weight kept)
     rows, cols = _sample_arcs(off, col, 20000, 23)
     checked = 0
@@ -117,10 +130,13 @@ def test_rgg_24_tr_kernels(sg, ctx):
     n, off, col, w = host
     deg = np.diff(off)
     assert 40 < deg.mean() < 56
+    cc_g = oracle.cc_count(host)
+    assert sg.cc_count(G) == cc_g
     for kernel, p in (("tr_maxw", 1.0), ("tr_random", 0.5)):
         H, hoff, hcol, _ = _union_parity(sg, G, host, kernel, p, 5, 1500)
         if kernel == "tr_maxw":
-            assert sg.cc_count(H) == sg.cc_count(G)
+            # components kept (Sec. 6): the oracle counts them in H
+            assert oracle.cc_count((n, hoff, hcol, None)) == cc_g
         H.free()
     # edge-once: invariants that hold at any size
     H = sg.compress(G, "tr_eo", 0.5, 5)
@@ -128,7 +144,7 @@ def test_rgg_24_tr_kernels(sg, ctx):
     dh = np.diff(hoff)
     assert np.all(deg - dh <= deg // 2)
     assert (off[-1] - hoff[-1]) // 2 <= (off[-1] // 2) / 3
-    assert sg.cc_count(H) == sg.cc_count(G)
+    assert oracle.cc_count((n, hoff, hcol, None)) == cc_g
     rows, cols = _sample_arcs(off, col, 5000, 29)
     for x, y in zip(rows, cols):
         x, y = int(x), int(y)

@@ -82,7 +82,8 @@ def test_tr_eo_invariants_full_size(sg, big, kern, p):
     dg, dh = np.diff(goff), np.diff(off)
     assert np.all(dh <= dg) and np.all(dg - dh <= dg // 2)
     assert (g.nnz - col.size) // 2 <= g.m / 3
-    assert sg.cc_count(H) == sg.cc_count(G) == oracle.cc_count(g)
+    cc = oracle.cc_count(g)
+    assert oracle.cc_count((g.n, off, col, None)) == cc and sg.cc_count(H) == sg.cc_count(G) == cc
     # sampled deleted edges keep a 2-path in H
     rows, cols = _edge_sample(g, 20000, 7)
     checked = 0
