@@ -74,6 +74,7 @@ _SIGS = {
     "sg_ctx_set_eo_list_capacity": [_vp, _i64],
     "sg_ctx_release_workspace": [_vp],
     "sg_device_free_memory": [_int, C.POINTER(C.c_uint64)],
+    "sg_ctx_set_scan_hold": [_vp, C.c_uint32],
     "sg_kernel_arch": [_int, C.POINTER(C.c_int)],
     "sg_graph_from_device": [_vp, C.POINTER(CsrView), _int, _int, _PP],
     "sg_graph_from_host": [_vp, _i64, _i64, _vp, _vp, _vp, _PP],
@@ -186,6 +187,10 @@ class Context:
     def set_eo_list_capacity(self, records: int):
         """0: automatic, -1: no triangle list, > 0: at most that many triangles."""
         _check(_lib.sg_ctx_set_eo_list_capacity(self.handle, int(records)))
+
+    def set_scan_hold(self, spin_limit: int):
+        """Test hook: make every prefix scan's first wait run out (0: off)."""
+        _check(_lib.sg_ctx_set_scan_hold(self.handle, int(spin_limit)))
 
     def release_workspace(self):
         """Free the edge-once list workspaces the context keeps between calls."""

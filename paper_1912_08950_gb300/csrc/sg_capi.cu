@@ -288,6 +288,12 @@ sg_status sg_ctx_release_workspace(sg_ctx *ctx) {
     return SG_OK;
 }
 
+sg_status sg_ctx_set_scan_hold(sg_ctx *ctx, uint32_t spin_limit) {
+    if (!ctx) return fail(SG_ERR_INVALID_ARG, "ctx is NULL");
+    C_(ctx)->scan_hold = spin_limit;
+    return SG_OK;
+}
+
 sg_status sg_device_free_memory(int device, uint64_t *free_out) {
     if (!free_out) return fail(SG_ERR_INVALID_ARG, "free_out is NULL");
     int ndev = 0, prev = 0;

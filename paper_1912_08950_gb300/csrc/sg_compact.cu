@@ -108,6 +108,8 @@ struct CompactArgs {
     unsigned int *ticket;
     int *err;
     uint32_t *keep_bits;  // optional: the keep mask of every 32-arc slab
+    uint32_t spin_limit;  // polls of a look-back wait before it gives up
+    int hold_first;       // test hook: tile 0 never publishes its prefix
 };
 
 struct SlabCtx {
@@ -146,11 +148,14 @@ __device__ __forceinline__ int64_t warp_row(const int64_t *__restrict__ off, int
 
 // Decoupled look-back by one warp: publish this tile's aggregate, sum the
 // predecessors' values back to the first inclusive prefix, publish our own
-// inclusive prefix, return the exclusive one.  Polls are bounded.
-__device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64_t agg, int *err) {
+// inclusive prefix, return the exclusive one.  Polls are bounded by `limit`.
+// hold_first (a test hook) keeps tile 0 from publishing, so that the wait of
+// the tile after it runs out and the error path can be exercised.
+__device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64_t agg, int *err,
+                                 uint32_t limit = kSpinLimit, bool hold_first = false) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        if (lane == 0) st_volatile_u64(status, kStInc | (unsigned long long)agg);
+        if (lane == 0 && !hold_first) st_volatile_u64(status, kStInc | (unsigned long long)agg);
         return 0;
     }
     if (lane == 0) st_volatile_u64(status + tile, kStAgg | (unsigned long long)agg);
@@ -163,10 +168,10 @@ __device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64
         const unsigned flag = (unsigned)(s >> 62);
         if (__any_sync(kFull, flag == 0)) {
             ++spins;
-            // give up after kSpinLimit polls, or at once if another tile already
+            // give up after `limit` polls, or at once if another tile already
             // gave up; publish a (meaningless) inclusive value so that no
             // successor waits on this tile either
-            bool quit = spins > kSpinLimit;
+            bool quit = spins > limit;
             if ((spins & 1023u) == 0) quit = quit || (*(volatile int *)err != 0);
             if (__any_sync(kFull, quit)) {
                 if (lane == 0) {
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
                 s_warp_excl[CW] = agg;
             }
             agg = __shfl_sync(kFull, agg, 0);
-            const int64_t excl = tile_lookback(a.status, tile, agg, a.err);
+            const int64_t excl = tile_lookback(a.status, tile, agg, a.err, a.spin_limit, a.hold_first != 0);
             if (lane == 0) s_tile_excl = excl;
         }
         __syncthreads();
@@ -426,6 +431,8 @@ static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Po
     a.ticket = reinterpret_cast<unsigned int *>(status + rm.num_tiles);
     a.err = c->d_err;
     a.keep_bits = keep_bits;
+    a.spin_limit = c->scan_hold ? c->scan_hold : kSpinLimit;
+    a.hold_first = c->scan_hold != 0;
     const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, blocks_per_sm<Pol>()) : blocks_per_sm<Pol>();
     const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * per_sm);
     {
@@ -908,6 +915,8 @@ sg_status noalloc_uniform(int device, void *cuda_stream, int64_t n, int64_t nnz,
     a.ticket = reinterpret_cast<unsigned int *>(status + num_tiles);
     a.err = err;
     a.keep_bits = nullptr;
+    a.spin_limit = kSpinLimit;
+    a.hold_first = 0;
     UniformPol pol{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), prob_threshold(p)};
     int per_sm = 0;
     SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<UniformPol>, CW * 32, 0));

@@ -49,6 +49,7 @@ struct Ctx {
     uint64_t eo_list_passes = 0;           // ... that listed triangles
     int64_t eo_list_cap = 0;               // 0 auto, -1 off, > 0 records
     bool profiling = false;
+    uint32_t scan_hold = 0;                // test hook (sg_ctx_set_scan_hold): 0 off
     // grow-only device workspaces kept across calls (edge-once list and active
     // lists), so that repeated calls do not churn the stream-ordered pool
     void *ws[3] = {nullptr, nullptr, nullptr};
