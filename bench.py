@@ -207,7 +207,13 @@ def byte_model(n, m, A_out, kernel):
     if kernel == "compact_orient":
         return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * m + A / 8
     if kernel == "compact_trmask":
-        return 8 * (n + 1) + 4 * A + A / 8 + 4 * m + A + 8 * (n + 1) + 4 * A_out
+        # offsets and columns, forward bits, the deletion flag of every forward
+        # arc, the resolved bits of the reverse arcs, the output CSR
+        return 8 * (n + 1) + 4 * A + A / 8 + m + A / 8 + 8 * (n + 1) + 4 * A_out
+    if kernel == "compact_revkeep":
+        # offsets and columns, forward bits; per reverse arc the E+ row bounds
+        # of its tail (16 B), the found column (4 B) and its deletion flag; the bits out
+        return 8 * (n + 1) + 4 * A + A / 8 + 21 * m + A / 8
     if kernel in ("compact_uniform",):
         return 8 * (n + 1) + 4 * A + 8 * (n + 1) + 4 * A_out
     if kernel in ("compact_spectral",):
@@ -217,7 +223,7 @@ def byte_model(n, m, A_out, kernel):
 
 KERNEL_NAMES = ("tri_enum", "tri_hubs", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve",
                 "tri_eo_list_accept", "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient",
-                "compact_trmask", "row_maps")
+                "compact_revkeep", "compact_trmask", "row_maps")
 
 
 def _timed(stream, fn, reps):
@@ -346,7 +352,7 @@ def run_ours(args, rank, world):
     enum_achieved = enum_bytes / pass_s / 1e9 if pass_s > 0 else None
     streamed_bytes = enum_streamed_bytes(n, m, work["head_arcs"], pst["probes"] / passes)
     streams = {}
-    for name in ("compact_orient", "compact_trmask"):
+    for name in ("compact_orient", "compact_revkeep", "compact_trmask"):
         t, launches = kt[name]
         if launches:
             b = byte_model(n, m, A_out, name)

@@ -367,30 +367,166 @@ struct MaskPol {
     static constexpr bool kMapCol = false;
     const uint32_t *fwd_bits;
     const unsigned long long *or_status;
-    const int64_t *offp;
-    const uint32_t *colp;
+    const uint32_t *rev_keep;  // keep bits of the reverse arcs (rev_keep_kernel)
     const uint8_t *del;
-    int *err;
     __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const {
         return tile == 0 ? 0 : (int64_t)(ld_volatile_u64(or_status + tile - 1) & kStVal);
     }
-    // the arc stays iff its edge's oriented arc carries no deletion flag
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t p, const SlabCtx &s, float &) const {
+    // the arc stays iff its edge's oriented arc carries no deletion flag: a
+    // forward arc finds its E+ index by the running prefix of forward arcs, a
+    // reverse arc reads the bit rev_keep_kernel resolved for it
+    __device__ __forceinline__ bool keep(int64_t, uint32_t, int64_t p, const SlabCtx &s, float &) const {
         const int lane = (int)(p & 31);
-        int64_t idx;
-        if ((s.or_word >> lane) & 1u) {
-            idx = s.or_base + __popc(s.or_word & lanemask_lt());
-        } else {
-            const int64_t end = __ldg(offp + y + 1);
-            idx = lower_bound_u32(colp, __ldg(offp + y), end, (uint32_t)x);
-            if (idx >= end || __ldg(colp + idx) != (uint32_t)x) {  // no reverse arc: not a symmetric CSR
-                atomicExch(err, (int)kDevBadGraph);
-                return true;
-            }
-        }
-        return __ldg(del + idx) == 0;
+        if ((s.or_word >> lane) & 1u) return __ldg(del + s.or_base + __popc(s.or_word & lanemask_lt())) == 0;
+        return (__ldg(rev_keep + (p >> 5)) >> lane) & 1u;
     }
 };
+
+// Keep bits of the reverse arcs.  A reverse arc (x, y) of the symmetric CSR --
+// y before x in the degree order -- is the E+ arc y->x, at the position of x
+// in the sorted row N+(y); it stays iff that arc carries no deletion flag.
+// Finding x is a chain of dependent loads, so every lane carries kRevK
+// searches (one per 32-arc slab of its warp's span) and advances them in
+// lockstep: their loads are independent and overlap.  Each search is a lower
+// bound (x lies in [base, base + len]) that narrows its window until it holds
+// at most kRevWin candidates, which are then loaded together and compared.
+// Vertex ids carry no order of their own, so a row's ids are spread over
+// [0, n): the first kRevInterp probes interpolate x's position from its value
+// and bisection takes over after them (a skewed row still costs O(log)
+// probes).  On rows of uniformly spread ids of length 500 / 3000 that reads
+// about 1.9 / 2.4 distinct 32-byte sectors per lookup instead of 6 / 8.5, and
+// those random sectors are the kernel's bound.
+// One 32-bit word per slab holds the bits of its reverse arcs.
+constexpr int kRevK = 4;
+constexpr int kRevWin = 4;
+constexpr int kRevInterp = 6;
+
+__global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restrict__ off, int64_t n, int64_t nnz,
+                                                       const uint32_t *__restrict__ col,
+                                                       const uint32_t *__restrict__ chunk_row,
+                                                       const uint32_t *__restrict__ fwd_bits,
+                                                       const int64_t *__restrict__ offp,
+                                                       const uint32_t *__restrict__ colp,
+                                                       const uint8_t *__restrict__ del, uint32_t *rev_keep, int *err,
+                                                       BatchDev batch) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nslabs = (nnz + 31) >> 5;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s0 = wid * kRevK; s0 < nslabs; s0 += nw * kRevK) {
+        int64_t base[kRevK];
+        int len[kRevK];
+        uint32_t xs[kRevK], vlo[kRevK], vhi[kRevK];
+        bool need[kRevK];
+        int64_t cursor = (int64_t)__ldg(chunk_row + ((s0 << 5) / kWarpSpan));
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
+            const int64_t sbase = (s0 + k) << 5;
+            need[k] = false;
+            base[k] = 0;
+            len[k] = 0;
+            xs[k] = 0;
+            vlo[k] = 0;
+            vhi[k] = (uint32_t)n;
+            if (sbase < nnz) {  // warp-uniform
+                const bool valid = sbase + lane < nnz;
+                const int q = valid ? lane : (int)(nnz - 1 - sbase);
+                const int64_t x = warp_row(off, n, cursor, sbase, q);
+                const uint32_t fw = __ldg(fwd_bits + (sbase >> 5));
+                // in a batch, graphs without a triangle kernel have no E+ arcs to look up
+                const bool tri = batch.params == nullptr ||
+                                 __ldg(&batch.params[__ldg(batch.vgid + x)].kernel) >= (int)SG_TR_RANDOM;
+                if (valid && tri && !((fw >> lane) & 1u)) {
+                    const uint32_t y = __ldg(col + sbase + q);
+                    base[k] = __ldg(offp + y);
+                    len[k] = (int)(__ldg(offp + y + 1) - base[k]);
+                    xs[k] = (uint32_t)x;
+                    need[k] = true;
+                }
+            }
+        }
+        // lockstep narrowing until every window [base, base + len] holds at
+        // most kRevWin candidates
+        for (int it = 0;; ++it) {
+            bool any = false;
+            uint32_t v[kRevK];
+            int h[kRevK];
+#pragma unroll
+            for (int k = 0; k < kRevK; ++k) {
+                if (it < kRevInterp) {  // interpolate from the value bracket [vlo, vhi]
+                    const float f = __fdividef((float)(xs[k] - vlo[k]), (float)(vhi[k] - vlo[k]) + 1.0f);
+                    h[k] = min(max((int)(f * (float)len[k]), 0), len[k] - 1);
+                } else {
+                    h[k] = len[k] >> 1;
+                }
+                v[k] = len[k] >= kRevWin ? __ldg(colp + base[k] + h[k]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kRevK; ++k) {
+                if (len[k] >= kRevWin) {
+                    any = true;
+                    if (v[k] < xs[k]) {
+                        base[k] += h[k] + 1;
+                        len[k] -= h[k] + 1;
+                        vlo[k] = v[k] + 1;
+                    } else {
+                        len[k] = h[k];
+                        vhi[k] = v[k];
+                    }
+                }
+            }
+            if (!any) break;
+        }
+        // the windows, loaded together (base + len may be one past the row, but
+        // stays inside the E+ column array, which has room for nnz >= m + 1
+        // entries; the first match is x's own position); then the deletion
+        // flags, loaded together
+        int64_t idx[kRevK];
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
+            uint32_t w[kRevWin];
+#pragma unroll
+            for (int j = 0; j < kRevWin; ++j) w[j] = (need[k] && j <= len[k]) ? __ldg(colp + base[k] + j) : kFull;
+            idx[k] = -1;
+#pragma unroll
+            for (int j = kRevWin - 1; j >= 0; --j)
+                if (need[k] && j <= len[k] && w[j] == xs[k]) idx[k] = base[k] + j;
+        }
+        uint8_t d[kRevK];
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) d[k] = (need[k] && idx[k] >= 0) ? __ldg(del + idx[k]) : (uint8_t)1;
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
+            const int64_t sbase = (s0 + k) << 5;
+            if (sbase < nnz) {  // warp-uniform
+                if (need[k] && idx[k] < 0) atomicExch(err, (int)kDevBadGraph);  // no reverse arc: not symmetric
+                const unsigned bits = __ballot_sync(kFull, need[k] && d[k] == 0);
+                if (lane == 0) rev_keep[sbase >> 5] = bits;
+            }
+        }
+    }
+}
+
+static sg_status launch_rev_keep(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
+                                 uint32_t *rev_keep, BatchDev batch = BatchDev{nullptr, nullptr}) {
+    if (g->nnz == 0) return SG_OK;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rev_keep_kernel, 256, 0) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    const int64_t warps = ((g->nnz + 31) / 32 + kRevK - 1) / kRevK;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)c->num_sms * per_sm));
+    {
+        SG_LAUNCH(c, "compact_revkeep");
+        rev_keep_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(g->off, g->n, g->nnz, g->col, rm.chunk_row,
+                                                             o.fwd_bits, o.off, o.col, del, rev_keep, c->d_err,
+                                                             batch);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
 
 // ------------------------------------------------------------------ driver
 template <class Pol>
@@ -552,14 +688,18 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
                        Graph **out) {
     Graph *h = nullptr;
     unsigned long long *status = nullptr;
+    uint32_t *rev_keep = nullptr;
     sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
     if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&rev_keep, sizeof(uint32_t) * (size_t)((g->nnz + 31) / 32 + 1));
+    if (st == SG_OK) st = launch_rev_keep(c, g, rm, o, del, rev_keep);
     if (st == SG_OK) {
-        MaskPol pol{o.fwd_bits, o.status, o.off, o.col, del, c->d_err};
+        MaskPol pol{o.fwd_bits, o.status, rev_keep, del};
         st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_trmask");
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
+    dfree(c, rev_keep);
     dfree(c, status);
     if (st != SG_OK) {
         delete_graph(c, h);
@@ -623,8 +763,12 @@ sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev
 
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      unsigned long long *status, int grid_per_sm) {
-    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, o.off, o.col, del, c->d_err}, o.fwd_bits};
+                      unsigned long long *status, uint32_t *rev_keep, int grid_per_sm) {
+    // the reverse arcs of graphs without a triangle kernel are not looked up
+    // (BatchFinalPol decides those arcs itself)
+    sg_status st = launch_rev_keep(c, u, rm, o, del, rev_keep, b);
+    if (st != SG_OK) return st;
+    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, rev_keep, del}, o.fwd_bits};
     return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, nullptr, status, "compact_final",
                        grid_per_sm);
 }

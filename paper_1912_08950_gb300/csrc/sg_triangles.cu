@@ -365,10 +365,7 @@ __device__ __noinline__ void drain32_call(const TriArgs &a, const HitQueue &q, i
 template <Mode M>
 __device__ __forceinline__ void drain32(const TriArgs &a, const HitQueue &q, int head, uint32_t u, unsigned &live,
                                         Emitter &em) {
-    if constexpr (M == Mode::EoEmit)
-        drain32_body<M>(a, q, head, u, live, em);
-    else
-        drain32_call<M>(a, q, head, u, live, em);
+    drain32_body<M>(a, q, head, u, live, em);
 }
 
 // Decide everything queued for the table vertex u (the last group with idle lanes).

@@ -124,3 +124,36 @@ def test_batch_edge_kernel_graphs_before_triangle_graphs(sg, ctx):
         o_off, o_col, _ = oracle.compress(graphs[i], kernels[::-1][i], ps[::-1][i], seeds[::-1][i])
         assert np.array_equal(off, o_off) and np.array_equal(col, o_col)
     B.free()
+
+
+def test_batch_at_benchmark_scale_range(sg, ctx):
+    """Three hundred R-MAT graphs drawn like the 4096-graph benchmark batch
+    (scale round(8 + 8u), edge factor 8..32, per-graph seed and p, kernels
+    uniform / spectral / union TR round-robin): every output equals its solo
+    run, every 10th the oracle's (union TR only up to scale 14, to keep the
+    oracle's time bounded)."""
+    count = 300
+    rng = np.random.default_rng(11)
+    scales = [int(round(8 + 8 * x)) for x in rng.random(count)]
+    efs = [int(e) for e in rng.integers(8, 33, size=count)]
+    seeds = [i + 1 for i in range(count)]
+    ps = [float(x) for x in rng.choice([0.2, 0.5, 0.8], size=count)]
+    kernels = [("uniform", "spectral_avgdeg", "tr_random")[i % 3] for i in range(count)]
+    u, vbase, _ = gg.rmat_batch(scales, efs, seeds, device="cuda")
+    graphs = [gg.batch_member(u, vbase, i, 1 << scales[i]) for i in range(count)]
+    G = [sg.Graph.from_csr(ctx, g) for g in graphs]
+    B = sg.Batch(ctx, G)
+    outs = B.compress(kernels, ps, seeds)
+    for i in range(count):
+        off, col, _ = outs[i].download()
+        solo = sg.compress(G[i], kernels[i], ps[i], seeds[i])
+        s_off, s_col, _ = solo.download()
+        solo.free()
+        assert np.array_equal(off, s_off) and np.array_equal(col, s_col), (i, scales[i], kernels[i])
+        if i % 10 == 0 and (kernels[i] != "tr_random" or scales[i] <= 14):
+            o_off, o_col, _ = oracle.compress(graphs[i].to("cpu"), kernels[i], ps[i], seeds[i])
+            assert np.array_equal(off, o_off) and np.array_equal(col, o_col), (i, scales[i], kernels[i])
+    assert B.info()["vertices"] == sum(g.n for g in graphs)
+    B.free()
+    for g in G:
+        g.free()
