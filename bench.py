@@ -364,35 +364,66 @@ def run_ours(args, rank, world):
     rows = {}
     if not args.no_rows and world == 1:
         rows.update(rows_same_graph(args, sg, ctx, stream, G))
-    # ---- end to end through the C-ABI with pinned host buffers
-    out_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
-    out_col = torch.empty(max(2 * m, 1), dtype=torch.int32).pin_memory()
-    L = sg.lib()
+    # ---- end to end through the C-ABI with pinned host buffers.  Every step
+    # uploads its graph from host memory (sg_graph_from_host), compresses it
+    # and downloads the output CSR (sg_graph_download).  As a serving pipeline
+    # would, a second context with its own stream moves the data: it uploads
+    # step i+1 and downloads step i-1 while step i computes.
     import ctypes
+    from concurrent.futures import ThreadPoolExecutor
 
-    def e2e_step():
+    L = sg.lib()
+    xctx = sg.Context(local)
+    outs = [(torch.empty(n + 1, dtype=torch.int64).pin_memory(),
+             torch.empty(max(2 * m, 1), dtype=torch.int32).pin_memory()) for _ in range(2)]
+
+    def upload():
         h = ctypes.c_void_p()
-        sg._check(L.sg_graph_from_host(ctx.handle, n, 2 * m, off_h.data_ptr(), col_h.data_ptr(), None,
+        sg._check(L.sg_graph_from_host(xctx.handle, n, 2 * m, off_h.data_ptr(), col_h.data_ptr(), None,
                                        ctypes.byref(h)))
-        gi = sg.Graph(ctx, h)
-        H = sg.compress(gi, args.kernel, args.p, 1)
-        sg._check(L.sg_graph_download(ctx.handle, H.handle, out_off.data_ptr(), out_col.data_ptr(), None))
-        nnz_out = H.nnz
-        H.free()
-        gi.free()
-        return nnz_out
+        xctx.synchronize()
+        return sg.Graph(xctx, h)
 
-    e2e_step()
+    def download(H, k):
+        o_off, o_col = outs[k & 1]
+        sg._check(L.sg_graph_download(xctx.handle, H.handle, o_off.data_ptr(), o_col.data_ptr(), None))
+        return H.nnz
+
+    def e2e_run(k_steps):
+        nnz = 0
+        with ThreadPoolExecutor(1) as ex:
+            g_next = upload()
+            prev = None
+            for i in range(k_steps):
+                g_cur = g_next
+                fut = ex.submit(lambda i=i, prev=prev: (upload() if i + 1 < k_steps else None,
+                                                        download(prev, i - 1) if prev is not None else None))
+                # compress on the compute context (sg.compress would use the graph's own, the transfer one)
+                h = ctypes.c_void_p()
+                sg._check(L.sg_compress(ctx.handle, g_cur.handle, sg.KERNELS[args.kernel], float(args.p), 1, 0,
+                                        ctypes.byref(h)))
+                H = sg.Graph(ctx, h)
+                g_next, got = fut.result()
+                if prev is not None:
+                    nnz = got
+                    prev.free()
+                g_cur.free()
+                prev = H
+            nnz = download(prev, k_steps - 1)
+            prev.free()
+        return nnz
+
+    e2e_run(2)
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = max(2, min(args.steps, 5))
-    for _ in range(e2e_steps):
-        nnz_out = e2e_step()
+    e2e_steps = max(3, min(args.steps, 8))
+    nnz_out = e2e_run(e2e_steps)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    xctx.close()
     G.free()
-    del off_h, col_h, out_off, out_col
+    del off_h, col_h, outs
     torch.cuda.empty_cache()
 
     if not args.no_rows and world == 1:
@@ -456,7 +487,8 @@ def run_ours(args, rank, world):
         "clocks": clk,
         "e2e": {"value": replica_throughput(world, m, e2e_s), "unit": "edges/s",
                 "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
-                "d2h_bytes_per_step": 8 * (n + 1) + 4 * int(nnz_out)},
+                "d2h_bytes_per_step": 8 * (n + 1) + 4 * int(nnz_out), "steps": e2e_steps,
+                "pipeline": "a transfer context uploads step i+1 and downloads step i-1 while step i computes"},
         "rows": rows,
         "cpu_baseline": cpu,
         "cpu_all_cores": cpu_cores,
