@@ -788,7 +788,23 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-min-scale", type=int, default=10)
     ap.add_argument("--serve-max-scale", type=int, default=22)
+    ap.add_argument("--mode", choices=["compress", "batch", "serve"], default="compress",
+                    help="batch / serve: print only that row of the default line")
     args = ap.parse_args()
+    if args.mode != "compress":
+        import torch
+
+        import paper_1912_08950_gb300 as sg
+
+        torch.cuda.set_device(0)
+        if args.mode == "serve":
+            print(json.dumps({"mode": "serve", **serve_row(args)}), flush=True)
+        else:
+            stream = torch.cuda.Stream()
+            ctx = sg.Context(0, stream=stream)
+            print(json.dumps({"mode": "batch", **batch_row(args, ctx, stream)}), flush=True)
+            ctx.close()
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", 0))

@@ -64,9 +64,34 @@ __global__ void row_maps_kernel(const int64_t *__restrict__ off, int64_t n, uint
     if (blockIdx.x == 0 && threadIdx.x == 0) tile_vlo[num_tiles] = n + 1;
 }
 
+// Every entry of the row maps gets a value in range before row_maps_kernel
+// writes the ones a well-formed CSR defines: chunk rows 0, tile rows n + 1.
+// With malformed offsets (not non-decreasing) some entries are never written
+// by row_maps_kernel; pre-filled, they still keep every compaction access
+// inside the row range and the offset array.
+__global__ void prefill_row_maps_kernel(uint32_t *chunk_row, int64_t num_chunks, int64_t *tile_vlo,
+                                        int64_t num_tiles, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= num_tiles || i < num_chunks; i += stride) {
+        if (i < num_chunks) chunk_row[i] = 0;
+        if (i <= num_tiles) tile_vlo[i] = n + 1;
+    }
+}
+
+static void prefill_row_maps(cudaStream_t stream, int num_sms, uint32_t *chunk_row, int64_t num_chunks,
+                             int64_t *tile_vlo, int64_t num_tiles, int64_t n) {
+    const int64_t items = std::max(num_chunks, num_tiles + 1);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, (int64_t)num_sms * 16));
+    prefill_row_maps_kernel<<<(unsigned)blocks, 256, 0, stream>>>(chunk_row, num_chunks, tile_vlo, num_tiles, n);
+}
+
 sg_status fill_row_maps(Ctx *c, const Graph *g, const RowMaps &rm) {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((g->n + 1 + threads - 1) / threads, (int64_t)c->num_sms * 16);
+    {
+        SG_LAUNCH(c, "row_maps");
+        prefill_row_maps(c->stream, c->num_sms, rm.chunk_row, rm.num_chunks, rm.tile_vlo, rm.num_tiles, g->n);
+    }
     {
         SG_LAUNCH(c, "row_maps");
         row_maps_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, c->stream>>>(
@@ -296,9 +321,8 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
             }
         }
         // new row offsets for the rows whose start lies in this tile
-        // (clamped to the offset array: only a malformed CSR could put them outside)
-        const int64_t v0 = max(__ldg(a.tile_vlo + tile), (int64_t)0);
-        const int64_t v1 = min(__ldg(a.tile_vlo + tile + 1), a.n + 1);
+        // (both in [0, n + 1] whatever the offsets: see prefill_row_maps)
+        const int64_t v0 = __ldg(a.tile_vlo + tile), v1 = __ldg(a.tile_vlo + tile + 1);
         const int64_t tlen = t1 - t0;
         for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
             const int64_t q = __ldg(a.off + v) - t0;
@@ -350,12 +374,29 @@ struct SpectralPol {
     }
 };
 
+// Degrees saturated to 16 bits: 2 bytes per vertex instead of the 16-byte
+// offset pair, so the random degree reads of the orientation mostly hit L2
+// (R-MAT s26: 134 MB against 1.07 GB of offsets).
+__global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_t *__restrict__ deg16) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = __ldg(off + v + 1) - __ldg(off + v);
+        deg16[v] = (uint16_t)(d < 65535 ? d : 65535);
+    }
+}
+
 struct OrientPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = false;
     const int64_t *off;
-    // x precedes y in the degree order (d_x, x) < (d_y, y)
+    const uint16_t *deg16;  // min(d, 65535)
+    // x precedes y in the degree order (d_x, x) < (d_y, y).  Unequal saturated
+    // degrees order the vertices as their degrees do; equal ones below 65535
+    // are the degrees themselves; only two saturated ones need the offsets.
     __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
+        const uint32_t sx = __ldg(deg16 + x), sy = __ldg(deg16 + y);
+        if (sx != sy) return sx < sy;
+        if (sx < 65535u) return (uint32_t)x < y;
         const int64_t dx = __ldg(off + x + 1) - __ldg(off + x);
         const int64_t dy = __ldg(off + y + 1) - __ldg(off + y);
         return dx < dy || (dx == dy && (uint32_t)x < y);
@@ -661,9 +702,18 @@ sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Orient
     if (st == SG_OK)
         st = dalloc(c, (void **)&o->status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
     if (st != SG_OK) return st;
-    OrientPol pol{g->off};
+    uint16_t *deg16 = nullptr;
+    st = dalloc(c, (void **)&deg16, sizeof(uint16_t) * (size_t)std::max<int64_t>(g->n, 1));
+    if (st != SG_OK) return st;
+    if (g->n > 0) {
+        const int64_t blocks = std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 16);
+        SG_LAUNCH(c, "compact_orient_deg");
+        deg16_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->n, deg16);
+    }
+    OrientPol pol{g->off, deg16};
     st = run_compact(c, g, rm, pol, weights ? g->w : nullptr, o->off, o->col, weights ? o->w : nullptr,
                      o->fwd_bits, o->status, "compact_orient");
+    dfree(c, deg16);
     if (st != SG_OK) return st;
     int64_t mp = 0;
     st = read_i64(c, o->off + g->n, &mp);
@@ -1040,6 +1090,7 @@ sg_status noalloc_uniform(int device, void *cuda_stream, int64_t n, int64_t nnz,
     // the status words and the ticket must start at zero on every call
     SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(num_tiles + 1), stream));
     const int64_t rb = std::min<int64_t>((n + 1 + 255) / 256, (int64_t)num_sms * 16);
+    prefill_row_maps(stream, num_sms, chunk_row, num_chunks, tile_vlo, num_tiles, n);
     row_maps_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, stream>>>(off, n, chunk_row, num_chunks, tile_vlo,
                                                                            num_tiles);
     SG_CUDA(cudaGetLastError());
