@@ -53,6 +53,8 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 1024x fewer edges than s
 # the kernel and the JSON line reports null.
 MEASURED_TRAFFIC = {
     # (workload, kernel): (bytes per pass, sha256 of the enumeration sources)
+    # hub launch 1417.66 + 144.67 GB, main launch 514.07 + 11.94 GB (read + written)
+    ("rmat26", "tr_random"): (2088335747072, "dc5696c02952d9f2bc09f069060807f966823644bf47c6edc9467bd24a448c72"),
 }
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 

@@ -158,42 +158,6 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t lo
     return lo;
 }
 
-// Index of x in the sorted, duplicate-free ids a[lo, hi), or -1.  Vertex ids
-// carry no order of their own (generators and callers number vertices
-// arbitrarily), so a row's ids are spread over [0, n) and the first probes
-// interpolate x's position from its value; bisection takes over after three
-// probes, so a skewed row still costs O(log) probes, and the last few entries
-// are scanned.  Every probe of a long row touches a new 32-byte sector, so
-// interpolating instead of bisecting cuts the sectors a lookup reads.
-__device__ __forceinline__ int64_t find_sorted_u32(const uint32_t *a, int64_t lo, int64_t hi, uint32_t x,
-                                                   uint32_t n) {
-    uint32_t vlo = 0, vhi = n;  // every a[i], lo <= i < hi, lies in [vlo, vhi) when x is present
-    for (int it = 0; hi - lo > 8; ++it) {
-        int64_t g;
-        if (it < 3) {
-            const float f = __fdividef((float)(x - vlo), (float)(vhi - vlo));
-            g = lo + (int64_t)(f * (float)(hi - lo));
-            g = g < lo ? lo : (g >= hi ? hi - 1 : g);
-        } else {
-            g = lo + ((hi - lo) >> 1);
-        }
-        const uint32_t v = __ldg(a + g);
-        if (v == x) return g;
-        if (v < x) {
-            lo = g + 1;
-            vlo = v + 1;
-        } else {
-            hi = g;
-            vhi = v;
-        }
-    }
-    for (; lo < hi; ++lo) {
-        const uint32_t v = __ldg(a + lo);
-        if (v >= x) return v == x ? lo : -1;
-    }
-    return -1;
-}
-
 #endif  // __CUDACC__
 
 // batched compression: per-graph parameters in the disjoint union
