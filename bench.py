@@ -209,13 +209,15 @@ def byte_model(n, m, A_out, kernel):
     if kernel == "compact_orient":
         return 8 * (n + 1) + 4 * A + 4 * A + 8 * (n + 1) + 4 * m + A / 8
     if kernel == "compact_trmask":
-        # offsets and columns, forward bits, the deletion flag of every forward
-        # arc, the resolved bits of the reverse arcs, the output CSR
-        return 8 * (n + 1) + 4 * A + A / 8 + m + A / 8 + 8 * (n + 1) + 4 * A_out
-    if kernel == "compact_revkeep":
-        # offsets and columns, forward bits; per reverse arc the E+ row bounds
-        # of its tail (16 B), the found column (4 B) and its deletion flag; the bits out
-        return 8 * (n + 1) + 4 * A + A / 8 + 21 * m + A / 8
+        # offsets and columns, forward bits, the deletion flag of every arc's
+        # oriented arc (the reverse arcs' through their 8-byte list entry), the
+        # output CSR
+        return 8 * (n + 1) + 4 * A + A / 8 + 2 * m + 8 * m + 8 * (n + 1) + 4 * A_out
+    if kernel == "tri_reverse_list":
+        # offsets and columns, forward bits, the orientation's tile prefixes;
+        # per reverse arc the E+ row bounds of its tail (16 B), the found column
+        # (4 B) and its list entry written (8 B)
+        return 8 * (n + 1) + 4 * A + A / 8 + 28 * m
     if kernel in ("compact_uniform",):
         return 8 * (n + 1) + 4 * A + 8 * (n + 1) + 4 * A_out
     if kernel in ("compact_spectral",):
@@ -223,9 +225,9 @@ def byte_model(n, m, A_out, kernel):
     return None
 
 
-KERNEL_NAMES = ("tri_enum", "tri_hubs", "tri_inarcs", "tri_eo_fresh_reserve", "tri_eo_list_reserve",
+KERNEL_NAMES = ("tri_enum", "tri_hubs", "tri_reverse_list", "tri_eo_fresh_reserve", "tri_eo_list_reserve",
                 "tri_eo_list_accept", "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient",
-                "compact_revkeep", "compact_trmask", "row_maps")
+                "compact_trmask", "row_maps")
 
 
 def _timed(stream, fn, reps):
@@ -354,7 +356,7 @@ def run_ours(args, rank, world):
     enum_achieved = enum_bytes / pass_s / 1e9 if pass_s > 0 else None
     streamed_bytes = enum_streamed_bytes(n, m, work["head_arcs"], pst["probes"] / passes)
     streams = {}
-    for name in ("compact_orient", "compact_revkeep", "compact_trmask"):
+    for name in ("compact_orient", "tri_reverse_list", "compact_trmask"):
         t, launches = kt[name]
         if launches:
             b = byte_model(n, m, A_out, name)

@@ -88,7 +88,6 @@ struct Batch {
     Oriented o;
     uint8_t *del = nullptr;
     unsigned long long *st_orient = nullptr, *st_final = nullptr;
-    uint32_t *rev_keep = nullptr;  // keep bits of the reverse arcs (mask resolution)
     BatchTri bt;
     int64_t *off_c = nullptr;      // union offsets after compaction
     int64_t *out_off = nullptr;    // per-graph offsets, n_g + 1 each
@@ -116,6 +115,8 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
         if (st != SG_OK) return st;
         st = batch_orient(c, &b->u, b->rm, dev, b->o.w != nullptr, &b->o, b->st_orient, t.compact_per_sm);
         if (st != SG_OK) return st;
+        st = reverse_list(c, &b->u, b->rm, b->o, b->bt.inl, dev);
+        if (st != SG_OK) return st;
         SG_CUDA(cudaMemsetAsync(b->del, 0, (size_t)std::max<int64_t>(b->u.nnz / 2, 1), c->stream));
         BatchTri bt = b->bt;
         bt.light_max = t.light_max;
@@ -123,7 +124,7 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
         st = batch_tr_mark(c, &b->u, b->o, dev, bt, b->del);
         if (st != SG_OK) return st;
         st = batch_final(c, &b->u, b->rm, b->o, dev, b->del, b->off_c, b->out_col, b->u.w, b->out_w,
-                         b->st_final, b->rev_keep, t.compact_per_sm);
+                         b->st_final, t.compact_per_sm);
         if (st != SG_OK) return st;
     }
     const int threads = 256;
@@ -335,7 +336,6 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
         b->st_orient = o.status;
         if (st == SG_OK) st = dalloc(c, (void **)&b->st_final, sizeof(unsigned long long) * (size_t)(b->rm.num_tiles + 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->del, (size_t)std::max<int64_t>(m, 1));
-        if (st == SG_OK) st = dalloc(c, (void **)&b->rev_keep, sizeof(uint32_t) * (size_t)((at + 31) / 32 + 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->off_c, sizeof(int64_t) * (size_t)(nt + 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->out_off, sizeof(int64_t) * (size_t)(nt + count));
         if (st == SG_OK) st = dalloc(c, (void **)&b->out_col, sizeof(uint32_t) * (size_t)std::max<int64_t>(at, 1));
@@ -362,6 +362,7 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
         if (st == SG_OK)
             st = batch_orient(c, &u, b->rm, BatchDev{b->d_params, b->vgid}, false, &b->o, b->st_orient, 0);
         if (st == SG_OK) st = batch_tr_prepare(c, &u, b->o, &b->bt);
+        if (st == SG_OK) b->o.inl = b->bt.inl;  // the mask resolution reads the batch's reverse list
         if (st == SG_OK) st = check_device_error(c);
     }
     if (st != SG_OK) {
@@ -382,7 +383,6 @@ void sg_batch_free(sg_batch *b) {
         for (void *p : {(void *)b->u.off, (void *)b->u.col, (void *)b->u.w, (void *)b->vgid, (void *)b->d_params,
                         (void *)b->rm.chunk_row, (void *)b->rm.tile_vlo, (void *)b->o.off, (void *)b->o.col,
                         (void *)b->o.w, (void *)b->o.fwd_bits, (void *)b->o.status, (void *)b->st_final,
-                        (void *)b->rev_keep,
                         (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->bt.din,
                         (void *)b->bt.inl, (void *)b->off_c,
                         (void *)b->out_off, (void *)b->out_col, (void *)b->out_w, (void *)b->d_info})
@@ -401,9 +401,9 @@ void sg_batch_free(sg_batch *b) {
     dfree(c, b->vgid);
     dfree(c, b->d_params);
     free_row_maps(c, &b->rm);
+    b->o.inl = nullptr;  // owned by b->bt, freed below
     free_oriented(c, &b->o);
     dfree(c, b->st_final);
-    dfree(c, b->rev_keep);
     dfree(c, b->del);
     batch_tr_free(c, &b->bt);
     dfree(c, b->off_c);

@@ -408,24 +408,32 @@ struct MaskPol {
     static constexpr bool kMapCol = false;
     const uint32_t *fwd_bits;
     const unsigned long long *or_status;
-    const uint32_t *rev_keep;  // keep bits of the reverse arcs (rev_keep_kernel)
+    const uint2 *inl;          // the reverse list (reverse_list)
     const uint8_t *del;
     __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const {
         return tile == 0 ? 0 : (int64_t)(ld_volatile_u64(or_status + tile - 1) & kStVal);
     }
     // the arc stays iff its edge's oriented arc carries no deletion flag: a
-    // forward arc finds its E+ index by the running prefix of forward arcs, a
-    // reverse arc reads the bit rev_keep_kernel resolved for it
+    // forward arc's E+ index is the running prefix of forward arcs; a reverse
+    // arc's rank p - (forward arcs before p) finds its E+ index in the reverse list
     __device__ __forceinline__ bool keep(int64_t, uint32_t, int64_t p, const SlabCtx &s, float &) const {
         const int lane = (int)(p & 31);
-        if ((s.or_word >> lane) & 1u) return __ldg(del + s.or_base + __popc(s.or_word & lanemask_lt())) == 0;
-        return (__ldg(rev_keep + (p >> 5)) >> lane) & 1u;
+        const int64_t fwd_before = s.or_base + __popc(s.or_word & lanemask_lt());
+        if ((s.or_word >> lane) & 1u) return __ldg(del + fwd_before) == 0;
+        return __ldg(del + __ldg(&inl[p - fwd_before].y)) == 0;
     }
 };
 
-// Keep bits of the reverse arcs.  A reverse arc (x, y) of the symmetric CSR --
-// y before x in the degree order -- is the E+ arc y->x, at the position of x
-// in the sorted row N+(y); it stays iff that arc carries no deletion flag.
+// The reverse list.  A reverse arc (x, y) of the symmetric CSR -- y before x
+// in the degree order -- is the E+ arc y->x, at the position of x in the
+// sorted row N+(y).  One pass finds that position for every reverse arc and
+// stores (y, arc index) at the arc's reverse rank p - (forward arcs before p):
+// x's in-arcs then lie contiguous at off(x) - off+(x), sorted by tail, for the
+// enumeration (which streams N+(y) there when d+(y) < d+(x)), and the CSR
+// rebuild reads a reverse arc's deletion flag through the same entry.  The
+// pass also sums the enumeration's work model: W (shorter out-list of every
+// arc), W+ (head's out-list) and the arcs streamed from the head's side.
+//
 // Finding x is a chain of dependent loads, so every lane carries kRevK
 // searches (one per 32-arc slab of its warp's span) and advances them in
 // lockstep: their loads are independent and overlap.  Each search is a lower
@@ -436,29 +444,36 @@ struct MaskPol {
 // and bisection takes over after them (a skewed row still costs O(log)
 // probes).  On rows of uniformly spread ids of length 500 / 3000 that reads
 // about 1.9 / 2.4 distinct 32-byte sectors per lookup instead of 6 / 8.5, and
-// those random sectors are the kernel's bound.
-// One 32-bit word per slab holds the bits of its reverse arcs.
+// those random sectors are the pass's bound.
 constexpr int kRevK = 4;
 constexpr int kRevWin = 4;
 constexpr int kRevInterp = 6;
 
-__global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restrict__ off, int64_t n, int64_t nnz,
-                                                       const uint32_t *__restrict__ col,
-                                                       const uint32_t *__restrict__ chunk_row,
-                                                       const uint32_t *__restrict__ fwd_bits,
-                                                       const int64_t *__restrict__ offp,
-                                                       const uint32_t *__restrict__ colp,
-                                                       const uint8_t *__restrict__ del, uint32_t *rev_keep, int *err,
-                                                       BatchDev batch) {
+__global__ void __launch_bounds__(256, 4) reverse_list_kernel(
+    const int64_t *__restrict__ off, int64_t n, int64_t nnz, const uint32_t *__restrict__ col,
+    const uint32_t *__restrict__ chunk_row, const uint32_t *__restrict__ fwd_bits,
+    const unsigned long long *__restrict__ or_status, const int64_t *__restrict__ offp,
+    const uint32_t *__restrict__ colp, uint2 *inl, unsigned long long *ctr, int *err, BatchDev batch) {
     const int lane = threadIdx.x & 31;
     const int64_t nslabs = (nnz + 31) >> 5;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long work = 0, fwd = 0, head = 0;
     for (int64_t s0 = wid * kRevK; s0 < nslabs; s0 += nw * kRevK) {
-        int64_t base[kRevK];
+        int64_t base[kRevK], rank[kRevK];
         int len[kRevK];
-        uint32_t xs[kRevK], vlo[kRevK], vhi[kRevK];
+        uint32_t xs[kRevK], ys[kRevK], vlo[kRevK], vhi[kRevK];
         bool need[kRevK];
+        // forward arcs before slab s0: the orientation's prefix up to its tile
+        // plus the forward bits of the tile's earlier slabs
+        const int64_t tile = (s0 << 5) / kTile;
+        const int64_t w0 = (tile * kTile) >> 5;  // the tile's first slab
+        int64_t fwd_run = tile == 0 ? 0 : (int64_t)(__ldg(or_status + tile - 1) & kStVal);
+        {
+            const int64_t wa = w0 + lane, wb = w0 + 32 + lane;
+            int cnt = (wa < s0 ? __popc(__ldg(fwd_bits + wa)) : 0) + (wb < s0 ? __popc(__ldg(fwd_bits + wb)) : 0);
+            fwd_run += warp_sum(cnt);
+        }
         int64_t cursor = (int64_t)__ldg(chunk_row + ((s0 << 5) / kWarpSpan));
 #pragma unroll
         for (int k = 0; k < kRevK; ++k) {
@@ -467,6 +482,8 @@ __global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restr
             base[k] = 0;
             len[k] = 0;
             xs[k] = 0;
+            ys[k] = 0;
+            rank[k] = 0;
             vlo[k] = 0;
             vhi[k] = (uint32_t)n;
             if (sbase < nnz) {  // warp-uniform
@@ -474,6 +491,8 @@ __global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restr
                 const int q = valid ? lane : (int)(nnz - 1 - sbase);
                 const int64_t x = warp_row(off, n, cursor, sbase, q);
                 const uint32_t fw = __ldg(fwd_bits + (sbase >> 5));
+                rank[k] = sbase + lane - (fwd_run + __popc(fw & lanemask_lt()));
+                fwd_run += __popc(fw);
                 // in a batch, graphs without a triangle kernel have no E+ arcs to look up
                 const bool tri = batch.params == nullptr ||
                                  __ldg(&batch.params[__ldg(batch.vgid + x)].kernel) >= (int)SG_TR_RANDOM;
@@ -482,7 +501,14 @@ __global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restr
                     base[k] = __ldg(offp + y);
                     len[k] = (int)(__ldg(offp + y + 1) - base[k]);
                     xs[k] = (uint32_t)x;
+                    ys[k] = y;
                     need[k] = true;
+                    // the work model of arc y->x: d+(y) streamed against d+(x)
+                    const int64_t dx = __ldg(offp + x + 1) - __ldg(offp + x);
+                    const int64_t dy = len[k];
+                    work += (unsigned long long)(dx < dy ? dx : dy);
+                    fwd += (unsigned long long)dx;
+                    head += dy < dx ? 1ull : 0ull;
                 }
             }
         }
@@ -520,54 +546,54 @@ __global__ void __launch_bounds__(256, 4) rev_keep_kernel(const int64_t *__restr
         }
         // the windows, loaded together (base + len may be one past the row, but
         // stays inside the E+ column array, which has room for nnz >= m + 1
-        // entries; the first match is x's own position); then the deletion
-        // flags, loaded together
-        int64_t idx[kRevK];
+        // entries; the first match is x's own position)
 #pragma unroll
         for (int k = 0; k < kRevK; ++k) {
             uint32_t w[kRevWin];
 #pragma unroll
             for (int j = 0; j < kRevWin; ++j) w[j] = (need[k] && j <= len[k]) ? __ldg(colp + base[k] + j) : kFull;
-            idx[k] = -1;
+            int64_t idx = -1;
 #pragma unroll
             for (int j = kRevWin - 1; j >= 0; --j)
-                if (need[k] && j <= len[k] && w[j] == xs[k]) idx[k] = base[k] + j;
-        }
-        uint8_t d[kRevK];
-#pragma unroll
-        for (int k = 0; k < kRevK; ++k) d[k] = (need[k] && idx[k] >= 0) ? __ldg(del + idx[k]) : (uint8_t)1;
-#pragma unroll
-        for (int k = 0; k < kRevK; ++k) {
-            const int64_t sbase = (s0 + k) << 5;
-            if (sbase < nnz) {  // warp-uniform
-                if (need[k] && idx[k] < 0) atomicExch(err, (int)kDevBadGraph);  // no reverse arc: not symmetric
-                const unsigned bits = __ballot_sync(kFull, need[k] && d[k] == 0);
-                if (lane == 0) rev_keep[sbase >> 5] = bits;
+                if (need[k] && j <= len[k] && w[j] == xs[k]) idx = base[k] + j;
+            if (need[k]) {
+                if (idx < 0) atomicExch(err, (int)kDevBadGraph);  // no reverse arc: not symmetric
+                else inl[rank[k]] = make_uint2(ys[k], (uint32_t)idx);
             }
         }
     }
+    work = warp_sum(work);
+    fwd = warp_sum(fwd);
+    head = warp_sum(head);
+    if (lane == 0 && work) atomicAdd(ctr + kCtrWork, work);
+    if (lane == 0 && fwd) atomicAdd(ctr + kCtrWorkFwd, fwd);
+    if (lane == 0 && head) atomicAdd(ctr + kCtrInArcs, head);
 }
 
-static sg_status launch_rev_keep(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
-                                 uint32_t *rev_keep, BatchDev batch = BatchDev{nullptr, nullptr}) {
+sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, uint2 *inl, BatchDev batch) {
+    // the work model's sums start afresh for this orientation
+    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrInArcs, 0, 3 * sizeof(unsigned long long), c->stream));
+    static_assert(kCtrWork == kCtrInArcs + 1 && kCtrWorkFwd == kCtrInArcs + 2, "work counters are adjacent");
     if (g->nnz == 0) return SG_OK;
     static int per_sm = -1;
     if (per_sm < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rev_keep_kernel, 256, 0) != cudaSuccess || b < 1) b = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, reverse_list_kernel, 256, 0) != cudaSuccess || b < 1)
+            b = 1;
         per_sm = b;
     }
     const int64_t warps = ((g->nnz + 31) / 32 + kRevK - 1) / kRevK;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)c->num_sms * per_sm));
     {
-        SG_LAUNCH(c, "compact_revkeep");
-        rev_keep_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(g->off, g->n, g->nnz, g->col, rm.chunk_row,
-                                                             o.fwd_bits, o.off, o.col, del, rev_keep, c->d_err,
-                                                             batch);
+        SG_LAUNCH(c, "tri_reverse_list");
+        reverse_list_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(g->off, g->n, g->nnz, g->col, rm.chunk_row,
+                                                                 o.fwd_bits, o.status, o.off, o.col, inl, c->d_ctr,
+                                                                 c->d_err, batch);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
+
 
 // ------------------------------------------------------------------ driver
 template <class Pol>
@@ -722,7 +748,9 @@ sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Orient
     if (st != SG_OK) return st;
     if (mp != o->m)
         return fail(SG_ERR_INVALID_GRAPH, "graph is not symmetric: oriented arcs != nnz/2");
-    return SG_OK;
+    st = dalloc(c, (void **)&o->inl, sizeof(uint2) * (size_t)std::max<int64_t>(g->nnz - o->m, 1));
+    if (st == SG_OK) st = reverse_list(c, g, rm, *o, o->inl);
+    return st;
 }
 
 void free_oriented(Ctx *c, Oriented *o) {
@@ -731,6 +759,7 @@ void free_oriented(Ctx *c, Oriented *o) {
     dfree(c, o->w);
     dfree(c, o->fwd_bits);
     dfree(c, o->status);
+    dfree(c, o->inl);
     *o = Oriented{};
 }
 
@@ -738,18 +767,14 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
                        Graph **out) {
     Graph *h = nullptr;
     unsigned long long *status = nullptr;
-    uint32_t *rev_keep = nullptr;
     sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
     if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
-    if (st == SG_OK) st = dalloc(c, (void **)&rev_keep, sizeof(uint32_t) * (size_t)((g->nnz + 31) / 32 + 1));
-    if (st == SG_OK) st = launch_rev_keep(c, g, rm, o, del, rev_keep);
     if (st == SG_OK) {
-        MaskPol pol{o.fwd_bits, o.status, rev_keep, del};
+        MaskPol pol{o.fwd_bits, o.status, o.inl, del};
         st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_trmask");
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
-    dfree(c, rev_keep);
     dfree(c, status);
     if (st != SG_OK) {
         delete_graph(c, h);
@@ -813,12 +838,10 @@ sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev
 
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      unsigned long long *status, uint32_t *rev_keep, int grid_per_sm) {
-    // the reverse arcs of graphs without a triangle kernel are not looked up
-    // (BatchFinalPol decides those arcs itself)
-    sg_status st = launch_rev_keep(c, u, rm, o, del, rev_keep, b);
-    if (st != SG_OK) return st;
-    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, rev_keep, del}, o.fwd_bits};
+                      unsigned long long *status, int grid_per_sm) {
+    // the reverse arcs of graphs without a triangle kernel are not in the
+    // reverse list (BatchFinalPol decides those arcs itself)
+    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, o.inl, del}, o.fwd_bits};
     return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, nullptr, status, "compact_final",
                        grid_per_sm);
 }

@@ -194,6 +194,11 @@ struct Oriented {
     float *w = nullptr;          // w+[m] (weighted TR only)
     uint32_t *fwd_bits = nullptr;  // bit per symmetric arc: 1 iff x precedes y
     unsigned long long *status = nullptr;  // inclusive prefix of forward arcs per tile
+    // the reverse arcs in symmetric order: the one at symmetric position p is
+    // E+ arc u->x (u = col[p] before its row x), stored as (u, arc index) at
+    // rank p - (forward arcs before p); x's in-arcs are thus contiguous at
+    // off(x) - off+(x), sorted by u (reverse_list)
+    uint2 *inl = nullptr;
 };
 sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Oriented *o);
 void free_oriented(Ctx *c, Oriented *o);
@@ -210,7 +215,11 @@ sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev
                        unsigned long long *status, int grid_per_sm);
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      unsigned long long *status, uint32_t *rev_keep, int grid_per_sm);
+                      unsigned long long *status, int grid_per_sm);
+// the reverse list of o (see Oriented::inl) into inl; in a batch only the
+// graphs with a triangle kernel are listed
+sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, uint2 *inl,
+                       BatchDev batch = BatchDev{nullptr, nullptr});
 
 // low_degree vertex kernel (sg_compact.cu)
 sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out);

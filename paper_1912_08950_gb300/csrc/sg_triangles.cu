@@ -579,7 +579,7 @@ __device__ __forceinline__ void probe_list(const TriArgs &a, const Table &tb, in
 // streams the lists one by one.
 template <Mode M>
 __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &tb, int log_slots, int stash_n,
-                                                uint32_t u, uint32_t tbase, int64_t ib, int first, int cnt,
+                                                uint32_t u, int du, uint32_t tbase, int64_t ib, int first, int cnt,
                                                 HitQueue &q, QState &qs, unsigned &live, unsigned long long &probes,
                                                 unsigned long long &tris, Emitter &em, bool count_probes) {
     const int lane = threadIdx.x & 31;
@@ -591,8 +591,9 @@ __device__ __forceinline__ void stream_in_group(const TriArgs &a, const Table &t
         se = it.y;
         const int64_t b0 = __ldg(a.offp + sv);
         so = (uint32_t)b0;
-        sd = (kEdgeOnce<M> && a.considered != nullptr && considered_bit(a.considered, se))
-                 ? 0 : (int)(__ldg(a.offp + sv + 1) - b0);
+        // an in-arc v->u whose tail has d+(v) >= d+(u) is streamed from v's side
+        const int dvv = (int)(__ldg(a.offp + sv + 1) - b0);
+        sd = (dvv >= du || (kEdgeOnce<M> && a.considered != nullptr && considered_bit(a.considered, se))) ? 0 : dvv;
     }
     // the next list's first slabs load while the current one is probed
     uint32_t pa, pb;
@@ -720,8 +721,8 @@ __global__ void __launch_bounds__(TW * 32, TW == kTW ? kEnumCtasPerSm<M> : 1) tr
                     }
                     if (i >= d) {  // 32 in-arcs v->u with d+(v) < d+(u): stream each N+(v)
                         const int g0 = (i - d) * 32;
-                        stream_in_group<M>(a, tb, log_slots, stash_n, u, ou + (uint32_t)c0, ib, g0, min(32, nin - g0),
-                                           q, qst, live, probes, tris, em, c0 == 0);
+                        stream_in_group<M>(a, tb, log_slots, stash_n, u, d, ou + (uint32_t)c0, ib, g0,
+                                           min(32, nin - g0), q, qst, live, probes, tris, em, c0 == 0);
                         continue;
                     }
                     // out-arc u->v: stream N+(v)
@@ -827,8 +828,8 @@ __global__ void __launch_bounds__(TW * 32, TW == kTW ? kEnumCtasPerSm<M> : 1) tr
                 // in-arcs v->u with d+(v) < d+(u), in groups of 32
                 const int64_t ib = nin > 0 ? __ldg(a.offs + u) - (int64_t)ou : 0;
                 for (int c = 0; c < nin; c += 32)
-                    stream_in_group<M>(a, tb, log_slots, stash_n, u, ou, ib, c, min(32, nin - c), q, qst, live,
-                                       probes, tris, em, true);
+                    stream_in_group<M>(a, tb, log_slots, stash_n, u, d, ou, ib, c, min(32, nin - c), q, qst,
+                                       live, probes, tris, em, true);
                 flush_hits<M>(a, q, qst, u, live, em);
                 __syncwarp();
             }
@@ -859,52 +860,8 @@ __device__ __forceinline__ int heavy_key(int64_t d, int64_t nin, int64_t hub_min
     return heavy_bucket(d, nin) + (d > hub_min ? kBuckets : 0);
 }
 
-// In-arcs streamed from the head's side: for every arc u->v of E+ with
-// d+(u) < d+(v), append (u, arc) to v's in-list.  The row of v in the
-// symmetric CSR holds its d(v) - d+(v) in-arcs, so v's list has room at
-// inl[offs(v) - offp(v) ...].  The order inside a list is whatever the
-// atomics give; nothing downstream depends on it.  A list that would outgrow
-// that room (an asymmetric input) raises kDevBadGraph instead of writing.
-__global__ void inarc_scatter_kernel(const int64_t *__restrict__ offp, const uint32_t *__restrict__ colp,
-                                     const int64_t *__restrict__ offs, int64_t n, uint32_t *din, uint2 *inl,
-                                     unsigned long long *ctr, int *err) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    // work: W, the probes of one enumeration pass; fwd: W+ = sum of d+(v) over arcs u->v,
-    // the probes of the plain forward algorithm (every arc streams N+(v))
-    unsigned long long cnt = 0, work = 0, fwd = 0;
-    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; u < n; u += nw) {
-        const int64_t ou = __ldg(offp + u), du = __ldg(offp + u + 1) - ou;
-        for (int64_t i = lane; i < du; i += 32) {
-            const uint32_t v = __ldg(colp + ou + i);
-            const int64_t ov = __ldg(offp + v);
-            const int64_t dv = __ldg(offp + v + 1) - ov;
-            work += (unsigned long long)(du < dv ? du : dv);
-            fwd += (unsigned long long)dv;
-            if (du < dv) {
-                const int64_t sv = __ldg(offs + v);
-                const int64_t room = (__ldg(offs + v + 1) - sv) - dv;
-                const uint32_t k = atomicAdd(din + v, 1u);
-                if ((int64_t)k < room) {
-                    inl[sv - ov + k] = make_uint2((uint32_t)u, (uint32_t)(ou + i));
-                    ++cnt;
-                } else {
-                    atomicExch(err, (int)kDevBadGraph);
-                }
-            }
-        }
-    }
-    cnt = warp_sum(cnt);
-    work = warp_sum(work);
-    fwd = warp_sum(fwd);
-    if (lane == 0 && cnt) atomicAdd(ctr + kCtrInArcs, cnt);
-    if (lane == 0 && work) atomicAdd(ctr + kCtrWork, work);
-    if (lane == 0 && fwd) atomicAdd(ctr + kCtrWorkFwd, fwd);
-}
-
-// Also clamps every in-list length to its room (only an asymmetric input,
-// already flagged by the scatter, can exceed it), so that no later read
-// leaves the in-arc array.
+// Also writes every vertex's in-degree d(u) - d+(u): the length of its
+// in-list in the reverse list (see Oriented::inl).
 __global__ void classify_count_kernel(const int64_t *__restrict__ offp, const int64_t *__restrict__ offs,
                                       uint32_t *din, int64_t n, int light_max, int light_items, int64_t hub_min,
                                       unsigned long long *bucket_cnt, unsigned long long *ctr) {
@@ -916,14 +873,9 @@ __global__ void classify_count_kernel(const int64_t *__restrict__ offp, const in
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
         const int64_t d = offp[u + 1] - offp[u];
         dmax = d > (int64_t)dmax ? (unsigned long long)d : dmax;
-        int64_t nin = din[u];
-        if (nin > 0) {
-            const int64_t room = (offs[u + 1] - offs[u]) - d;
-            if (nin > room) {
-                nin = room < 0 ? 0 : room;
-                din[u] = (uint32_t)nin;
-            }
-        }
+        int64_t nin = (offs[u + 1] - offs[u]) - d;
+        nin = nin < 0 ? 0 : nin;
+        din[u] = (uint32_t)nin;
         if (is_heavy(d, nin, light_max, light_items)) atomicAdd(&s_cnt[heavy_key(d, nin, hub_min)], 1u);
     }
 #pragma unroll
@@ -1223,31 +1175,16 @@ static void free_plan(Ctx *c, Plan *pl) {
     dfree(c, pl->heavy);
     dfree(c, pl->buckets);
     dfree(c, pl->din);
-    dfree(c, pl->inl);
     pl->heavy = nullptr;
     pl->buckets = nullptr;
     pl->din = nullptr;
     pl->inl = nullptr;
 }
 
-// Gather the in-arcs streamed from the head's side (zeroed counts, then the
-// scatter); the classification that follows clamps the counts.
-static sg_status launch_inarcs(Ctx *c, const Oriented &o, const int64_t *offs, uint32_t *din, uint2 *inl) {
-    SG_CUDA(cudaMemsetAsync(din, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1), c->stream));
-    if (o.n == 0) return SG_OK;
-    const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 7) / 8, (int64_t)c->num_sms * 16));
-    {
-        SG_LAUNCH(c, "tri_inarcs");
-        inarc_scatter_kernel<<<(unsigned)wblocks, 256, 0, c->stream>>>(o.off, o.col, offs, o.n, din, inl, c->d_ctr,
-                                                                       c->d_err);
-    }
-    SG_CUDA(cudaGetLastError());
-    return SG_OK;
-}
 
 // inl_cap: room for in-arc records; nnz - m when E+ holds all m arcs, nnz
 // when it may hold fewer (batches orient only their triangle-kernel graphs).
-static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64_t inl_cap, Plan *pl) {
+static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, Plan *pl) {
     if (o.m >= (int64_t)0xFFFFFFFFll)
         return fail(SG_ERR_UNSUPPORTED, "triangle kernels address oriented arcs with 32 bits: m must be < 2^32");
     if (o.n >= (int64_t)0xFFFFFFFEll)
@@ -1256,13 +1193,10 @@ static sg_status make_plan(Ctx *c, const Oriented &o, const int64_t *offs, int64
     sg_status st = dalloc(c, (void **)&pl->heavy, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&pl->buckets, sizeof(unsigned long long) * 2 * kKeys);
     if (st == SG_OK) st = dalloc(c, (void **)&pl->din, sizeof(uint32_t) * (size_t)std::max<int64_t>(o.n, 1));
-    if (st == SG_OK) st = dalloc(c, (void **)&pl->inl, sizeof(uint2) * (size_t)std::max<int64_t>(inl_cap, 1));
     if (st != SG_OK) return st;
+    pl->inl = o.inl;  // the orientation's reverse list (not owned by the plan)
     SG_CUDA(cudaMemsetAsync(pl->buckets, 0, sizeof(unsigned long long) * 2 * kKeys, c->stream));
     SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrMaxDeg, 0, sizeof(unsigned long long), c->stream));
-    SG_CUDA(cudaMemsetAsync(c->d_ctr + kCtrWork, 0, sizeof(unsigned long long), c->stream));
-    st = launch_inarcs(c, o, offs, pl->din, pl->inl);
-    if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     if (o.n > 0) {
         SG_LAUNCH(c, "tri_classify");
@@ -1702,7 +1636,7 @@ static sg_status eo_rounds(Ctx *c, const Graph *g, const Oriented &o, sg_kernel 
 
 sg_status tr_mark(Ctx *c, const Graph *g, const Oriented &o, sg_kernel k, double p, uint64_t seed, uint8_t *del) {
     Plan pl;
-    sg_status st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
+    sg_status st = make_plan(c, o, g->off, &pl);
     TriArgs a = base_args(c, o);
     a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(seed >> 32);
@@ -1737,14 +1671,15 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
     Plan pl;
     unsigned long long v0[kCtrCount] = {}, v1[kCtrCount] = {};
     sg_status st = read_ctr(c, 0, kCtrCount, v0);
-    if (st == SG_OK) st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
+    if (st == SG_OK) st = make_plan(c, o, g->off, &pl);
     if (st == SG_OK) st = launch_enum<Mode::Count>(c, base_args(c, o), pl);
     if (st == SG_OK) st = read_ctr(c, 0, kCtrCount, v1);
     if (count) *count = (int64_t)(v1[kCtrTriangles] - v0[kCtrTriangles]);
     if (probes) *probes = (int64_t)(v1[kCtrProbes] - v0[kCtrProbes]);
     if (maxdeg) *maxdeg = pl.max_deg;
-    if (in_arcs) *in_arcs = (int64_t)(v1[kCtrInArcs] - v0[kCtrInArcs]);
-    if (fwd_probes) *fwd_probes = (int64_t)(v1[kCtrWorkFwd] - v0[kCtrWorkFwd]);
+    // summed afresh by this orientation's reverse list
+    if (in_arcs) *in_arcs = (int64_t)v1[kCtrInArcs];
+    if (fwd_probes) *fwd_probes = (int64_t)v1[kCtrWorkFwd];
     free_plan(c, &pl);
     return st;
 }
@@ -1752,7 +1687,7 @@ sg_status tr_count(Ctx *c, const Graph *g, const Oriented &o, int64_t *count, in
 // Triangles through every vertex (device uint64[n], overwritten).
 sg_status tr_vertex_counts(Ctx *c, const Graph *g, const Oriented &o, unsigned long long *vcnt) {
     Plan pl;
-    sg_status st = make_plan(c, o, g->off, g->nnz - o.m, &pl);
+    sg_status st = make_plan(c, o, g->off, &pl);
     if (st == SG_OK && cudaMemsetAsync(vcnt, 0, sizeof(unsigned long long) * (size_t)std::max<int64_t>(o.n, 1),
                                        c->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync(vcnt)");
@@ -1768,7 +1703,7 @@ sg_status batch_tr_prepare(Ctx *c, const Graph *u, const Oriented &o, BatchTri *
     Plan pl;
     pl.light_max = bt->light_max;
     pl.light_items = 4 * bt->light_max;
-    sg_status st = make_plan(c, o, u->off, u->nnz, &pl);  // an unvalidated member may orient fewer arcs
+    sg_status st = make_plan(c, o, u->off, &pl);
     if (st == SG_OK) {
         bt->log_slots = pl.log_slots;
         bt->smem = pl.smem;
@@ -1805,7 +1740,7 @@ sg_status batch_tr_mark(Ctx *c, const Graph *u, const Oriented &o, const BatchDe
     if (o.n == 0) return SG_OK;
     const int light_items = 4 * bt.light_max;
     SG_CUDA(cudaMemsetAsync(bt.buckets, 0, sizeof(unsigned long long) * (2 * kKeys + 1), c->stream));
-    sg_status st = launch_inarcs(c, o, u->off, bt.din, bt.inl);
+    sg_status st = SG_OK;  // the reverse list bt.inl was filled after the batch orientation
     if (st != SG_OK) return st;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((o.n + 255) / 256, (int64_t)c->num_sms * 8));
     {
