@@ -194,13 +194,14 @@ def enum_pass_bytes(n, m, fwd_probes):
     return 8 * (n + 1) + 4 * m + 4 * fwd_probes
 
 
-def enum_streamed_bytes(n, m, head_arcs, probes):
-    """Bytes the enumeration actually reads per pass: off+ and the in-list
-    length of every vertex (8 + 4 B), N+(x) staged in the tables (4 B/arc), the
-    off+ pair of every streamed list (8 B/arc), the in-list records (8 B per
-    arc streamed from the head's side) and one 4-byte read per probe made
-    (W = sum over arcs of min(d+(u), d+(v)))."""
-    return 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * head_arcs + 4 * probes
+def enum_streamed_bytes(n, m, probes):
+    """Bytes the enumeration actually reads per pass: off+ and the in-degree
+    of every vertex (8 + 4 B), N+(x) staged in the tables (4 B/arc), the off+
+    pair of every streamed list (8 B/arc), the in-list entry of every in-arc
+    (8 B/arc: the entries of in-arcs streamed from the tail's side are read
+    and skipped) and one 4-byte read per probe made (W = sum over arcs of
+    min(d+(u), d+(v)))."""
+    return 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * m + 4 * probes
 
 
 def byte_model(n, m, A_out, kernel):
@@ -354,7 +355,7 @@ def run_ours(args, rank, world):
     enum_bytes = enum_pass_bytes(n, m, fwd_total / passes)
     pass_s = enum_ms / passes / 1e3
     enum_achieved = enum_bytes / pass_s / 1e9 if pass_s > 0 else None
-    streamed_bytes = enum_streamed_bytes(n, m, work["head_arcs"], pst["probes"] / passes)
+    streamed_bytes = enum_streamed_bytes(n, m, pst["probes"] / passes)
     streams = {}
     for name in ("compact_orient", "tri_reverse_list", "compact_trmask"):
         t, launches = kt[name]
@@ -476,7 +477,7 @@ def run_ours(args, rank, world):
                      "streamed": {"algorithmic_bytes_per_launch": streamed_bytes,
                                   "achieved": streamed_bytes / pass_s / 1e9 if pass_s > 0 else None,
                                   "frac": streamed_bytes / pass_s / 1e9 / hbm if pass_s > 0 else None,
-                                  "byte_model": "probes made: 8(n+1) + 4n + 12m + 8H + 4 W"},
+                                  "byte_model": "probes made: 8(n+1) + 4n + 20m + 4 W"},
                      "eo_list_bytes_per_step": 16 * pst["eo_listed"] / psteps},
         "step_roofline": {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms / 1e3) / 1e9,
                           "frac": step_bytes / (ms / 1e3) / 1e9 / hbm, "unit": "GB/s",

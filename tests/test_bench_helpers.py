@@ -16,8 +16,8 @@ def test_enumeration_byte_models():
     n, m = 1000, 8000
     # the enumeration pass: E+ once, 4 B per probe of the forward algorithm
     assert bench.enum_pass_bytes(n, m, 10_000) == 8 * (n + 1) + 4 * m + 40_000
-    # the probes-made model adds the in-list lengths, staged bounds and in-list records
-    assert bench.enum_streamed_bytes(n, m, 500, 10_000) == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * 500 + 40_000
+    # the probes-made model adds the in-degrees, staged bounds and in-list entries
+    assert bench.enum_streamed_bytes(n, m, 10_000) == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 8 * m + 40_000
 
 
 def test_tr_step_byte_model():
