@@ -356,6 +356,7 @@ sg_status sg_graph_from_device(sg_ctx *ctx, const sg_csr_view *in, int copy, int
     if (in->n >= (int64_t)4294967295ll) return fail(SG_ERR_UNSUPPORTED, "n >= 2^32 - 1: ids are uint32");
     if (!in->off || (in->nnz > 0 && !in->col)) return fail(SG_ERR_INVALID_ARG, "NULL CSR array");
     if (in->nnz % 2) return fail(SG_ERR_INVALID_GRAPH, "a symmetric CSR has an even arc count");
+    if (in->n == 0 && in->nnz > 0) return fail(SG_ERR_INVALID_GRAPH, "arcs without vertices");
     Ctx *c = C_(ctx);
     sg_status st = set_device(c);
     if (st != SG_OK) return st;
@@ -402,6 +403,7 @@ sg_status sg_graph_from_host(sg_ctx *ctx, int64_t n, int64_t nnz, const int64_t 
     if (n < 0 || nnz < 0) return fail(SG_ERR_INVALID_ARG, "negative size");
     if (n >= (int64_t)4294967295ll) return fail(SG_ERR_UNSUPPORTED, "n >= 2^32 - 1: ids are uint32");
     if (nnz % 2) return fail(SG_ERR_INVALID_GRAPH, "a symmetric CSR has an even arc count");
+    if (n == 0 && nnz > 0) return fail(SG_ERR_INVALID_GRAPH, "arcs without vertices");
     Ctx *c = C_(ctx);
     sg_status st = set_device(c);
     if (st != SG_OK) return st;

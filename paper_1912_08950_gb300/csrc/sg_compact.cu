@@ -142,33 +142,46 @@ struct SlabCtx {
     int64_t or_base;   // E+ index of the slab's first forward arc
 };
 
-// Row of position sbase + q (q in [0,32), non-decreasing across lanes).
-// `cursor` is a row starting at or before sbase; it advances to the row of
-// lane 31 so the next slab starts its search there.
-__device__ __forceinline__ int64_t warp_row(const int64_t *__restrict__ off, int64_t n, int64_t &cursor,
-                                            int64_t sbase, int q) {
+// Rows of the arcs of K consecutive 32-arc slabs starting at wbase, one arc
+// per lane (arcs at or past t1 take the row of arc t1 - 1), clamped to
+// [0, n - 1].  r0 is a row with off[r0] <= wbase (the row holding wbase, from
+// the row maps).  Lane j holds the start off[rb + 1 + j] of one batch of 32
+// rows; a slab's rows follow from a search of that batch by shuffles, and a
+// new batch is loaded only when a slab runs past the batch's last start, so
+// the searches of the K slabs do not wait on one another's loads.
+template <int K>
+__device__ __forceinline__ void warp_rows(const int64_t *__restrict__ off, int64_t n, int64_t r0, int64_t wbase,
+                                          int64_t t1, uint32_t (&rows)[K]) {
     const int lane = threadIdx.x & 31;
-    int64_t cur = cursor;
-    int64_t row = -1;
-    for (;;) {
-        const int64_t bi = cur + 1 + lane;  // lane j holds the start of row cur+1+j
-        const int64_t b = (bi <= n) ? __ldg(off + bi) : LLONG_MAX;
-        const int64_t rel = b - sbase;
-        const int r = rel < 0 ? -1 : (rel > 32 ? 32 : (int)rel);
-        int cnt = 0;  // boundaries at or before sbase + q
+    int64_t rb = r0;
+    int64_t bst = (rb + 1 + lane <= n) ? __ldg(off + rb + 1 + lane) : LLONG_MAX;
+    uint32_t prev = (uint32_t)min(r0, n - 1);
 #pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            const int v = __shfl_sync(kFull, r, cnt + s - 1);
-            if (v <= q) cnt += s;
+    for (int k = 0; k < K; ++k) {
+        const int64_t sbase = wbase + k * 32;
+        rows[k] = prev;
+        if (sbase >= t1) continue;  // warp-uniform
+        const int q = sbase + lane < t1 ? lane : (int)(t1 - 1 - sbase);
+        int64_t row = -1;
+        for (;;) {
+            const int64_t rel = bst - sbase;
+            const int r = rel < 0 ? -1 : (rel > 32 ? 32 : (int)rel);
+            int cnt = 0;  // batch starts at or before sbase + q
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int v = __shfl_sync(kFull, r, cnt + s - 1);
+                if (v <= q) cnt += s;
+            }
+            const int r31 = __shfl_sync(kFull, r, 31);
+            if (cnt == 31 && r31 <= q) cnt = 32;
+            if (row < 0 && cnt < 32) row = rb + cnt;
+            if (!__any_sync(kFull, row < 0)) break;
+            rb += 32;
+            bst = (rb + 1 + lane <= n) ? __ldg(off + rb + 1 + lane) : LLONG_MAX;
         }
-        const int r31 = __shfl_sync(kFull, r, 31);
-        if (cnt == 31 && r31 <= q) cnt = 32;
-        if (row < 0 && cnt < 32) row = cur + cnt;
-        if (!__any_sync(kFull, row < 0)) break;
-        cur += 32;
+        prev = (uint32_t)min(row, n - 1);
+        rows[k] = prev;
     }
-    cursor = __shfl_sync(kFull, row, 31);
-    return row;
 }
 
 // Decoupled look-back by one warp: publish this tile's aggregate, sum the
@@ -219,13 +232,17 @@ __device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64
     return excl;
 }
 
-template <class Pol>
-__global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol) {
+// A policy decides the arcs of a slab in three steps, so that the loads of all
+// CI slabs of a warp are in flight together: load() issues the loads that need
+// only the arc (x, y) at p, load2() those that depend on them, keep() decides.
+// kW: the launch carries weights (read from a.w when present, written to
+// a.w_out; a policy may set the weight of a kept arc).
+template <class Pol, bool kW>
+__global__ void __launch_bounds__(CW * 32, 4) compact_kernel(CompactArgs a, Pol pol) {
     __shared__ uint32_t s_mask[CW][CI];
     __shared__ int s_slab_excl[CW][CI];
     __shared__ int s_warp_cnt[CW];
     __shared__ int s_warp_excl[CW + 1];
-    __shared__ int s_or_cnt[CW];
     __shared__ long long s_tile_excl;
     __shared__ long long s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -240,48 +257,61 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
         const int64_t t1 = min(t0 + (int64_t)kTile, a.nnz);
         const int64_t wbase = t0 + (int64_t)warp * kWarpSpan;
 
-        int64_t or_run = 0;
-        if constexpr (Pol::kOrPrefix) {
-            uint32_t wd = 0;
-            if (lane < CI && wbase + lane * 32 < t1) wd = __ldg(pol.fwd_bits + (wbase >> 5) + lane);
-            const int cnt = warp_sum(__popc(wd));
-            if (lane == 0) s_or_cnt[warp] = cnt;
-            __syncthreads();
-            int64_t base = pol.tile_or_excl(tile);
-            for (int i = 0; i < warp; ++i) base += s_or_cnt[i];
-            or_run = base;
-        }
-
+        // independent loads first: the warp's first row, its slabs' columns
+        // (and weights), their forward bits
+        const int64_t r0 = (wbase < t1) ? (int64_t)__ldg(a.chunk_row + wbase / kWarpSpan) : 0;
         uint32_t ys[CI];
         float ws[CI];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            const int64_t sbase = wbase + k * 32;
+            const int64_t pe = min(sbase + lane, t1 - 1);
+            ys[k] = sbase < t1 ? __ldg(a.col + pe) : 0u;
+            if constexpr (kW) ws[k] = (sbase < t1 && a.w) ? __ldg(a.w + pe) : 0.f;
+        }
+        uint32_t or_words = 0;  // lane k < CI: forward bits of slab k
+        int64_t or_run = 0;     // forward arcs before the warp's span
+        if constexpr (Pol::kOrPrefix) {
+            const int64_t w0 = t0 >> 5, ww = wbase >> 5;
+            if (lane < CI && ww + lane < ((t1 + 31) >> 5)) or_words = __ldg(pol.fwd_bits + ww + lane);
+            // the tile's earlier warps hold at most (CW - 1) * CI words
+            static_assert((CW - 1) * CI <= 64, "two words per lane");
+            const int64_t wa = w0 + lane, wb = w0 + 32 + lane;
+            const int cnt = (wa < ww ? __popc(__ldg(pol.fwd_bits + wa)) : 0) +
+                            (wb < ww ? __popc(__ldg(pol.fwd_bits + wb)) : 0);
+            or_run = pol.tile_or_excl(tile) + warp_sum(cnt);
+        }
+
+        uint32_t xs[CI];
+        warp_rows<CI>(a.off, a.n, r0, wbase, t1, xs);
+
+        typename Pol::Pre pre[CI];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            SlabCtx sc{0u, 0};
+            if constexpr (Pol::kOrPrefix) {
+                sc.or_word = __shfl_sync(kFull, or_words, k);
+                sc.or_base = or_run;
+                or_run += __popc(sc.or_word);
+            }
+            pre[k] = pol.load(xs[k], ys[k], wbase + k * 32 + lane, sc);
+        }
+#pragma unroll
+        for (int k = 0; k < CI; ++k) pol.load2(pre[k]);
+
         uint32_t masks[CI];
-        int wcnt = 0;
-        int64_t cursor = (wbase < t1) ? (int64_t)__ldg(a.chunk_row + wbase / kWarpSpan) : 0;
 #pragma unroll
         for (int k = 0; k < CI; ++k) {
             const int64_t sbase = wbase + k * 32;
             masks[k] = 0;
-            ys[k] = 0;
-            ws[k] = 0.f;
             if (sbase < t1) {  // warp-uniform
                 const int64_t p = sbase + lane;
-                const bool valid = p < t1;
-                const int q = valid ? lane : (int)(t1 - 1 - sbase);
-                const int64_t x = warp_row(a.off, a.n, cursor, sbase, q);
-                const int64_t pe = sbase + q;
-                const uint32_t y = __ldg(a.col + pe);
-                float wv = a.w ? __ldg(a.w + pe) : 0.f;
-                SlabCtx sc{0u, 0};
-                if constexpr (Pol::kOrPrefix) {
-                    sc.or_word = __ldg(pol.fwd_bits + (sbase >> 5));
-                    sc.or_base = or_run;
-                    or_run += __popc(sc.or_word);
-                }
-                const bool keep = valid && pol.keep(x, y, p, sc, wv);
+                float wv = 0.f;
+                if constexpr (kW) wv = ws[k];
+                const bool keep = p < t1 && pol.keep(pre[k], xs[k], ys[k], p, wv);
+                if constexpr (kW) ws[k] = wv;
                 masks[k] = __ballot_sync(kFull, keep);
-                if constexpr (Pol::kMapCol) ys[k] = pol.map_col(x, y); else ys[k] = y;
-                ws[k] = wv;
-                wcnt += __popc(masks[k]);
+                if constexpr (Pol::kMapCol) ys[k] = pol.map_col(pre[k], xs[k], ys[k]);
                 if (a.keep_bits != nullptr && lane == 0) a.keep_bits[sbase >> 5] = masks[k];
             }
         }
@@ -317,7 +347,7 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
             if ((masks[k] >> lane) & 1u) {
                 const int64_t g = wexcl + s_slab_excl[warp][k] + __popc(masks[k] & lt);
                 a.col_out[g] = ys[k];
-                if (a.w_out) a.w_out[g] = ws[k];
+                if constexpr (kW) a.w_out[g] = ws[k];
             }
         }
         // new row offsets for the rows whose start lies in this tile
@@ -329,6 +359,8 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
             int local;
             if (q >= tlen) {
                 local = s_warp_excl[CW];
+            } else if (q < 0) {  // only with offsets that are not non-decreasing
+                local = 0;
             } else {
                 const int wq = (int)(q / kWarpSpan), kq = (int)((q >> 5) % CI), lq = (int)(q & 31);
                 local = s_warp_excl[wq] + s_slab_excl[wq][kq] + __popc(s_mask[wq][kq] & ((1u << lq) - 1u));
@@ -343,12 +375,14 @@ __global__ void __launch_bounds__(CW * 32) compact_kernel(CompactArgs a, Pol pol
 struct UniformPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = false;
+    struct Pre {};
     uint32_t k0, k1;
     unsigned long long tp;
+    __device__ __forceinline__ Pre load(uint32_t, uint32_t, int64_t, const SlabCtx &) const { return Pre{}; }
+    __device__ __forceinline__ void load2(Pre &) const {}
     // random_uniform(E e): the edge stays iff its draw is below floor(p 2^32)
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
-        const uint32_t ux = (uint32_t)x;
-        const uint4 r = philox4x32_10(make_uint4(min(ux, y), max(ux, y), 0u, kTagEdge), k0, k1);
+    __device__ __forceinline__ bool keep(const Pre &, uint32_t x, uint32_t y, int64_t, float &) const {
+        const uint4 r = philox4x32_10(make_uint4(min(x, y), max(x, y), 0u, kTagEdge), k0, k1);
         return (unsigned long long)r.x < tp;
     }
 };
@@ -356,19 +390,25 @@ struct UniformPol {
 struct SpectralPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = false;
+    struct Pre {
+        uint64_t dmin;
+    };
     const int64_t *off;
     uint32_t k0, k1;
     unsigned long long ty;  // floor(Y 2^32)
     float yf;               // Y rounded to float
     bool reweight;
-    // spectral_sparsify(E e): stays with probability min(1, Y / min(d_u, d_v)),
-    // i.e. iff r * min(d_u, d_v) < Y 2^32; kept edges may take weight 1/p_uv.
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &w) const {
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
         const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
         const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
-        const uint64_t dmin = dx < dy ? dx : dy;
-        const uint32_t ux = (uint32_t)x;
-        const uint4 r = philox4x32_10(make_uint4(min(ux, y), max(ux, y), 0u, kTagEdge), k0, k1);
+        return Pre{dx < dy ? dx : dy};
+    }
+    __device__ __forceinline__ void load2(Pre &) const {}
+    // spectral_sparsify(E e): stays with probability min(1, Y / min(d_u, d_v)),
+    // i.e. iff r * min(d_u, d_v) < Y 2^32; kept edges may take weight 1/p_uv.
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &w) const {
+        const uint64_t dmin = pr.dmin;
+        const uint4 r = philox4x32_10(make_uint4(min(x, y), max(x, y), 0u, kTagEdge), k0, k1);
         if (reweight) w = (dmin * 4294967296ull <= ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), yf);
         return (unsigned long long)r.x * dmin < ty;
     }
@@ -388,39 +428,62 @@ __global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_
 struct OrientPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = false;
+    struct Pre {
+        uint32_t sxy;  // saturated degrees of x (high half) and y (low half)
+    };
     const int64_t *off;
     const uint16_t *deg16;  // min(d, 65535)
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
+        return Pre{((uint32_t)__ldg(deg16 + x) << 16) | (uint32_t)__ldg(deg16 + y)};
+    }
+    __device__ __forceinline__ void load2(Pre &) const {}
     // x precedes y in the degree order (d_x, x) < (d_y, y).  Unequal saturated
     // degrees order the vertices as their degrees do; equal ones below 65535
     // are the degrees themselves; only two saturated ones need the offsets.
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
-        const uint32_t sx = __ldg(deg16 + x), sy = __ldg(deg16 + y);
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &) const {
+        const uint32_t sx = pr.sxy >> 16, sy = pr.sxy & 0xFFFFu;
         if (sx != sy) return sx < sy;
-        if (sx < 65535u) return (uint32_t)x < y;
+        if (sx < 65535u) return x < y;
         const int64_t dx = __ldg(off + x + 1) - __ldg(off + x);
         const int64_t dy = __ldg(off + y + 1) - __ldg(off + y);
-        return dx < dy || (dx == dy && (uint32_t)x < y);
+        return dx < dy || (dx == dy && x < y);
     }
 };
 
 struct MaskPol {
     static constexpr bool kOrPrefix = true;
     static constexpr bool kMapCol = false;
+    struct Pre {
+        uint32_t idx;  // E+ index of the arc's edge, then its deletion flag
+    };
     const uint32_t *fwd_bits;
     const unsigned long long *or_status;
-    const uint2 *inl;          // the reverse list (reverse_list)
+    const uint2 *inl;  // the reverse list (reverse_list)
     const uint8_t *del;
+    int64_t ninl;      // entries of inl (>= 1)
+    int64_t ndel;      // entries of del (>= 1)
     __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const {
         return tile == 0 ? 0 : (int64_t)(ld_volatile_u64(or_status + tile - 1) & kStVal);
     }
-    // the arc stays iff its edge's oriented arc carries no deletion flag: a
-    // forward arc's E+ index is the running prefix of forward arcs; a reverse
-    // arc's rank p - (forward arcs before p) finds its E+ index in the reverse list
-    __device__ __forceinline__ bool keep(int64_t, uint32_t, int64_t p, const SlabCtx &s, float &) const {
+    // A forward arc's E+ index is the running prefix of forward arcs; a reverse
+    // arc's rank p - (forward arcs before p) finds it in the reverse list.  The
+    // indices are clamped to the arrays: an arc whose answer is not used (past
+    // the end, or of a batch graph without a triangle kernel, whose reverse
+    // list entries are never written) still reads inside them.
+    __device__ __forceinline__ Pre load(uint32_t, uint32_t, int64_t p, const SlabCtx &s) const {
         const int lane = (int)(p & 31);
-        const int64_t fwd_before = s.or_base + __popc(s.or_word & lanemask_lt());
-        if ((s.or_word >> lane) & 1u) return __ldg(del + fwd_before) == 0;
-        return __ldg(del + __ldg(&inl[p - fwd_before].y)) == 0;
+        const int64_t fwd_before = s.or_base + __popc(s.or_word & ((1u << lane) - 1u));
+        int64_t idx = fwd_before;
+        if (!((s.or_word >> lane) & 1u)) {
+            const int64_t r = min(max(p - fwd_before, (int64_t)0), ninl - 1);
+            idx = __ldg(&inl[r].y);
+        }
+        return Pre{(uint32_t)min(idx, ndel - 1)};
+    }
+    __device__ __forceinline__ void load2(Pre &pr) const { pr.idx = __ldg(del + pr.idx); }
+    // the arc stays iff its edge's oriented arc carries no deletion flag
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t, float &) const {
+        return pr.idx == 0;
     }
 };
 
@@ -474,42 +537,48 @@ __global__ void __launch_bounds__(256, 4) reverse_list_kernel(
             int cnt = (wa < s0 ? __popc(__ldg(fwd_bits + wa)) : 0) + (wb < s0 ? __popc(__ldg(fwd_bits + wb)) : 0);
             fwd_run += warp_sum(cnt);
         }
-        int64_t cursor = (int64_t)__ldg(chunk_row + ((s0 << 5) / kWarpSpan));
+        // independent loads first: the slabs' forward bits and columns
+        const int64_t sb0 = s0 << 5;
+        const int64_t r0 = (int64_t)__ldg(chunk_row + sb0 / kWarpSpan);  // a row at or before arc sb0
+        uint32_t fws[kRevK];
 #pragma unroll
         for (int k = 0; k < kRevK; ++k) {
-            const int64_t sbase = (s0 + k) << 5;
-            need[k] = false;
-            base[k] = 0;
-            len[k] = 0;
-            xs[k] = 0;
-            ys[k] = 0;
-            rank[k] = 0;
+            const int64_t sbase = sb0 + k * 32;
+            fws[k] = sbase < nnz ? __ldg(fwd_bits + (sbase >> 5)) : 0u;
+            ys[k] = sbase < nnz ? __ldg(col + min(sbase + lane, nnz - 1)) : 0u;
+        }
+        warp_rows<kRevK>(off, n, r0, sb0, nnz, xs);
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
+            const int64_t sbase = sb0 + k * 32;
+            const uint32_t fw = fws[k];
+            rank[k] = sbase + lane - (fwd_run + __popc(fw & lanemask_lt()));
+            fwd_run += __popc(fw);
+            // in a batch, graphs without a triangle kernel have no E+ arcs to look up
+            const bool tri = batch.params == nullptr ||
+                             __ldg(&batch.params[__ldg(batch.vgid + xs[k])].kernel) >= (int)SG_TR_RANDOM;
+            need[k] = sbase + lane < nnz && tri && !((fw >> lane) & 1u);
+        }
+        int64_t dxs[kRevK];
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
+            const uint32_t y = need[k] ? ys[k] : 0u, x = need[k] ? xs[k] : 0u;
+            base[k] = __ldg(offp + y);
+            len[k] = (int)(__ldg(offp + y + 1) - base[k]);
+            dxs[k] = __ldg(offp + x + 1) - __ldg(offp + x);
+        }
+#pragma unroll
+        for (int k = 0; k < kRevK; ++k) {
             vlo[k] = 0;
             vhi[k] = (uint32_t)n;
-            if (sbase < nnz) {  // warp-uniform
-                const bool valid = sbase + lane < nnz;
-                const int q = valid ? lane : (int)(nnz - 1 - sbase);
-                const int64_t x = warp_row(off, n, cursor, sbase, q);
-                const uint32_t fw = __ldg(fwd_bits + (sbase >> 5));
-                rank[k] = sbase + lane - (fwd_run + __popc(fw & lanemask_lt()));
-                fwd_run += __popc(fw);
-                // in a batch, graphs without a triangle kernel have no E+ arcs to look up
-                const bool tri = batch.params == nullptr ||
-                                 __ldg(&batch.params[__ldg(batch.vgid + x)].kernel) >= (int)SG_TR_RANDOM;
-                if (valid && tri && !((fw >> lane) & 1u)) {
-                    const uint32_t y = __ldg(col + sbase + q);
-                    base[k] = __ldg(offp + y);
-                    len[k] = (int)(__ldg(offp + y + 1) - base[k]);
-                    xs[k] = (uint32_t)x;
-                    ys[k] = y;
-                    need[k] = true;
-                    // the work model of arc y->x: d+(y) streamed against d+(x)
-                    const int64_t dx = __ldg(offp + x + 1) - __ldg(offp + x);
-                    const int64_t dy = len[k];
-                    work += (unsigned long long)(dx < dy ? dx : dy);
-                    fwd += (unsigned long long)dx;
-                    head += dy < dx ? 1ull : 0ull;
-                }
+            if (need[k]) {
+                // the work model of arc y->x: d+(y) streamed against d+(x)
+                const int64_t dx = dxs[k], dy = len[k];
+                work += (unsigned long long)(dx < dy ? dx : dy);
+                fwd += (unsigned long long)dx;
+                head += dy < dx ? 1ull : 0ull;
+            } else {
+                len[k] = 0;
             }
         }
         // lockstep narrowing until every window [base, base + len] holds at
@@ -596,12 +665,13 @@ sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
 
 
 // ------------------------------------------------------------------ driver
-template <class Pol>
+template <class Pol, bool kW>
 static int blocks_per_sm() {
     static int cached = -1;
     if (cached < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, compact_kernel<Pol>, CW * 32, 0) != cudaSuccess || b < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, compact_kernel<Pol, kW>, CW * 32, 0) != cudaSuccess ||
+            b < 1)
             b = 1;
         cached = b;
     }
@@ -636,11 +706,16 @@ static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Po
     a.keep_bits = keep_bits;
     a.spin_limit = c->scan_hold ? c->scan_hold : kSpinLimit;
     a.hold_first = c->scan_hold != 0;
-    const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, blocks_per_sm<Pol>()) : blocks_per_sm<Pol>();
+    const bool wt = w_out != nullptr;
+    const int cap = wt ? blocks_per_sm<Pol, true>() : blocks_per_sm<Pol, false>();
+    const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, cap) : cap;
     const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * per_sm);
     {
         SG_LAUNCH(c, name);
-        compact_kernel<Pol><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
+        if (wt)
+            compact_kernel<Pol, true><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
+        else
+            compact_kernel<Pol, false><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -770,7 +845,8 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
     sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
     if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
     if (st == SG_OK) {
-        MaskPol pol{o.fwd_bits, o.status, o.inl, del};
+        MaskPol pol{o.fwd_bits, o.status, o.inl, del, std::max<int64_t>(g->nnz - o.m, 1),
+                    std::max<int64_t>(o.m, 1)};
         st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_trmask");
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
@@ -791,39 +867,55 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
 struct BatchOrientPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = false;
+    struct Pre {
+        uint32_t g;  // the graph of x
+        int64_t dx, dy;
+    };
     const int64_t *off;
     BatchDev b;
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
+        return Pre{__ldg(b.vgid + x), __ldg(off + x + 1) - __ldg(off + x), __ldg(off + y + 1) - __ldg(off + y)};
+    }
+    __device__ __forceinline__ void load2(Pre &) const {}
     // only graphs compressed by a triangle kernel need E+
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
-        const int kern = __ldg(&b.params[__ldg(b.vgid + x)].kernel);
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &) const {
+        const int kern = __ldg(&b.params[pr.g].kernel);
         if (kern < (int)SG_TR_RANDOM) return false;
-        const int64_t dx = __ldg(off + x + 1) - __ldg(off + x);
-        const int64_t dy = __ldg(off + y + 1) - __ldg(off + y);
-        return dx < dy || (dx == dy && (uint32_t)x < y);
+        return pr.dx < pr.dy || (pr.dx == pr.dy && x < y);
     }
 };
 
 struct BatchFinalPol {
     static constexpr bool kOrPrefix = true;
     static constexpr bool kMapCol = true;
+    struct Pre {
+        MaskPol::Pre mp;
+        uint32_t g;  // the graph of x
+        uint64_t dmin;
+    };
     const int64_t *off;
     BatchDev b;
     MaskPol mask;
     const uint32_t *fwd_bits;  // = mask.fwd_bits (read directly by the tile prologue)
     __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const { return mask.tile_or_excl(tile); }
-    __device__ __forceinline__ uint32_t map_col(int64_t x, uint32_t y) const {
-        return y - (uint32_t)__ldg(&b.params[__ldg(b.vgid + x)].vbase);
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t p, const SlabCtx &s) const {
+        const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
+        const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
+        return Pre{mask.load(x, y, p, s), __ldg(b.vgid + x), dx < dy ? dx : dy};
     }
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t p, const SlabCtx &s, float &w) const {
-        const BatchParam &P = b.params[__ldg(b.vgid + x)];
+    __device__ __forceinline__ void load2(Pre &pr) const { mask.load2(pr.mp); }
+    __device__ __forceinline__ uint32_t map_col(const Pre &pr, uint32_t, uint32_t y) const {
+        return y - (uint32_t)__ldg(&b.params[pr.g].vbase);
+    }
+    // a graph's own kernel decides its arcs; a triangle kernel's through the mask
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t p, float &w) const {
+        const BatchParam &P = b.params[pr.g];
         const int kern = P.kernel;
-        if (kern >= (int)SG_TR_RANDOM) return mask.keep(x, y, p, s, w);
+        if (kern >= (int)SG_TR_RANDOM) return mask.keep(pr.mp, x, y, p, w);
         const uint32_t lx = (uint32_t)(x - P.vbase), ly = (uint32_t)(y - P.vbase);
         const uint4 r = philox4x32_10(make_uint4(min(lx, ly), max(lx, ly), 0u, kTagEdge), P.k0, P.k1);
         if (kern == (int)SG_UNIFORM) return (unsigned long long)r.x < P.tp;
-        const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
-        const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
-        const uint64_t dmin = dx < dy ? dx : dy;
+        const uint64_t dmin = pr.dmin;
         if (P.reweight) w = (dmin * 4294967296ull <= P.ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), P.yf);
         return (unsigned long long)r.x * dmin < P.ty;
     }
@@ -841,7 +933,10 @@ sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented 
                       unsigned long long *status, int grid_per_sm) {
     // the reverse arcs of graphs without a triangle kernel are not in the
     // reverse list (BatchFinalPol decides those arcs itself)
-    BatchFinalPol pol{u->off, b, MaskPol{o.fwd_bits, o.status, o.inl, del}, o.fwd_bits};
+    // (its reverse list has room for every arc of the union, del for its m edges)
+    BatchFinalPol pol{u->off, b,
+                      MaskPol{o.fwd_bits, o.status, o.inl, del, std::max<int64_t>(u->nnz, 1), std::max<int64_t>(o.m, 1)},
+                      o.fwd_bits};
     return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, nullptr, status, "compact_final",
                        grid_per_sm);
 }
@@ -929,12 +1024,19 @@ __global__ void __launch_bounds__(256) lowdeg_ids_kernel(const int64_t *__restri
 struct LowDegPol {
     static constexpr bool kOrPrefix = false;
     static constexpr bool kMapCol = true;
+    struct Pre {
+        uint32_t nx, ny;  // new ids of x and y
+    };
     const uint32_t *new_id;
-    // an arc stays iff both of its ends stay; its head is renumbered
-    __device__ __forceinline__ bool keep(int64_t x, uint32_t y, int64_t, const SlabCtx &, float &) const {
-        return __ldg(new_id + x) != kNoVertex && __ldg(new_id + y) != kNoVertex;
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
+        return Pre{__ldg(new_id + x), __ldg(new_id + y)};
     }
-    __device__ __forceinline__ uint32_t map_col(int64_t, uint32_t y) const { return __ldg(new_id + y); }
+    __device__ __forceinline__ void load2(Pre &) const {}
+    // an arc stays iff both of its ends stay; its head is renumbered
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t, float &) const {
+        return pr.nx != kNoVertex && pr.ny != kNoVertex;
+    }
+    __device__ __forceinline__ uint32_t map_col(const Pre &pr, uint32_t, uint32_t) const { return pr.ny; }
 };
 
 // off'[new_id[v]] = off_c[v] for every kept row v; off'[n'] = off_c[n]
@@ -1137,9 +1239,9 @@ sg_status noalloc_uniform(int device, void *cuda_stream, int64_t n, int64_t nnz,
     a.hold_first = 0;
     UniformPol pol{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), prob_threshold(p)};
     int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<UniformPol>, CW * 32, 0));
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<UniformPol, false>, CW * 32, 0));
     const int64_t grid = std::min<int64_t>(num_tiles, (int64_t)num_sms * std::max(per_sm, 1));
-    compact_kernel<UniformPol><<<(unsigned)grid, CW * 32, 0, stream>>>(a, pol);
+    compact_kernel<UniformPol, false><<<(unsigned)grid, CW * 32, 0, stream>>>(a, pol);
     SG_CUDA(cudaGetLastError());
     int64_t count = 0;
     int code = 0;

@@ -71,6 +71,26 @@ def test_empty_vertex_set(sg, ctx):
 
 
 # ------------------------------------------------- R-MAT scale 14 (workload)
+def _sparse_rows(n, m, seed):
+    """n vertices, m random edges: most rows empty, the rest of degree 1-3."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, n, size=m)
+    b = rng.integers(0, n, size=m)
+    keep = a != b
+    return gg.csr_from_edges(n, torch.from_numpy(a[keep]), torch.from_numpy(b[keep]))
+
+
+@pytest.mark.parametrize("kern", KERNELS)
+def test_sparse_rows_bit_exact(sg, ctx, kern):
+    # a 256-arc warp span holds well over 32 row starts and long runs of empty
+    # rows, so every compaction's row search takes several batches of starts,
+    # and tiles begin and end inside runs of empty rows
+    for n, m, seed in ((200_000, 3_000, 1), (20_000, 9_000, 2), (4_100, 4_100, 3)):
+        g = _sparse_rows(n, m, seed)
+        for p, s in ((0.5, 7), (1.0, 8)):
+            _same(sg, ctx, g, kern, p, s)
+
+
 @pytest.fixture(scope="module")
 def rmat14():
     return gg.rmat(14, 16, seed=1)
