@@ -342,16 +342,16 @@ sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg
  * The input must be a valid symmetric CSR as defined at the top of this
  * header; the call checks only that off[0] = 0 and off[n] = nnz
  * (SG_ERR_INVALID_GRAPH otherwise).
- * Scratch lives in one fixed device array inside the library (about 3 MB per
+ * Scratch lives in one fixed device array inside the library (about 23 MB per
  * GPU that loads it, held until the process exits), which caps the input at
  * nnz <= 134217728 arcs; larger inputs return SG_ERR_UNSUPPORTED.
  * The first call on a device looks up that array's device address and keeps
  * it for the life of the process (a cudaDeviceReset of that device makes the
  * kept address stale); make the first call before any stream capture.  The
  * call synchronises cuda_stream and leaves the caller's current device as it
- * found it.  All calls share the one array: calls that overlap on the GPU
- * (different streams, threads or processes sharing the library) race and
- * must be serialised by the caller.  No context is needed; errors are
+ * found it.  All calls of a process share the one array on a device: calls
+ * that overlap on the GPU (different streams or threads of that process) race
+ * and must be serialised by the caller.  No context is needed; errors are
  * reported as by every other entry point (sg_last_error). */
 sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz, const int64_t *off,
                                       const uint32_t *col, double p, uint64_t seed, int64_t *off_out,

@@ -87,7 +87,8 @@ struct Batch {
     RowMaps rm;
     Oriented o;
     uint8_t *del = nullptr;
-    unsigned long long *st_orient = nullptr, *st_final = nullptr;
+    unsigned long long *scan = nullptr;  // chunk-scan status words (orientation, then output)
+    CompactScratch final_cs;              // the output compaction's keep masks and chunk prefixes
     BatchTri bt;
     int64_t *off_c = nullptr;      // union offsets after compaction
     int64_t *out_off = nullptr;    // per-graph offsets, n_g + 1 each
@@ -113,7 +114,7 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
     } else {
         st = fill_row_maps(c, &b->u, b->rm);
         if (st != SG_OK) return st;
-        st = batch_orient(c, &b->u, b->rm, dev, b->o.w != nullptr, &b->o, b->st_orient, t.compact_per_sm);
+        st = batch_orient(c, &b->u, b->rm, dev, b->o.w != nullptr, &b->o, b->scan, t.compact_per_sm);
         if (st != SG_OK) return st;
         st = reverse_list(c, &b->u, b->rm, b->o, b->bt.inl, dev);
         if (st != SG_OK) return st;
@@ -124,7 +125,7 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
         st = batch_tr_mark(c, &b->u, b->o, dev, bt, b->del);
         if (st != SG_OK) return st;
         st = batch_final(c, &b->u, b->rm, b->o, dev, b->del, b->off_c, b->out_col, b->u.w, b->out_w,
-                         b->st_final, t.compact_per_sm);
+                         b->final_cs, t.compact_per_sm);
         if (st != SG_OK) return st;
     }
     const int threads = 256;
@@ -323,7 +324,6 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
     // per-call scratch
     const int64_t m = at / 2;
     if (st == SG_OK) {
-        b->rm.num_tiles = (at + kTile - 1) / kTile;
         b->rm.num_chunks = (at + kWarpSpan - 1) / kWarpSpan;
         Oriented &o = b->o;
         o.n = nt;
@@ -332,9 +332,11 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
         if (st == SG_OK) st = dalloc(c, (void **)&o.col, sizeof(uint32_t) * (size_t)std::max<int64_t>(at, 1));
         if (st == SG_OK && weighted) st = dalloc(c, (void **)&o.w, sizeof(float) * (size_t)std::max<int64_t>(at, 1));
         if (st == SG_OK) st = dalloc(c, (void **)&o.fwd_bits, sizeof(uint32_t) * (size_t)(b->rm.num_chunks * CI + 1));
-        if (st == SG_OK) st = dalloc(c, (void **)&o.status, sizeof(unsigned long long) * (size_t)(b->rm.num_tiles + 1));
-        b->st_orient = o.status;
-        if (st == SG_OK) st = dalloc(c, (void **)&b->st_final, sizeof(unsigned long long) * (size_t)(b->rm.num_tiles + 1));
+        if (st == SG_OK) st = dalloc(c, (void **)&o.fwd_excl, sizeof(int64_t) * (size_t)(b->rm.num_chunks + 1));
+        if (st == SG_OK)
+            st = dalloc(c, (void **)&b->scan,
+                        sizeof(unsigned long long) * (size_t)compact_scan_words(b->rm.num_chunks));
+        if (st == SG_OK) st = alloc_compact_scratch(c, b->rm.num_chunks, true, &b->final_cs);
         if (st == SG_OK) st = dalloc(c, (void **)&b->del, (size_t)std::max<int64_t>(m, 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->off_c, sizeof(int64_t) * (size_t)(nt + 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->out_off, sizeof(int64_t) * (size_t)(nt + count));
@@ -357,10 +359,9 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
         st = build_row_maps(c, &u, &rm);
         if (st == SG_OK) {
             b->rm.chunk_row = rm.chunk_row;
-            b->rm.tile_vlo = rm.tile_vlo;
         }
         if (st == SG_OK)
-            st = batch_orient(c, &u, b->rm, BatchDev{b->d_params, b->vgid}, false, &b->o, b->st_orient, 0);
+            st = batch_orient(c, &u, b->rm, BatchDev{b->d_params, b->vgid}, false, &b->o, b->scan, 0);
         if (st == SG_OK) st = batch_tr_prepare(c, &u, b->o, &b->bt);
         if (st == SG_OK) b->o.inl = b->bt.inl;  // the mask resolution reads the batch's reverse list
         if (st == SG_OK) st = check_device_error(c);
@@ -381,8 +382,9 @@ void sg_batch_free(sg_batch *b) {
         (void)cudaSetDevice(b->u.device);
         if (b->exec) cudaGraphExecDestroy(b->exec);
         for (void *p : {(void *)b->u.off, (void *)b->u.col, (void *)b->u.w, (void *)b->vgid, (void *)b->d_params,
-                        (void *)b->rm.chunk_row, (void *)b->rm.tile_vlo, (void *)b->o.off, (void *)b->o.col,
-                        (void *)b->o.w, (void *)b->o.fwd_bits, (void *)b->o.status, (void *)b->st_final,
+                        (void *)b->rm.chunk_row, (void *)b->o.off, (void *)b->o.col, (void *)b->o.w,
+                        (void *)b->o.fwd_bits, (void *)b->o.fwd_excl, (void *)b->scan, (void *)b->final_cs.keep,
+                        (void *)b->final_cs.cexcl, (void *)b->final_cs.scan,
                         (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->bt.din,
                         (void *)b->bt.inl, (void *)b->off_c,
                         (void *)b->out_off, (void *)b->out_col, (void *)b->out_w, (void *)b->d_info})
@@ -403,7 +405,8 @@ void sg_batch_free(sg_batch *b) {
     free_row_maps(c, &b->rm);
     b->o.inl = nullptr;  // owned by b->bt, freed below
     free_oriented(c, &b->o);
-    dfree(c, b->st_final);
+    dfree(c, b->scan);
+    free_compact_scratch(c, &b->final_cs);
     dfree(c, b->del);
     batch_tr_free(c, &b->bt);
     dfree(c, b->off_c);

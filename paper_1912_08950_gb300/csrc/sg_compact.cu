@@ -1,23 +1,30 @@
-// Arc-tiled stream compaction of a symmetric CSR with a single-pass
-// decoupled-lookback prefix scan (Merrill & Garland, "Single-pass parallel
-// prefix scan with decoupled look-back", NVIDIA TR 2016), written without CUB.
+// Arc compaction of a symmetric CSR in two passes over 256-arc chunks.
 //
-// One pass over the arc array decides, for every arc (x, y), whether it stays,
-// scatters the kept column ids (and weights) to their final positions and
-// writes the new row offsets: off'[v] = number of kept arcs before off[v].
-// Rows stay sorted because arcs keep their order.  The same engine serves
+// For every arc (x, y) a policy decides whether it stays; the kept column ids
+// (and weights) move to their final positions and the new row offsets are
+// off'[v] = number of kept arcs before off[v].  Rows stay sorted because arcs
+// keep their order.  The same engine serves
 //   * the edge kernels of Listing 1 (random_uniform, spectral_sparsify),
 //   * the degree-ordered orientation E+ that triangle listing needs (Sec. 4.3:
 //     O(m^{3/2}) listing), and
 //   * the final mask resolution of the Triangle p-1-Reduction kernels, which
 //     replaces the paper's "atomic SG.del(e)" by per-edge flags read here.
 //
-// Layout: a tile is kTile consecutive arcs handled by one CTA; warp w owns
-// arcs [t0 + w*kWarpSpan, +kWarpSpan) as CI slabs of 32 consecutive arcs, one
-// per lane, so every global read of col[] is a 128-byte coalesced access and
-// ballots give the slab's keep mask directly.  Tiles are claimed through an
-// atomic ticket, so a CTA only ever waits on tiles already owned by running
-// CTAs; every wait is bounded and reports a device error instead of hanging.
+// Layout: a chunk is kWarpSpan = 32 * CI consecutive arcs handled by one warp
+// as CI slabs of 32, one arc per lane, so every read of col[] is a 128-byte
+// coalesced access and a ballot gives a slab's keep mask.  The passes are
+//   decide  -- every warp decides its chunks on its own and writes their keep
+//              masks and kept counts (no barrier, no wait on other warps);
+//   scan    -- the exclusive prefix of the chunk counts, a single-pass scan
+//              with decoupled look-back (Merrill & Garland, "Single-pass
+//              parallel prefix scan with decoupled look-back", NVIDIA TR
+//              2016; written here without CUB) over tiles of chunks;
+//   scatter -- every warp moves the kept arcs of its chunks to the chunk's
+//              prefix plus their rank in the keep masks;
+//   offsets -- one thread per row: the chunk prefix of its first arc plus
+//              the kept arcs before it in that chunk's masks.
+// Only the short scan has waits between CTAs, and those are bounded: a wait
+// that runs out reports a device error instead of hanging.
 #include <climits>
 #include <mutex>
 #include <string>
@@ -45,98 +52,57 @@ static uint64_t scaled_threshold(double y) {
 }
 
 // --------------------------------------------------------------- row maps
-// chunk_row[c] = the row holding arc c*kWarpSpan; tile_vlo[t] = first row v
-// with off[v] >= t*kTile (tile_vlo[num_tiles] = n + 1).  One thread per row,
-// no searches: row v owns the chunk and tile starts that fall in its range.
+// chunk_row[c] = the row holding arc c * kWarpSpan.  One thread per row, no
+// searches: row v owns the chunk starts that fall in its range.
 __global__ void row_maps_kernel(const int64_t *__restrict__ off, int64_t n, uint32_t *__restrict__ chunk_row,
-                                int64_t num_chunks, int64_t *__restrict__ tile_vlo, int64_t num_tiles) {
+                                int64_t num_chunks) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
-        const int64_t b = off[v];
-        const int64_t a = (v == 0) ? -1 : off[v - 1];
-        for (int64_t t = (a < 0) ? 0 : a / kTile + 1; t < num_tiles && t * kTile <= b; ++t) tile_vlo[t] = v;
-        if (v < n) {
-            const int64_t e = off[v + 1];
-            for (int64_t c = (b + kWarpSpan - 1) / kWarpSpan; c < num_chunks && c * kWarpSpan < e; ++c)
-                chunk_row[c] = (uint32_t)v;
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) tile_vlo[num_tiles] = n + 1;
-}
-
-// Every entry of the row maps gets a value in range before row_maps_kernel
-// writes the ones a well-formed CSR defines: chunk rows 0, tile rows n + 1.
-// With malformed offsets (not non-decreasing) some entries are never written
-// by row_maps_kernel; pre-filled, they still keep every compaction access
-// inside the row range and the offset array.
-__global__ void prefill_row_maps_kernel(uint32_t *chunk_row, int64_t num_chunks, int64_t *tile_vlo,
-                                        int64_t num_tiles, int64_t n) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= num_tiles || i < num_chunks; i += stride) {
-        if (i < num_chunks) chunk_row[i] = 0;
-        if (i <= num_tiles) tile_vlo[i] = n + 1;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t b = off[v], e = off[v + 1];
+        for (int64_t c = b <= 0 ? 0 : (b + kWarpSpan - 1) / kWarpSpan; c < num_chunks && c * kWarpSpan < e; ++c)
+            chunk_row[c] = (uint32_t)v;
     }
 }
 
-static void prefill_row_maps(cudaStream_t stream, int num_sms, uint32_t *chunk_row, int64_t num_chunks,
-                             int64_t *tile_vlo, int64_t num_tiles, int64_t n) {
-    const int64_t items = std::max(num_chunks, num_tiles + 1);
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, (int64_t)num_sms * 16));
-    prefill_row_maps_kernel<<<(unsigned)blocks, 256, 0, stream>>>(chunk_row, num_chunks, tile_vlo, num_tiles, n);
+// Every entry of the row map gets a row in range before row_maps_kernel
+// writes the ones a well-formed CSR defines: with malformed offsets (not
+// non-decreasing) some entries are never written by row_maps_kernel, and the
+// pre-filled 0 still keeps every compaction access inside the row range.
+__global__ void prefill_row_maps_kernel(uint32_t *chunk_row, int64_t num_chunks) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < num_chunks; i += stride) chunk_row[i] = 0;
+}
+
+static void launch_row_maps(cudaStream_t stream, int num_sms, const int64_t *off, int64_t n, uint32_t *chunk_row,
+                            int64_t num_chunks) {
+    const int64_t pb = std::max<int64_t>(1, std::min<int64_t>((num_chunks + 255) / 256, (int64_t)num_sms * 16));
+    prefill_row_maps_kernel<<<(unsigned)pb, 256, 0, stream>>>(chunk_row, num_chunks);
+    const int64_t rb = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16));
+    row_maps_kernel<<<(unsigned)rb, 256, 0, stream>>>(off, n, chunk_row, num_chunks);
 }
 
 sg_status fill_row_maps(Ctx *c, const Graph *g, const RowMaps &rm) {
-    const int threads = 256;
-    const int64_t blocks = std::min<int64_t>((g->n + 1 + threads - 1) / threads, (int64_t)c->num_sms * 16);
     {
         SG_LAUNCH(c, "row_maps");
-        prefill_row_maps(c->stream, c->num_sms, rm.chunk_row, rm.num_chunks, rm.tile_vlo, rm.num_tiles, g->n);
-    }
-    {
-        SG_LAUNCH(c, "row_maps");
-        row_maps_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, c->stream>>>(
-            g->off, g->n, rm.chunk_row, rm.num_chunks, rm.tile_vlo, rm.num_tiles);
+        launch_row_maps(c->stream, c->num_sms, g->off, g->n, rm.chunk_row, rm.num_chunks);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
 
 sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm) {
-    rm->num_tiles = (g->nnz + kTile - 1) / kTile;
     rm->num_chunks = (g->nnz + kWarpSpan - 1) / kWarpSpan;
     sg_status st = dalloc(c, (void **)&rm->chunk_row, sizeof(uint32_t) * (size_t)(rm->num_chunks + 1));
-    if (st != SG_OK) return st;
-    st = dalloc(c, (void **)&rm->tile_vlo, sizeof(int64_t) * (size_t)(rm->num_tiles + 1));
     if (st != SG_OK) return st;
     return fill_row_maps(c, g, *rm);
 }
 
 void free_row_maps(Ctx *c, RowMaps *rm) {
     dfree(c, rm->chunk_row);
-    dfree(c, rm->tile_vlo);
     rm->chunk_row = nullptr;
-    rm->tile_vlo = nullptr;
 }
 
 // ------------------------------------------------------------ device parts
-struct CompactArgs {
-    const int64_t *off;
-    const uint32_t *col;
-    const float *w;
-    int64_t n, nnz, num_tiles;
-    const uint32_t *chunk_row;
-    const int64_t *tile_vlo;
-    int64_t *off_out;
-    uint32_t *col_out;
-    float *w_out;
-    unsigned long long *status;
-    unsigned int *ticket;
-    int *err;
-    uint32_t *keep_bits;  // optional: the keep mask of every 32-arc slab
-    uint32_t spin_limit;  // polls of a look-back wait before it gives up
-    int hold_first;       // test hook: tile 0 never publishes its prefix
-};
-
 struct SlabCtx {
     uint32_t or_word;  // forward-arc bits of this slab (mask resolution only)
     int64_t or_base;   // E+ index of the slab's first forward arc
@@ -232,164 +198,39 @@ __device__ int64_t tile_lookback(unsigned long long *status, int64_t tile, int64
     return excl;
 }
 
-// A policy decides the arcs of a slab in three steps, so that the loads of all
-// CI slabs of a warp are in flight together: load() issues the loads that need
-// only the arc (x, y) at p, load2() those that depend on them, keep() decides.
-// kW: the launch carries weights (read from a.w when present, written to
-// a.w_out; a policy may set the weight of a kept arc).
-template <class Pol, bool kW>
-__global__ void __launch_bounds__(CW * 32, 4) compact_kernel(CompactArgs a, Pol pol) {
-    __shared__ uint32_t s_mask[CW][CI];
-    __shared__ int s_slab_excl[CW][CI];
-    __shared__ int s_warp_cnt[CW];
-    __shared__ int s_warp_excl[CW + 1];
-    __shared__ long long s_tile_excl;
-    __shared__ long long s_tile;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
-
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(a.ticket, 1u);
-        __syncthreads();
-        const int64_t tile = s_tile;
-        if (tile >= a.num_tiles) break;
-        const int64_t t0 = tile * kTile;
-        const int64_t t1 = min(t0 + (int64_t)kTile, a.nnz);
-        const int64_t wbase = t0 + (int64_t)warp * kWarpSpan;
-
-        // independent loads first: the warp's first row, its slabs' columns
-        // (and weights), their forward bits
-        const int64_t r0 = (wbase < t1) ? (int64_t)__ldg(a.chunk_row + wbase / kWarpSpan) : 0;
-        uint32_t ys[CI];
-        float ws[CI];
-#pragma unroll
-        for (int k = 0; k < CI; ++k) {
-            const int64_t sbase = wbase + k * 32;
-            const int64_t pe = min(sbase + lane, t1 - 1);
-            ys[k] = sbase < t1 ? __ldg(a.col + pe) : 0u;
-            if constexpr (kW) ws[k] = (sbase < t1 && a.w) ? __ldg(a.w + pe) : 0.f;
-        }
-        uint32_t or_words = 0;  // lane k < CI: forward bits of slab k
-        int64_t or_run = 0;     // forward arcs before the warp's span
-        if constexpr (Pol::kOrPrefix) {
-            const int64_t w0 = t0 >> 5, ww = wbase >> 5;
-            if (lane < CI && ww + lane < ((t1 + 31) >> 5)) or_words = __ldg(pol.fwd_bits + ww + lane);
-            // the tile's earlier warps hold at most (CW - 1) * CI words
-            static_assert((CW - 1) * CI <= 64, "two words per lane");
-            const int64_t wa = w0 + lane, wb = w0 + 32 + lane;
-            const int cnt = (wa < ww ? __popc(__ldg(pol.fwd_bits + wa)) : 0) +
-                            (wb < ww ? __popc(__ldg(pol.fwd_bits + wb)) : 0);
-            or_run = pol.tile_or_excl(tile) + warp_sum(cnt);
-        }
-
-        uint32_t xs[CI];
-        warp_rows<CI>(a.off, a.n, r0, wbase, t1, xs);
-
-        typename Pol::Pre pre[CI];
-#pragma unroll
-        for (int k = 0; k < CI; ++k) {
-            SlabCtx sc{0u, 0};
-            if constexpr (Pol::kOrPrefix) {
-                sc.or_word = __shfl_sync(kFull, or_words, k);
-                sc.or_base = or_run;
-                or_run += __popc(sc.or_word);
-            }
-            pre[k] = pol.load(xs[k], ys[k], wbase + k * 32 + lane, sc);
-        }
-#pragma unroll
-        for (int k = 0; k < CI; ++k) pol.load2(pre[k]);
-
-        uint32_t masks[CI];
-#pragma unroll
-        for (int k = 0; k < CI; ++k) {
-            const int64_t sbase = wbase + k * 32;
-            masks[k] = 0;
-            if (sbase < t1) {  // warp-uniform
-                const int64_t p = sbase + lane;
-                float wv = 0.f;
-                if constexpr (kW) wv = ws[k];
-                const bool keep = p < t1 && pol.keep(pre[k], xs[k], ys[k], p, wv);
-                if constexpr (kW) ws[k] = wv;
-                masks[k] = __ballot_sync(kFull, keep);
-                if constexpr (Pol::kMapCol) ys[k] = pol.map_col(pre[k], xs[k], ys[k]);
-                if (a.keep_bits != nullptr && lane == 0) a.keep_bits[sbase >> 5] = masks[k];
-            }
-        }
-        if (lane == 0) {
-            int run = 0;
-#pragma unroll
-            for (int k = 0; k < CI; ++k) {
-                s_mask[warp][k] = masks[k];
-                s_slab_excl[warp][k] = run;
-                run += __popc(masks[k]);
-            }
-            s_warp_cnt[warp] = run;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            int agg = 0;
-            if (lane == 0) {
-                for (int i = 0; i < CW; ++i) {
-                    s_warp_excl[i] = agg;
-                    agg += s_warp_cnt[i];
-                }
-                s_warp_excl[CW] = agg;
-            }
-            agg = __shfl_sync(kFull, agg, 0);
-            const int64_t excl = tile_lookback(a.status, tile, agg, a.err, a.spin_limit, a.hold_first != 0);
-            if (lane == 0) s_tile_excl = excl;
-        }
-        __syncthreads();
-        const int64_t texcl = s_tile_excl;
-        const int64_t wexcl = texcl + s_warp_excl[warp];
-#pragma unroll
-        for (int k = 0; k < CI; ++k) {
-            if ((masks[k] >> lane) & 1u) {
-                const int64_t g = wexcl + s_slab_excl[warp][k] + __popc(masks[k] & lt);
-                a.col_out[g] = ys[k];
-                if constexpr (kW) a.w_out[g] = ws[k];
-            }
-        }
-        // new row offsets for the rows whose start lies in this tile
-        // (both in [0, n + 1] whatever the offsets: see prefill_row_maps)
-        const int64_t v0 = __ldg(a.tile_vlo + tile), v1 = __ldg(a.tile_vlo + tile + 1);
-        const int64_t tlen = t1 - t0;
-        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-            const int64_t q = __ldg(a.off + v) - t0;
-            int local;
-            if (q >= tlen) {
-                local = s_warp_excl[CW];
-            } else if (q < 0) {  // only with offsets that are not non-decreasing
-                local = 0;
-            } else {
-                const int wq = (int)(q / kWarpSpan), kq = (int)((q >> 5) % CI), lq = (int)(q & 31);
-                local = s_warp_excl[wq] + s_slab_excl[wq][kq] + __popc(s_mask[wq][kq] & ((1u << lq) - 1u));
-            }
-            a.off_out[v] = texcl + local;
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------- policies
+// A policy decides an arc in three steps, so that the loads of all CI slabs of
+// a warp are in flight together: load() issues the loads that need only the
+// arc (x, y) at position p, load2() those that depend on them, keep() decides.
+//   kNeedRow / kNeedCol: the decision reads x / y;
+//   kOrPrefix: it reads the orientation's forward bits and their prefix;
+//   kMapCol: the scatter stores map_col(y) instead of y;
+//   kReweight: the scatter may replace a kept arc's weight (weight(x, y, w)),
+//              when reweights() says so;
+//   kMinBlocks: CTAs of 256 threads per SM the decide pass is compiled for.
 struct UniformPol {
-    static constexpr bool kOrPrefix = false;
-    static constexpr bool kMapCol = false;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = false, kReweight = false;
+    static constexpr int kMinBlocks = 4;
     struct Pre {};
     uint32_t k0, k1;
     unsigned long long tp;
     __device__ __forceinline__ Pre load(uint32_t, uint32_t, int64_t, const SlabCtx &) const { return Pre{}; }
     __device__ __forceinline__ void load2(Pre &) const {}
     // random_uniform(E e): the edge stays iff its draw is below floor(p 2^32)
-    __device__ __forceinline__ bool keep(const Pre &, uint32_t x, uint32_t y, int64_t, float &) const {
+    __device__ __forceinline__ bool keep(const Pre &, uint32_t x, uint32_t y, int64_t) const {
         const uint4 r = philox4x32_10(make_uint4(min(x, y), max(x, y), 0u, kTagEdge), k0, k1);
         return (unsigned long long)r.x < tp;
     }
 };
 
+// 1/p_uv for an edge kept with probability p_uv = min(1, Y / dmin)
+__device__ __forceinline__ float spectral_weight(uint64_t dmin, unsigned long long ty, float yf) {
+    return (dmin * 4294967296ull <= ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), yf);
+}
+
 struct SpectralPol {
-    static constexpr bool kOrPrefix = false;
-    static constexpr bool kMapCol = false;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = false, kReweight = true;
+    static constexpr int kMinBlocks = 4;
     struct Pre {
         uint64_t dmin;
     };
@@ -398,19 +239,25 @@ struct SpectralPol {
     unsigned long long ty;  // floor(Y 2^32)
     float yf;               // Y rounded to float
     bool reweight;
-    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
+    __device__ __forceinline__ uint64_t dmin(uint32_t x, uint32_t y) const {
         const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
         const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
-        return Pre{dx < dy ? dx : dy};
+        return dx < dy ? dx : dy;
+    }
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
+        return Pre{dmin(x, y)};
     }
     __device__ __forceinline__ void load2(Pre &) const {}
     // spectral_sparsify(E e): stays with probability min(1, Y / min(d_u, d_v)),
-    // i.e. iff r * min(d_u, d_v) < Y 2^32; kept edges may take weight 1/p_uv.
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &w) const {
-        const uint64_t dmin = pr.dmin;
+    // i.e. iff r * min(d_u, d_v) < Y 2^32
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t) const {
         const uint4 r = philox4x32_10(make_uint4(min(x, y), max(x, y), 0u, kTagEdge), k0, k1);
-        if (reweight) w = (dmin * 4294967296ull <= ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), yf);
-        return (unsigned long long)r.x * dmin < ty;
+        return (unsigned long long)r.x * pr.dmin < ty;
+    }
+    __device__ __forceinline__ bool reweights() const { return reweight; }
+    // kept edges may take the weight 1/p_uv
+    __device__ __forceinline__ float weight(uint32_t x, uint32_t y, float) const {
+        return spectral_weight(dmin(x, y), ty, yf);
     }
 };
 
@@ -426,8 +273,8 @@ __global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_
 }
 
 struct OrientPol {
-    static constexpr bool kOrPrefix = false;
-    static constexpr bool kMapCol = false;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = false, kReweight = false;
+    static constexpr int kMinBlocks = 4;
     struct Pre {
         uint32_t sxy;  // saturated degrees of x (high half) and y (low half)
     };
@@ -440,7 +287,7 @@ struct OrientPol {
     // x precedes y in the degree order (d_x, x) < (d_y, y).  Unequal saturated
     // degrees order the vertices as their degrees do; equal ones below 65535
     // are the degrees themselves; only two saturated ones need the offsets.
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &) const {
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t) const {
         const uint32_t sx = pr.sxy >> 16, sy = pr.sxy & 0xFFFFu;
         if (sx != sy) return sx < sy;
         if (sx < 65535u) return x < y;
@@ -451,20 +298,17 @@ struct OrientPol {
 };
 
 struct MaskPol {
-    static constexpr bool kOrPrefix = true;
-    static constexpr bool kMapCol = false;
+    static constexpr bool kNeedRow = false, kNeedCol = false, kOrPrefix = true, kMapCol = false, kReweight = false;
+    static constexpr int kMinBlocks = 4;
     struct Pre {
         uint32_t idx;  // E+ index of the arc's edge, then its deletion flag
     };
     const uint32_t *fwd_bits;
-    const unsigned long long *or_status;
-    const uint2 *inl;  // the reverse list (reverse_list)
+    const int64_t *fwd_excl;  // forward arcs before every chunk
+    const uint2 *inl;         // the reverse list (reverse_list)
     const uint8_t *del;
-    int64_t ninl;      // entries of inl (>= 1)
-    int64_t ndel;      // entries of del (>= 1)
-    __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const {
-        return tile == 0 ? 0 : (int64_t)(ld_volatile_u64(or_status + tile - 1) & kStVal);
-    }
+    int64_t ninl;             // entries of inl (>= 1)
+    int64_t ndel;             // entries of del (>= 1)
     // A forward arc's E+ index is the running prefix of forward arcs; a reverse
     // arc's rank p - (forward arcs before p) finds it in the reverse list.  The
     // indices are clamped to the arrays: an arc whose answer is not used (past
@@ -482,10 +326,209 @@ struct MaskPol {
     }
     __device__ __forceinline__ void load2(Pre &pr) const { pr.idx = __ldg(del + pr.idx); }
     // the arc stays iff its edge's oriented arc carries no deletion flag
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t, float &) const {
-        return pr.idx == 0;
-    }
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t) const { return pr.idx == 0; }
 };
+
+// ---------------------------------------------------------------- engine
+struct EngineArgs {
+    const int64_t *off;
+    const uint32_t *col;
+    const float *w;
+    int64_t n, nnz, num_chunks;
+    const uint32_t *chunk_row;
+    uint32_t *keep;    // CI keep words per chunk
+    int64_t *cexcl;    // kept arcs per chunk, then their exclusive prefix; [num_chunks] = total
+    uint32_t *col_out;
+    float *w_out;
+};
+
+// decide: keep masks and kept counts of every chunk, one warp per chunk
+template <class Pol>
+__global__ void __launch_bounds__(256, Pol::kMinBlocks) decide_kernel(EngineArgs a, Pol pol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < a.num_chunks; c += nw) {
+        const int64_t wbase = c * kWarpSpan;
+        const int64_t t1 = min(wbase + (int64_t)kWarpSpan, a.nnz);
+        // independent loads first: the slabs' columns, forward bits and prefix
+        uint32_t ys[CI];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) ys[k] = Pol::kNeedCol ? __ldg(a.col + min(wbase + k * 32 + lane, t1 - 1)) : 0u;
+        uint32_t words = 0;  // lane k < CI: forward bits of slab k
+        int64_t run = 0;
+        if constexpr (Pol::kOrPrefix) {
+            if (lane < CI) words = __ldg(pol.fwd_bits + c * CI + lane);
+            run = __ldg(pol.fwd_excl + c);
+        }
+        uint32_t xs[CI];
+        if constexpr (Pol::kNeedRow) {
+            warp_rows<CI>(a.off, a.n, (int64_t)__ldg(a.chunk_row + c), wbase, t1, xs);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CI; ++k) xs[k] = 0;
+        }
+        typename Pol::Pre pre[CI];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            SlabCtx sc{0u, 0};
+            if constexpr (Pol::kOrPrefix) {
+                sc.or_word = __shfl_sync(kFull, words, k);
+                sc.or_base = run;
+                run += __popc(sc.or_word);
+            }
+            pre[k] = pol.load(xs[k], ys[k], wbase + k * 32 + lane, sc);
+        }
+#pragma unroll
+        for (int k = 0; k < CI; ++k) pol.load2(pre[k]);
+        uint32_t mine = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            const int64_t p = wbase + k * 32 + lane;
+            const bool keep = p < t1 && pol.keep(pre[k], xs[k], ys[k], p);
+            const uint32_t m = __ballot_sync(kFull, keep);
+            if (lane == k) mine = m;
+            cnt += __popc(m);
+        }
+        if (lane < CI) a.keep[c * CI + lane] = mine;
+        if (lane == 0) a.cexcl[c] = cnt;
+    }
+}
+
+// scan: v[0, nv) -> exclusive prefix in place, v[nv] = total.  Tiles of
+// kScanTile values claimed through a ticket (status[num_tiles]), so a CTA
+// only waits on tiles owned by running CTAs.
+constexpr int kScanPer = 4;
+constexpr int kScanTile = 256 * kScanPer;
+
+int64_t compact_scan_words(int64_t num_chunks) { return (num_chunks + kScanTile - 1) / kScanTile + 1; }
+
+__global__ void __launch_bounds__(256) chunk_scan_kernel(int64_t *v, int64_t nv, int64_t num_tiles,
+                                                         unsigned long long *status, int *err, uint32_t spin_limit,
+                                                         int hold_first) {
+    __shared__ long long s_warp[8];
+    __shared__ long long s_tile, s_excl;
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(status + num_tiles);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= num_tiles) break;
+        const int64_t b0 = tile * kScanTile + (int64_t)threadIdx.x * kScanPer;
+        int64_t x[kScanPer];
+        int64_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            x[i] = b0 + i < nv ? v[b0 + i] : 0;
+            sum += x[i];
+        }
+        int64_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const int64_t wv = lane < 8 ? s_warp[lane] : 0;
+            int64_t winc = wv;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int64_t t = __shfl_up_sync(kFull, winc, o);
+                if (lane >= o) winc += t;
+            }
+            const int64_t agg = __shfl_sync(kFull, winc, 7);
+            if (lane < 8) s_warp[lane] = winc - wv;
+            const int64_t excl = tile_lookback(status, tile, agg, err, spin_limit, hold_first != 0);
+            if (lane == 0) {
+                s_excl = excl;
+                if (tile == num_tiles - 1) v[nv] = excl + agg;
+            }
+        }
+        __syncthreads();
+        int64_t run = s_excl + s_warp[warp] + (inc - sum);
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            if (b0 + i < nv) v[b0 + i] = run;
+            run += x[i];
+        }
+        __syncthreads();
+    }
+}
+
+// scatter: the kept arcs of every chunk to the chunk's prefix plus their rank
+template <class Pol, bool kW>
+__global__ void __launch_bounds__(256, 4) scatter_kernel(EngineArgs a, Pol pol) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < a.num_chunks; c += nw) {
+        const int64_t wbase = c * kWarpSpan;
+        const int64_t t1 = min(wbase + (int64_t)kWarpSpan, a.nnz);
+        const uint32_t word = lane < CI ? __ldg(a.keep + c * CI + lane) : 0u;
+        const int64_t base = __ldg(a.cexcl + c);
+        uint32_t ys[CI];
+        float ws[CI];
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            const int64_t pe = min(wbase + k * 32 + lane, t1 - 1);
+            ys[k] = __ldg(a.col + pe);
+            if constexpr (kW) ws[k] = a.w ? __ldg(a.w + pe) : 0.f;
+        }
+        if constexpr (kW && Pol::kReweight) {
+            if (pol.reweights()) {
+                uint32_t xs[CI];
+                warp_rows<CI>(a.off, a.n, (int64_t)__ldg(a.chunk_row + c), wbase, t1, xs);
+#pragma unroll
+                for (int k = 0; k < CI; ++k) ws[k] = pol.weight(xs[k], ys[k], ws[k]);
+            }
+        }
+        // kept arcs of the chunk's slabs before slab k (lanes 0..CI-1)
+        int inc = __popc(word);
+#pragma unroll
+        for (int o = 1; o < CI; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int excl = inc - __popc(word);
+#pragma unroll
+        for (int k = 0; k < CI; ++k) {
+            const uint32_t wk = __shfl_sync(kFull, word, k);
+            const int ek = __shfl_sync(kFull, excl, k);
+            if ((wk >> lane) & 1u) {
+                const int64_t g = base + ek + __popc(wk & lt);
+                if constexpr (Pol::kMapCol) a.col_out[g] = pol.map_col(ys[k]);
+                else a.col_out[g] = ys[k];
+                if constexpr (kW) a.w_out[g] = ws[k];
+            }
+        }
+    }
+}
+
+// offsets: off'[v] = kept arcs before off[v], for every v in [0, n]
+__global__ void offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64_t nnz, int64_t num_chunks,
+                               const uint32_t *__restrict__ keep, const int64_t *__restrict__ cexcl,
+                               int64_t *__restrict__ off_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+        const int64_t o = __ldg(off + v);
+        int64_t r;
+        if (o >= nnz) {
+            r = __ldg(cexcl + num_chunks);
+        } else if (o <= 0) {  // (o < 0 only with malformed offsets)
+            r = 0;
+        } else {
+            const int64_t c = o / kWarpSpan;
+            const int j = (int)((o >> 5) & (CI - 1)), l = (int)(o & 31);
+            const uint32_t *kw = keep + c * CI;
+            r = __ldg(cexcl + c) + __popc(__ldg(kw + j) & ((1u << l) - 1u));
+            for (int i = 0; i < j; ++i) r += __popc(__ldg(kw + i));
+        }
+        off_out[v] = r;
+    }
+}
 
 // The reverse list.  A reverse arc (x, y) of the symmetric CSR -- y before x
 // in the degree order -- is the E+ arc y->x, at the position of x in the
@@ -509,13 +552,14 @@ struct MaskPol {
 // about 1.9 / 2.4 distinct 32-byte sectors per lookup instead of 6 / 8.5, and
 // those random sectors are the pass's bound.
 constexpr int kRevK = 4;
+static_assert(CI % kRevK == 0, "a warp's slabs lie in one chunk");
 constexpr int kRevWin = 4;
 constexpr int kRevInterp = 6;
 
 __global__ void __launch_bounds__(256, 4) reverse_list_kernel(
     const int64_t *__restrict__ off, int64_t n, int64_t nnz, const uint32_t *__restrict__ col,
     const uint32_t *__restrict__ chunk_row, const uint32_t *__restrict__ fwd_bits,
-    const unsigned long long *__restrict__ or_status, const int64_t *__restrict__ offp,
+    const int64_t *__restrict__ fwd_excl, const int64_t *__restrict__ offp,
     const uint32_t *__restrict__ colp, uint2 *inl, unsigned long long *ctr, int *err, BatchDev batch) {
     const int lane = threadIdx.x & 31;
     const int64_t nslabs = (nnz + 31) >> 5;
@@ -527,15 +571,13 @@ __global__ void __launch_bounds__(256, 4) reverse_list_kernel(
         int len[kRevK];
         uint32_t xs[kRevK], ys[kRevK], vlo[kRevK], vhi[kRevK];
         bool need[kRevK];
-        // forward arcs before slab s0: the orientation's prefix up to its tile
-        // plus the forward bits of the tile's earlier slabs
-        const int64_t tile = (s0 << 5) / kTile;
-        const int64_t w0 = (tile * kTile) >> 5;  // the tile's first slab
-        int64_t fwd_run = tile == 0 ? 0 : (int64_t)(__ldg(or_status + tile - 1) & kStVal);
+        // forward arcs before slab s0: the orientation's prefix up to its chunk
+        // plus the forward bits of the chunk's earlier slabs
+        const int64_t chunk = s0 / CI;
+        int64_t fwd_run = __ldg(fwd_excl + chunk);
         {
-            const int64_t wa = w0 + lane, wb = w0 + 32 + lane;
-            int cnt = (wa < s0 ? __popc(__ldg(fwd_bits + wa)) : 0) + (wb < s0 ? __popc(__ldg(fwd_bits + wb)) : 0);
-            fwd_run += warp_sum(cnt);
+            const int64_t wa = chunk * CI + lane;
+            fwd_run += warp_sum(wa < s0 ? __popc(__ldg(fwd_bits + wa)) : 0);
         }
         // independent loads first: the slabs' forward bits and columns
         const int64_t sb0 = s0 << 5;
@@ -656,7 +698,7 @@ sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
     {
         SG_LAUNCH(c, "tri_reverse_list");
         reverse_list_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(g->off, g->n, g->nnz, g->col, rm.chunk_row,
-                                                                 o.fwd_bits, o.status, o.off, o.col, inl, c->d_ctr,
+                                                                 o.fwd_bits, o.fwd_excl, o.off, o.col, inl, c->d_ctr,
                                                                  c->d_err, batch);
     }
     SG_CUDA(cudaGetLastError());
@@ -665,57 +707,101 @@ sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
 
 
 // ------------------------------------------------------------------ driver
-template <class Pol, bool kW>
-static int blocks_per_sm() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, compact_kernel<Pol, kW>, CW * 32, 0) != cudaSuccess ||
-            b < 1)
-            b = 1;
-        cached = b;
+template <class K>
+static int occupancy(K kernel, int threads) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) {
+        (void)cudaGetLastError();
+        b = 1;
     }
-    return cached;
+    return b;
 }
 
 template <class Pol>
+static int decide_per_sm() {
+    static const int v = occupancy(decide_kernel<Pol>, 256);
+    return v;
+}
+
+template <class Pol, bool kW>
+static int scatter_per_sm() {
+    static const int v = occupancy(scatter_kernel<Pol, kW>, 256);
+    return v;
+}
+
+static int scan_per_sm() {
+    static const int v = occupancy(chunk_scan_kernel, 256);
+    return v;
+}
+
+sg_status alloc_compact_scratch(Ctx *c, int64_t num_chunks, bool with_keep, CompactScratch *s) {
+    sg_status st = SG_OK;
+    if (with_keep) st = dalloc(c, (void **)&s->keep, sizeof(uint32_t) * (size_t)(num_chunks * CI + 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&s->cexcl, sizeof(int64_t) * (size_t)(num_chunks + 1));
+    if (st == SG_OK)
+        st = dalloc(c, (void **)&s->scan, sizeof(unsigned long long) * (size_t)compact_scan_words(num_chunks));
+    return st;
+}
+
+void free_compact_scratch(Ctx *c, CompactScratch *s) {
+    dfree(c, s->keep);
+    dfree(c, s->cexcl);
+    dfree(c, s->scan);
+    *s = CompactScratch{};
+}
+
+// The four passes of one compaction on the context stream, all under `name`.
+template <class Pol>
 static sg_status run_compact(Ctx *c, const Graph *g, const RowMaps &rm, const Pol &pol, const float *w_in,
-                             int64_t *off_out, uint32_t *col_out, float *w_out, uint32_t *keep_bits,
-                             unsigned long long *status, const char *name, int grid_per_sm = 0) {
+                             int64_t *off_out, uint32_t *col_out, float *w_out, const CompactScratch &s,
+                             const char *name, int grid_per_sm = 0) {
     if (g->nnz == 0) {
         SG_CUDA(cudaMemsetAsync(off_out, 0, sizeof(int64_t) * (size_t)(g->n + 1), c->stream));
         return SG_OK;
     }
-    // status words for every tile + the tile ticket, zeroed together
-    SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1), c->stream));
-    CompactArgs a;
+    const int64_t nc = rm.num_chunks;
+    const int64_t words = compact_scan_words(nc);  // tile status words + the ticket
+    SG_CUDA(cudaMemsetAsync(s.scan, 0, sizeof(unsigned long long) * (size_t)words, c->stream));
+    EngineArgs a;
     a.off = g->off;
     a.col = g->col;
     a.w = w_in;
     a.n = g->n;
     a.nnz = g->nnz;
-    a.num_tiles = rm.num_tiles;
+    a.num_chunks = nc;
     a.chunk_row = rm.chunk_row;
-    a.tile_vlo = rm.tile_vlo;
-    a.off_out = off_out;
+    a.keep = s.keep;
+    a.cexcl = s.cexcl;
     a.col_out = col_out;
     a.w_out = w_out;
-    a.status = status;
-    a.ticket = reinterpret_cast<unsigned int *>(status + rm.num_tiles);
-    a.err = c->d_err;
-    a.keep_bits = keep_bits;
-    a.spin_limit = c->scan_hold ? c->scan_hold : kSpinLimit;
-    a.hold_first = c->scan_hold != 0;
     const bool wt = w_out != nullptr;
-    const int cap = wt ? blocks_per_sm<Pol, true>() : blocks_per_sm<Pol, false>();
-    const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, cap) : cap;
-    const int64_t grid = std::min<int64_t>(rm.num_tiles, (int64_t)c->num_sms * per_sm);
+    auto grid_of = [&](int cap) {
+        const int per_sm = grid_per_sm > 0 ? std::min(grid_per_sm, cap) : cap;
+        return std::max<int64_t>(1, std::min<int64_t>((nc + 7) / 8, (int64_t)c->num_sms * per_sm));
+    };
+    {
+        SG_LAUNCH(c, name);
+        decide_kernel<Pol><<<(unsigned)grid_of(decide_per_sm<Pol>()), 256, 0, c->stream>>>(a, pol);
+    }
+    {
+        SG_LAUNCH(c, name);
+        const int64_t tiles = words - 1;
+        const int64_t grid = std::min<int64_t>(tiles, (int64_t)c->num_sms * scan_per_sm());
+        chunk_scan_kernel<<<(unsigned)grid, 256, 0, c->stream>>>(s.cexcl, nc, tiles, s.scan, c->d_err,
+                                                                 c->scan_hold ? c->scan_hold : kSpinLimit,
+                                                                 c->scan_hold != 0);
+    }
     {
         SG_LAUNCH(c, name);
         if (wt)
-            compact_kernel<Pol, true><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
+            scatter_kernel<Pol, true><<<(unsigned)grid_of(scatter_per_sm<Pol, true>()), 256, 0, c->stream>>>(a, pol);
         else
-            compact_kernel<Pol, false><<<(unsigned)grid, CW * 32, 0, c->stream>>>(a, pol);
+            scatter_kernel<Pol, false><<<(unsigned)grid_of(scatter_per_sm<Pol, false>()), 256, 0, c->stream>>>(a, pol);
+    }
+    {
+        SG_LAUNCH(c, name);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 256) / 256, (int64_t)c->num_sms * 16));
+        offsets_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->n, g->nnz, nc, s.keep, s.cexcl, off_out);
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -759,29 +845,29 @@ static void delete_graph(Ctx *c, Graph *h) {
 sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t seed, int want_weights,
                          Graph **out) {
     RowMaps rm;
+    CompactScratch cs;
     sg_status st = build_row_maps(c, g, &rm);
-    unsigned long long *status = nullptr;
     Graph *h = nullptr;
     const bool spectral = (k == SG_SPECTRAL_LOGN || k == SG_SPECTRAL_AVGDEG);
     const bool out_w = (spectral && want_weights) || g->w != nullptr;
-    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = alloc_compact_scratch(c, rm.num_chunks, true, &cs);
     if (st == SG_OK) st = new_graph(c, g->n, g->nnz, out_w, &h);
     if (st == SG_OK) {
         const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
         if (k == SG_UNIFORM) {
             UniformPol pol{k0, k1, prob_threshold(p)};
-            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_uniform");
+            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_uniform");
         } else {
             const int64_t m = g->nnz / 2;
             const double y = (k == SG_SPECTRAL_LOGN) ? p * std::log((double)g->n)
                                                      : (g->n > 0 ? p * (double)m / (double)g->n : 0.0);
             SpectralPol pol{g->off, k0, k1, scaled_threshold(y), (float)y, want_weights != 0};
-            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_spectral");
+            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_spectral");
         }
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
-    dfree(c, status);
+    free_compact_scratch(c, &cs);
     free_row_maps(c, &rm);
     if (st != SG_OK) {
         delete_graph(c, h);
@@ -800,21 +886,27 @@ sg_status orient(Ctx *c, const Graph *g, const RowMaps &rm, bool weights, Orient
     if (st == SG_OK && weights) st = dalloc(c, (void **)&o->w, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1));
     if (st == SG_OK)
         st = dalloc(c, (void **)&o->fwd_bits, sizeof(uint32_t) * (size_t)(rm.num_chunks * CI + 1));
-    if (st == SG_OK)
-        st = dalloc(c, (void **)&o->status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = dalloc(c, (void **)&o->fwd_excl, sizeof(int64_t) * (size_t)(rm.num_chunks + 1));
     if (st != SG_OK) return st;
     uint16_t *deg16 = nullptr;
+    CompactScratch cs;
+    cs.keep = o->fwd_bits;  // the keep masks and their prefix are the orientation's
+    cs.cexcl = o->fwd_excl;
     st = dalloc(c, (void **)&deg16, sizeof(uint16_t) * (size_t)std::max<int64_t>(g->n, 1));
-    if (st != SG_OK) return st;
-    if (g->n > 0) {
+    if (st == SG_OK)
+        st = dalloc(c, (void **)&cs.scan, sizeof(unsigned long long) * (size_t)compact_scan_words(rm.num_chunks));
+    if (st == SG_OK && g->n > 0) {
         const int64_t blocks = std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 16);
         SG_LAUNCH(c, "compact_orient_deg");
         deg16_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->n, deg16);
     }
-    OrientPol pol{g->off, deg16};
-    st = run_compact(c, g, rm, pol, weights ? g->w : nullptr, o->off, o->col, weights ? o->w : nullptr,
-                     o->fwd_bits, o->status, "compact_orient");
+    if (st == SG_OK) {
+        OrientPol pol{g->off, deg16};
+        st = run_compact(c, g, rm, pol, weights ? g->w : nullptr, o->off, o->col, weights ? o->w : nullptr, cs,
+                         "compact_orient");
+    }
     dfree(c, deg16);
+    dfree(c, cs.scan);
     if (st != SG_OK) return st;
     int64_t mp = 0;
     st = read_i64(c, o->off + g->n, &mp);
@@ -833,7 +925,7 @@ void free_oriented(Ctx *c, Oriented *o) {
     dfree(c, o->col);
     dfree(c, o->w);
     dfree(c, o->fwd_bits);
-    dfree(c, o->status);
+    dfree(c, o->fwd_excl);
     dfree(c, o->inl);
     *o = Oriented{};
 }
@@ -841,17 +933,17 @@ void free_oriented(Ctx *c, Oriented *o) {
 sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, const uint8_t *del,
                        Graph **out) {
     Graph *h = nullptr;
-    unsigned long long *status = nullptr;
+    CompactScratch cs;
     sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
-    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = alloc_compact_scratch(c, rm.num_chunks, true, &cs);
     if (st == SG_OK) {
-        MaskPol pol{o.fwd_bits, o.status, o.inl, del, std::max<int64_t>(g->nnz - o.m, 1),
+        MaskPol pol{o.fwd_bits, o.fwd_excl, o.inl, del, std::max<int64_t>(g->nnz - o.m, 1),
                     std::max<int64_t>(o.m, 1)};
-        st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, nullptr, status, "compact_trmask");
+        st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_trmask");
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
-    dfree(c, status);
+    free_compact_scratch(c, &cs);
     if (st != SG_OK) {
         delete_graph(c, h);
         return st;
@@ -865,80 +957,94 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
 // every graph carries its own kernel, p, seed and vertex base.  Random keys use
 // the graph's local ids, so every graph's output equals its solo compression.
 struct BatchOrientPol {
-    static constexpr bool kOrPrefix = false;
-    static constexpr bool kMapCol = false;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = false, kReweight = false;
+    static constexpr int kMinBlocks = 4;
     struct Pre {
-        uint32_t g;  // the graph of x
-        int64_t dx, dy;
+        uint32_t g;      // the graph of x
+        uint32_t first;  // x precedes y in the degree order
     };
     const int64_t *off;
     BatchDev b;
     __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t, const SlabCtx &) const {
-        return Pre{__ldg(b.vgid + x), __ldg(off + x + 1) - __ldg(off + x), __ldg(off + y + 1) - __ldg(off + y)};
+        const int64_t dx = __ldg(off + x + 1) - __ldg(off + x), dy = __ldg(off + y + 1) - __ldg(off + y);
+        return Pre{__ldg(b.vgid + x), (dx < dy || (dx == dy && x < y)) ? 1u : 0u};
     }
     __device__ __forceinline__ void load2(Pre &) const {}
     // only graphs compressed by a triangle kernel need E+
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t, float &) const {
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t) const {
         const int kern = __ldg(&b.params[pr.g].kernel);
-        if (kern < (int)SG_TR_RANDOM) return false;
-        return pr.dx < pr.dy || (pr.dx == pr.dy && x < y);
+        return kern >= (int)SG_TR_RANDOM && pr.first != 0;
     }
 };
 
 struct BatchFinalPol {
-    static constexpr bool kOrPrefix = true;
-    static constexpr bool kMapCol = true;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = true, kMapCol = true, kReweight = true;
+    static constexpr int kMinBlocks = 2;  // 128 registers: its decision holds a Philox per slab
     struct Pre {
         MaskPol::Pre mp;
-        uint32_t g;  // the graph of x
-        uint64_t dmin;
+        uint32_t g;     // the graph of x
+        uint32_t dmin;  // min(d_x, d_y) (degrees of a simple graph with n < 2^32 fit)
     };
     const int64_t *off;
     BatchDev b;
     MaskPol mask;
-    const uint32_t *fwd_bits;  // = mask.fwd_bits (read directly by the tile prologue)
-    __device__ __forceinline__ int64_t tile_or_excl(int64_t tile) const { return mask.tile_or_excl(tile); }
-    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t p, const SlabCtx &s) const {
+    const uint32_t *fwd_bits;  // = mask.fwd_bits, mask.fwd_excl (read by the decide pass)
+    const int64_t *fwd_excl;
+    __device__ __forceinline__ uint64_t dmin(uint32_t x, uint32_t y) const {
         const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
         const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
-        return Pre{mask.load(x, y, p, s), __ldg(b.vgid + x), dx < dy ? dx : dy};
+        return dx < dy ? dx : dy;
+    }
+    __device__ __forceinline__ Pre load(uint32_t x, uint32_t y, int64_t p, const SlabCtx &s) const {
+        return Pre{mask.load(x, y, p, s), __ldg(b.vgid + x), (uint32_t)min(dmin(x, y), (uint64_t)0xFFFFFFFFu)};
     }
     __device__ __forceinline__ void load2(Pre &pr) const { mask.load2(pr.mp); }
-    __device__ __forceinline__ uint32_t map_col(const Pre &pr, uint32_t, uint32_t y) const {
-        return y - (uint32_t)__ldg(&b.params[pr.g].vbase);
-    }
     // a graph's own kernel decides its arcs; a triangle kernel's through the mask
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t p, float &w) const {
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t x, uint32_t y, int64_t p) const {
         const BatchParam &P = b.params[pr.g];
         const int kern = P.kernel;
-        if (kern >= (int)SG_TR_RANDOM) return mask.keep(pr.mp, x, y, p, w);
+        if (kern >= (int)SG_TR_RANDOM) return mask.keep(pr.mp, x, y, p);
         const uint32_t lx = (uint32_t)(x - P.vbase), ly = (uint32_t)(y - P.vbase);
         const uint4 r = philox4x32_10(make_uint4(min(lx, ly), max(lx, ly), 0u, kTagEdge), P.k0, P.k1);
         if (kern == (int)SG_UNIFORM) return (unsigned long long)r.x < P.tp;
-        const uint64_t dmin = pr.dmin;
-        if (P.reweight) w = (dmin * 4294967296ull <= P.ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), P.yf);
-        return (unsigned long long)r.x * dmin < P.ty;
+        return (unsigned long long)r.x * (uint64_t)pr.dmin < P.ty;
+    }
+    // the output is per graph: local column ids (x and y share a graph)
+    __device__ __forceinline__ uint32_t map_col(uint32_t y) const {
+        return y - (uint32_t)__ldg(&b.params[__ldg(b.vgid + y)].vbase);
+    }
+    // per graph: spectral graphs that want 1/p_uv weights take them
+    __device__ __forceinline__ bool reweights() const { return true; }
+    __device__ __forceinline__ float weight(uint32_t x, uint32_t y, float w) const {
+        const BatchParam &P = b.params[__ldg(b.vgid + y)];
+        const int kern = P.kernel;
+        if (kern == (int)SG_UNIFORM || kern >= (int)SG_TR_RANDOM || !P.reweight) return w;
+        return spectral_weight(dmin(x, y), P.ty, P.yf);
     }
 };
 
 sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev &b, bool weights, Oriented *o,
-                       unsigned long long *status, int grid_per_sm) {
+                       unsigned long long *scan, int grid_per_sm) {
     BatchOrientPol pol{u->off, b};
-    return run_compact(c, u, rm, pol, weights ? u->w : nullptr, o->off, o->col, weights ? o->w : nullptr,
-                       o->fwd_bits, status, "compact_orient", grid_per_sm);
+    CompactScratch cs;
+    cs.keep = o->fwd_bits;
+    cs.cexcl = o->fwd_excl;
+    cs.scan = scan;
+    return run_compact(c, u, rm, pol, weights ? u->w : nullptr, o->off, o->col, weights ? o->w : nullptr, cs,
+                       "compact_orient", grid_per_sm);
 }
 
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      unsigned long long *status, int grid_per_sm) {
+                      const CompactScratch &cs, int grid_per_sm) {
     // the reverse arcs of graphs without a triangle kernel are not in the
-    // reverse list (BatchFinalPol decides those arcs itself)
-    // (its reverse list has room for every arc of the union, del for its m edges)
+    // reverse list (BatchFinalPol decides those arcs itself); the list has room
+    // for every arc of the union, del for its m edges
     BatchFinalPol pol{u->off, b,
-                      MaskPol{o.fwd_bits, o.status, o.inl, del, std::max<int64_t>(u->nnz, 1), std::max<int64_t>(o.m, 1)},
-                      o.fwd_bits};
-    return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, nullptr, status, "compact_final",
-                       grid_per_sm);
+                      MaskPol{o.fwd_bits, o.fwd_excl, o.inl, del, std::max<int64_t>(u->nnz, 1),
+                              std::max<int64_t>(o.m, 1)},
+                      o.fwd_bits, o.fwd_excl};
+    return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, cs, "compact_final", grid_per_sm);
 }
 
 // ------------------------------------------- low_degree (Listing 1; Sec. 4.4)
@@ -1022,8 +1128,8 @@ __global__ void __launch_bounds__(256) lowdeg_ids_kernel(const int64_t *__restri
 }
 
 struct LowDegPol {
-    static constexpr bool kOrPrefix = false;
-    static constexpr bool kMapCol = true;
+    static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = true, kReweight = false;
+    static constexpr int kMinBlocks = 4;
     struct Pre {
         uint32_t nx, ny;  // new ids of x and y
     };
@@ -1033,10 +1139,10 @@ struct LowDegPol {
     }
     __device__ __forceinline__ void load2(Pre &) const {}
     // an arc stays iff both of its ends stay; its head is renumbered
-    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t, float &) const {
+    __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t) const {
         return pr.nx != kNoVertex && pr.ny != kNoVertex;
     }
-    __device__ __forceinline__ uint32_t map_col(const Pre &pr, uint32_t, uint32_t) const { return pr.ny; }
+    __device__ __forceinline__ uint32_t map_col(uint32_t y) const { return __ldg(new_id + y); }
 };
 
 // off'[new_id[v]] = off_c[v] for every kept row v; off'[n'] = off_c[n]
@@ -1055,13 +1161,14 @@ sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out) 
     const int64_t vtiles = (g->n + kVTile - 1) / kVTile;
     uint32_t *new_id = nullptr;
     int64_t *off_c = nullptr;
-    unsigned long long *status = nullptr, *vstatus = nullptr;
+    unsigned long long *vstatus = nullptr;
+    CompactScratch cs;
     Graph *h = nullptr;
     int64_t kept = 0;
     sg_status st = build_row_maps(c, g, &rm);
     if (st == SG_OK) st = dalloc(c, (void **)&new_id, sizeof(uint32_t) * (size_t)std::max<int64_t>(g->n, 1));
     if (st == SG_OK) st = dalloc(c, (void **)&off_c, sizeof(int64_t) * (size_t)(g->n + 1));
-    if (st == SG_OK) st = dalloc(c, (void **)&status, sizeof(unsigned long long) * (size_t)(rm.num_tiles + 1));
+    if (st == SG_OK) st = alloc_compact_scratch(c, rm.num_chunks, true, &cs);
     // tile status words, the tile ticket and the kept-vertex count, zeroed together
     if (st == SG_OK) st = dalloc(c, (void **)&vstatus, sizeof(unsigned long long) * (size_t)(vtiles + 2));
     if (st == SG_OK && g->n > 0) {
@@ -1080,7 +1187,7 @@ sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out) 
     if (st == SG_OK) st = new_graph(c, kept, g->nnz, g->w != nullptr, &h);
     if (st == SG_OK && g->n > 0) {
         LowDegPol pol{new_id};
-        st = run_compact(c, g, rm, pol, g->w, off_c, h->col, h->w, nullptr, status, "compact_lowdeg");
+        st = run_compact(c, g, rm, pol, g->w, off_c, h->col, h->w, cs, "compact_lowdeg");
         if (st == SG_OK) {
             const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 8));
             SG_LAUNCH(c, "lowdeg_offsets");
@@ -1095,7 +1202,7 @@ sg_status low_degree(Ctx *c, const Graph *g, uint32_t *new_to_old, Graph **out) 
     if (st == SG_OK) st = check_device_error(c);
     dfree(c, new_id);
     dfree(c, off_c);
-    dfree(c, status);
+    free_compact_scratch(c, &cs);
     dfree(c, vstatus);
     free_row_maps(c, &rm);
     if (st != SG_OK) {
@@ -1127,21 +1234,22 @@ extern "C" sg_status sg_kernel_arch(int device, int *binary_version) {
 
 // ------------------------------------------------ no-allocation entry point
 // Uniform edge sampling for callers that must not allocate device memory:
-// the scratch (row maps, tile status words, the tile ticket and an error
-// word) lives in one fixed file-scope device array instead of the stream-
-// ordered pool.  Every process that loads this library reserves the array on
+// the scratch (the row map, the keep masks and chunk prefixes, the chunk
+// scan's status words and ticket, an error word; about 23 MB) lives in one
+// fixed file-scope device array instead of the stream-ordered pool.  Every process that loads this library reserves the array on
 // each GPU it touches, for as long as the library stays loaded.
 namespace sg {
 namespace {
 
 constexpr int64_t kNaMaxArcs = int64_t(1) << 27;
 constexpr int64_t kNaMaxChunks = kNaMaxArcs / kWarpSpan;
-constexpr int64_t kNaMaxTiles = kNaMaxArcs / kTile;
+constexpr int64_t kNaScanWords = (kNaMaxChunks + kScanTile - 1) / kScanTile + 1;
 constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kNaChunkOff = 0;
-constexpr size_t kNaTileOff = na_align(kNaChunkOff + sizeof(uint32_t) * (kNaMaxChunks + 1));
-constexpr size_t kNaStatusOff = na_align(kNaTileOff + sizeof(int64_t) * (kNaMaxTiles + 1));
-constexpr size_t kNaErrOff = na_align(kNaStatusOff + sizeof(unsigned long long) * (kNaMaxTiles + 1));
+constexpr size_t kNaKeepOff = na_align(kNaChunkOff + sizeof(uint32_t) * (kNaMaxChunks + 1));
+constexpr size_t kNaExclOff = na_align(kNaKeepOff + sizeof(uint32_t) * (kNaMaxChunks * CI + 1));
+constexpr size_t kNaScanOff = na_align(kNaExclOff + sizeof(int64_t) * (kNaMaxChunks + 1));
+constexpr size_t kNaErrOff = na_align(kNaScanOff + sizeof(unsigned long long) * kNaScanWords);
 constexpr size_t kNaBytes = na_align(kNaErrOff + sizeof(int));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -1207,41 +1315,36 @@ sg_status noalloc_uniform(int device, void *cuda_stream, int64_t n, int64_t nnz,
     }
     int num_sms = 0;
     SG_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
-    const int64_t num_tiles = (nnz + kTile - 1) / kTile;
-    const int64_t num_chunks = (nnz + kWarpSpan - 1) / kWarpSpan;
+    const int64_t nc = (nnz + kWarpSpan - 1) / kWarpSpan;
+    const int64_t words = compact_scan_words(nc);
     uint32_t *chunk_row = reinterpret_cast<uint32_t *>(base + kNaChunkOff);
-    int64_t *tile_vlo = reinterpret_cast<int64_t *>(base + kNaTileOff);
-    unsigned long long *status = reinterpret_cast<unsigned long long *>(base + kNaStatusOff);
-    // the status words and the ticket must start at zero on every call
-    SG_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(num_tiles + 1), stream));
-    const int64_t rb = std::min<int64_t>((n + 1 + 255) / 256, (int64_t)num_sms * 16);
-    prefill_row_maps(stream, num_sms, chunk_row, num_chunks, tile_vlo, num_tiles, n);
-    row_maps_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, stream>>>(off, n, chunk_row, num_chunks, tile_vlo,
-                                                                           num_tiles);
-    SG_CUDA(cudaGetLastError());
-    CompactArgs a;
+    EngineArgs a;
     a.off = off;
     a.col = col;
     a.w = nullptr;
     a.n = n;
     a.nnz = nnz;
-    a.num_tiles = num_tiles;
+    a.num_chunks = nc;
     a.chunk_row = chunk_row;
-    a.tile_vlo = tile_vlo;
-    a.off_out = off_out;
+    a.keep = reinterpret_cast<uint32_t *>(base + kNaKeepOff);
+    a.cexcl = reinterpret_cast<int64_t *>(base + kNaExclOff);
     a.col_out = col_out;
     a.w_out = nullptr;
-    a.status = status;
-    a.ticket = reinterpret_cast<unsigned int *>(status + num_tiles);
-    a.err = err;
-    a.keep_bits = nullptr;
-    a.spin_limit = kSpinLimit;
-    a.hold_first = 0;
+    unsigned long long *scan = reinterpret_cast<unsigned long long *>(base + kNaScanOff);
+    // the scan's status words and ticket must start at zero on every call
+    SG_CUDA(cudaMemsetAsync(scan, 0, sizeof(unsigned long long) * (size_t)words, stream));
+    launch_row_maps(stream, num_sms, off, n, chunk_row, nc);
+    SG_CUDA(cudaGetLastError());
     UniformPol pol{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), prob_threshold(p)};
-    int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_kernel<UniformPol, false>, CW * 32, 0));
-    const int64_t grid = std::min<int64_t>(num_tiles, (int64_t)num_sms * std::max(per_sm, 1));
-    compact_kernel<UniformPol, false><<<(unsigned)grid, CW * 32, 0, stream>>>(a, pol);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nc + 7) / 8, (int64_t)num_sms * decide_per_sm<UniformPol>()));
+    decide_kernel<UniformPol><<<(unsigned)grid, 256, 0, stream>>>(a, pol);
+    const int64_t sgrid = std::min<int64_t>(words - 1, (int64_t)num_sms * scan_per_sm());
+    chunk_scan_kernel<<<(unsigned)sgrid, 256, 0, stream>>>(a.cexcl, nc, words - 1, scan, err, kSpinLimit, 0);
+    const int64_t xgrid =
+        std::max<int64_t>(1, std::min<int64_t>((nc + 7) / 8, (int64_t)num_sms * scatter_per_sm<UniformPol, false>()));
+    scatter_kernel<UniformPol, false><<<(unsigned)xgrid, 256, 0, stream>>>(a, pol);
+    const int64_t ob = std::max<int64_t>(1, std::min<int64_t>((n + 256) / 256, (int64_t)num_sms * 16));
+    offsets_kernel<<<(unsigned)ob, 256, 0, stream>>>(off, n, nnz, nc, a.keep, a.cexcl, off_out);
     SG_CUDA(cudaGetLastError());
     int64_t count = 0;
     int code = 0;

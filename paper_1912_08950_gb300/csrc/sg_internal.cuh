@@ -22,11 +22,10 @@ enum DevErr : int { kDevOk = 0, kDevLookbackTimeout = 1, kDevBadGraph = 2, kDevT
 // bounded spin: polls of a not-yet-published status word before giving up
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-// compaction geometry: CW warps x 32 lanes x CI items per tile
-constexpr int CW = 8;
+// compaction geometry: a chunk of kWarpSpan arcs is one warp's CI slabs of 32
 constexpr int CI = 8;
-constexpr int kWarpSpan = 32 * CI;       // arcs per warp per tile
-constexpr int kTile = CW * kWarpSpan;    // arcs per tile
+constexpr int kWarpSpan = 32 * CI;  // arcs per chunk
+static_assert((CI & (CI - 1)) == 0 && CI <= 32, "CI is a power of two of at most 32 slabs");
 
 // ------------------------------------------------------------- host objects
 struct ProfRec {
@@ -176,9 +175,17 @@ struct BatchParam {
 // compaction / edge kernels (sg_compact.cu)
 struct RowMaps {
     uint32_t *chunk_row = nullptr;  // row containing arc c * kWarpSpan
-    int64_t *tile_vlo = nullptr;    // first row v with off[v] >= t * kTile; [num_tiles] = n + 1
-    int64_t num_tiles = 0, num_chunks = 0;
+    int64_t num_chunks = 0;
 };
+// scratch of one arc compaction
+struct CompactScratch {
+    uint32_t *keep = nullptr;            // keep bit of every arc: CI words per chunk
+    int64_t *cexcl = nullptr;            // kept arcs per chunk, then their exclusive prefix; [num_chunks] = total
+    unsigned long long *scan = nullptr;  // the chunk scan's tile status words and ticket
+};
+int64_t compact_scan_words(int64_t num_chunks);  // entries of CompactScratch::scan
+sg_status alloc_compact_scratch(Ctx *c, int64_t num_chunks, bool with_keep, CompactScratch *s);
+void free_compact_scratch(Ctx *c, CompactScratch *s);
 sg_status build_row_maps(Ctx *c, const Graph *g, RowMaps *rm);
 sg_status fill_row_maps(Ctx *c, const Graph *g, const RowMaps &rm);  // into allocated maps
 void free_row_maps(Ctx *c, RowMaps *rm);
@@ -193,7 +200,7 @@ struct Oriented {
     uint32_t *col = nullptr;     // col+[m]
     float *w = nullptr;          // w+[m] (weighted TR only)
     uint32_t *fwd_bits = nullptr;  // bit per symmetric arc: 1 iff x precedes y
-    unsigned long long *status = nullptr;  // inclusive prefix of forward arcs per tile
+    int64_t *fwd_excl = nullptr;   // forward arcs before every chunk; [num_chunks] = m
     // the reverse arcs in symmetric order: the one at symmetric position p is
     // E+ arc u->x (u = col[p] before its row x), stored as (u, arc index) at
     // rank p - (forward arcs before p); x's in-arcs are thus contiguous at
@@ -212,10 +219,10 @@ struct BatchDev {
     const uint32_t *vgid;       // graph of every union vertex
 };
 sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev &b, bool weights, Oriented *o,
-                       unsigned long long *status, int grid_per_sm);
+                       unsigned long long *scan, int grid_per_sm);
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
                       const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      unsigned long long *status, int grid_per_sm);
+                      const CompactScratch &cs, int grid_per_sm);
 // the reverse list of o (see Oriented::inl) into inl; in a batch only the
 // graphs with a triangle kernel are listed
 sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, uint2 *inl,

@@ -21,7 +21,9 @@ def sg():
 @pytest.mark.parametrize("kern", ["uniform", "spectral_avgdeg", "tr_random", "tr_eo"])
 def test_scan_wait_runs_out_and_the_context_recovers(sg, kern):
     ctx = sg.Context(0)
-    g = gg.rmat(12, 16, seed=3)  # 32 tiles of 2048 arcs: tile 1 waits on tile 0
+    # about 3,450 chunks of 256 arcs: the chunk scan runs over four tiles of
+    # 1024 chunks, and tile 1 waits on tile 0
+    g = gg.rmat(15, 16, seed=3)
     G = sg.Graph.from_csr(ctx, g)
     ctx.set_scan_hold(4096)  # tile 0 never publishes; a wait gives up after 4096 polls
     with pytest.raises(sg.SgError) as ei:
