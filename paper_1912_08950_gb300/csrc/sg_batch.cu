@@ -89,6 +89,7 @@ struct Batch {
     uint8_t *del = nullptr;
     unsigned long long *scan = nullptr;  // chunk-scan status words (orientation, then output)
     CompactScratch final_cs;              // the output compaction's keep masks and chunk prefixes
+    uint32_t *delbits = nullptr;          // the deletion flags packed to bits
     BatchTri bt;
     int64_t *off_c = nullptr;      // union offsets after compaction
     int64_t *out_off = nullptr;    // per-graph offsets, n_g + 1 each
@@ -124,7 +125,7 @@ static sg_status enqueue_pipeline(Batch *b, const Tune &t) {
         bt.grid_per_sm = t.enum_per_sm;
         st = batch_tr_mark(c, &b->u, b->o, dev, bt, b->del);
         if (st != SG_OK) return st;
-        st = batch_final(c, &b->u, b->rm, b->o, dev, b->del, b->off_c, b->out_col, b->u.w, b->out_w,
+        st = batch_final(c, &b->u, b->rm, b->o, dev, b->del, b->delbits, b->off_c, b->out_col, b->u.w, b->out_w,
                          b->final_cs, t.compact_per_sm);
         if (st != SG_OK) return st;
     }
@@ -338,6 +339,8 @@ sg_status sg_batch_create(sg_ctx *ctx, int count, const sg_graph *const *graphs,
                         sizeof(unsigned long long) * (size_t)compact_scan_words(b->rm.num_chunks));
         if (st == SG_OK) st = alloc_compact_scratch(c, b->rm.num_chunks, true, &b->final_cs);
         if (st == SG_OK) st = dalloc(c, (void **)&b->del, (size_t)std::max<int64_t>(m, 1));
+        if (st == SG_OK)
+            st = dalloc(c, (void **)&b->delbits, sizeof(uint32_t) * (size_t)((std::max<int64_t>(m, 1) + 31) / 32));
         if (st == SG_OK) st = dalloc(c, (void **)&b->off_c, sizeof(int64_t) * (size_t)(nt + 1));
         if (st == SG_OK) st = dalloc(c, (void **)&b->out_off, sizeof(int64_t) * (size_t)(nt + count));
         if (st == SG_OK) st = dalloc(c, (void **)&b->out_col, sizeof(uint32_t) * (size_t)std::max<int64_t>(at, 1));
@@ -384,7 +387,7 @@ void sg_batch_free(sg_batch *b) {
         for (void *p : {(void *)b->u.off, (void *)b->u.col, (void *)b->u.w, (void *)b->vgid, (void *)b->d_params,
                         (void *)b->rm.chunk_row, (void *)b->o.off, (void *)b->o.col, (void *)b->o.w,
                         (void *)b->o.fwd_bits, (void *)b->o.fwd_excl, (void *)b->scan, (void *)b->final_cs.keep,
-                        (void *)b->final_cs.cexcl, (void *)b->final_cs.scan,
+                        (void *)b->final_cs.cexcl, (void *)b->final_cs.scan, (void *)b->delbits,
                         (void *)b->del, (void *)b->bt.heavy, (void *)b->bt.buckets, (void *)b->bt.din,
                         (void *)b->bt.inl, (void *)b->off_c,
                         (void *)b->out_off, (void *)b->out_col, (void *)b->out_w, (void *)b->d_info})
@@ -407,6 +410,7 @@ void sg_batch_free(sg_batch *b) {
     free_oriented(c, &b->o);
     dfree(c, b->scan);
     free_compact_scratch(c, &b->final_cs);
+    dfree(c, b->delbits);
     dfree(c, b->del);
     batch_tr_free(c, &b->bt);
     dfree(c, b->off_c);

@@ -111,27 +111,39 @@ struct SlabCtx {
 // Rows of the arcs of K consecutive 32-arc slabs starting at wbase, one arc
 // per lane (arcs at or past t1 take the row of arc t1 - 1), clamped to
 // [0, n - 1].  r0 is a row with off[r0] <= wbase (the row holding wbase, from
-// the row maps).  Lane j holds the start off[rb + 1 + j] of one batch of 32
-// rows; a slab's rows follow from a search of that batch by shuffles, and a
-// new batch is loaded only when a slab runs past the batch's last start, so
-// the searches of the K slabs do not wait on one another's loads.
+// the row map).  Lane j holds the start of row rb + 1 + j, relative to wbase,
+// for one batch of 32 rows.  A slab with no row start inside it (the common
+// case: most arcs lie in long rows) takes its one row from two ballots; the
+// others search the batch by shuffles.  A new batch is loaded only when a slab
+// runs past the batch's last start, so the slabs do not wait on one another.
 template <int K>
 __device__ __forceinline__ void warp_rows(const int64_t *__restrict__ off, int64_t n, int64_t r0, int64_t wbase,
                                           int64_t t1, uint32_t (&rows)[K]) {
     const int lane = threadIdx.x & 31;
+    auto rel_start = [&](int64_t rb) {  // start of row rb + 1 + lane - wbase, clamped to [-1, K * 32 + 1]
+        const int64_t v = rb + 1 + lane;
+        const int64_t st = (v <= n) ? __ldg(off + v) - wbase : (int64_t)(K * 32 + 1);
+        return st < 0 ? -1 : (st > K * 32 + 1 ? K * 32 + 1 : (int)st);
+    };
     int64_t rb = r0;
-    int64_t bst = (rb + 1 + lane <= n) ? __ldg(off + rb + 1 + lane) : LLONG_MAX;
+    int brel = rel_start(rb);
     uint32_t prev = (uint32_t)min(r0, n - 1);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int64_t sbase = wbase + k * 32;
         rows[k] = prev;
         if (sbase >= t1) continue;  // warp-uniform
+        const int lo = k * 32;
         const int q = sbase + lane < t1 ? lane : (int)(t1 - 1 - sbase);
         int64_t row = -1;
         for (;;) {
-            const int64_t rel = bst - sbase;
-            const int r = rel < 0 ? -1 : (rel > 32 ? 32 : (int)rel);
+            const uint32_t before = __ballot_sync(kFull, brel <= lo);
+            const uint32_t inside = __ballot_sync(kFull, brel > lo && brel <= lo + 31);
+            if (inside == 0 && before != kFull) {  // one row for the whole slab
+                if (row < 0) row = rb + __popc(before);
+                break;
+            }
+            const int r = brel - lo < -1 ? -1 : (brel - lo > 32 ? 32 : brel - lo);
             int cnt = 0;  // batch starts at or before sbase + q
 #pragma unroll
             for (int s = 16; s >= 1; s >>= 1) {
@@ -143,7 +155,7 @@ __device__ __forceinline__ void warp_rows(const int64_t *__restrict__ off, int64
             if (row < 0 && cnt < 32) row = rb + cnt;
             if (!__any_sync(kFull, row < 0)) break;
             rb += 32;
-            bst = (rb + 1 + lane <= n) ? __ldg(off + rb + 1 + lane) : LLONG_MAX;
+            brel = rel_start(rb);
         }
         prev = (uint32_t)min(row, n - 1);
         rows[k] = prev;
@@ -306,9 +318,9 @@ struct MaskPol {
     const uint32_t *fwd_bits;
     const int64_t *fwd_excl;  // forward arcs before every chunk
     const uint2 *inl;         // the reverse list (reverse_list)
-    const uint8_t *del;
+    const uint32_t *delbits;  // the deletion flags, one bit per E+ arc (pack_flags_kernel)
     int64_t ninl;             // entries of inl (>= 1)
-    int64_t ndel;             // entries of del (>= 1)
+    int64_t ndel;             // E+ arcs (>= 1)
     // A forward arc's E+ index is the running prefix of forward arcs; a reverse
     // arc's rank p - (forward arcs before p) finds it in the reverse list.  The
     // indices are clamped to the arrays: an arc whose answer is not used (past
@@ -324,10 +336,46 @@ struct MaskPol {
         }
         return Pre{(uint32_t)min(idx, ndel - 1)};
     }
-    __device__ __forceinline__ void load2(Pre &pr) const { pr.idx = __ldg(del + pr.idx); }
+    __device__ __forceinline__ void load2(Pre &pr) const {
+        pr.idx = (__ldg(delbits + (pr.idx >> 5)) >> (pr.idx & 31)) & 1u;
+    }
     // the arc stays iff its edge's oriented arc carries no deletion flag
     __device__ __forceinline__ bool keep(const Pre &pr, uint32_t, uint32_t, int64_t) const { return pr.idx == 0; }
 };
+
+// The deletion flags packed to one bit per E+ arc before the CSR rebuild:
+// m/8 bytes (R-MAT s26: 131 MB, about the size of L2), so that the random
+// flag reads of the reverse arcs mostly hit L2 instead of each fetching a
+// 32-byte sector of the byte flags from DRAM.  One thread per output word.
+__global__ void pack_flags_kernel(const uint8_t *__restrict__ del, int64_t m, uint32_t *__restrict__ bits) {
+    const int64_t words = (m + 31) / 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(del) & 15u) == 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
+        const int64_t b0 = w * 32;
+        uint32_t v = 0;
+        if (vec && b0 + 32 <= m) {  // 32 flags from two 16-byte loads
+            const uint4 *p = reinterpret_cast<const uint4 *>(del + b0);
+            const uint4 a = __ldg(p), b = __ldg(p + 1);
+            const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                // bit 7 of every nonzero byte, moved to bits 24..27 in byte order
+                const uint32_t nz = (__vcmpne4(x[i], 0u) >> 7) & 0x01010101u;
+                v |= ((nz * 0x01020408u) >> 24) << (4 * i);
+            }
+        } else {
+            for (int64_t i = b0; i < m; ++i) v |= (del[i] != 0 ? 1u : 0u) << (i - b0);
+        }
+        bits[w] = v;
+    }
+}
+
+static void launch_pack_flags(cudaStream_t stream, int num_sms, const uint8_t *del, int64_t m, uint32_t *bits) {
+    const int64_t words = (m + 31) / 32;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms * 16));
+    pack_flags_kernel<<<(unsigned)blocks, 256, 0, stream>>>(del, m, bits);
+}
 
 // ---------------------------------------------------------------- engine
 struct EngineArgs {
@@ -352,8 +400,19 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) decide_kernel(EngineArgs
         const int64_t t1 = min(wbase + (int64_t)kWarpSpan, a.nnz);
         // independent loads first: the slabs' columns, forward bits and prefix
         uint32_t ys[CI];
+        if constexpr (Pol::kNeedCol) {
+            if (t1 - wbase == kWarpSpan) {  // a full chunk: no clamping
+                const uint32_t *cp = a.col + wbase + lane;
 #pragma unroll
-        for (int k = 0; k < CI; ++k) ys[k] = Pol::kNeedCol ? __ldg(a.col + min(wbase + k * 32 + lane, t1 - 1)) : 0u;
+                for (int k = 0; k < CI; ++k) ys[k] = __ldg(cp + k * 32);
+            } else {
+#pragma unroll
+                for (int k = 0; k < CI; ++k) ys[k] = __ldg(a.col + min(wbase + k * 32 + lane, t1 - 1));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < CI; ++k) ys[k] = 0u;
+        }
         uint32_t words = 0;  // lane k < CI: forward bits of slab k
         int64_t run = 0;
         if constexpr (Pol::kOrPrefix) {
@@ -471,11 +530,17 @@ __global__ void __launch_bounds__(256, 4) scatter_kernel(EngineArgs a, Pol pol) 
         const int64_t base = __ldg(a.cexcl + c);
         uint32_t ys[CI];
         float ws[CI];
+        if (t1 - wbase == kWarpSpan) {  // a full chunk: no clamping
+            const uint32_t *cp = a.col + wbase + lane;
 #pragma unroll
-        for (int k = 0; k < CI; ++k) {
-            const int64_t pe = min(wbase + k * 32 + lane, t1 - 1);
-            ys[k] = __ldg(a.col + pe);
-            if constexpr (kW) ws[k] = a.w ? __ldg(a.w + pe) : 0.f;
+            for (int k = 0; k < CI; ++k) ys[k] = __ldg(cp + k * 32);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CI; ++k) ys[k] = __ldg(a.col + min(wbase + k * 32 + lane, t1 - 1));
+        }
+        if constexpr (kW) {
+#pragma unroll
+            for (int k = 0; k < CI; ++k) ws[k] = a.w ? __ldg(a.w + min(wbase + k * 32 + lane, t1 - 1)) : 0.f;
         }
         if constexpr (kW && Pol::kReweight) {
             if (pol.reweights()) {
@@ -934,16 +999,23 @@ sg_status resolve_mask(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented
                        Graph **out) {
     Graph *h = nullptr;
     CompactScratch cs;
+    uint32_t *delbits = nullptr;
+    const int64_t m1 = std::max<int64_t>(o.m, 1);
     sg_status st = new_graph(c, g->n, g->nnz, g->w != nullptr, &h);
     if (st == SG_OK) st = alloc_compact_scratch(c, rm.num_chunks, true, &cs);
+    if (st == SG_OK) st = dalloc(c, (void **)&delbits, sizeof(uint32_t) * (size_t)((m1 + 31) / 32));
+    if (st == SG_OK && o.m > 0) {
+        SG_LAUNCH(c, "compact_trmask");
+        launch_pack_flags(c->stream, c->num_sms, del, o.m, delbits);
+    }
     if (st == SG_OK) {
-        MaskPol pol{o.fwd_bits, o.fwd_excl, o.inl, del, std::max<int64_t>(g->nnz - o.m, 1),
-                    std::max<int64_t>(o.m, 1)};
+        MaskPol pol{o.fwd_bits, o.fwd_excl, o.inl, delbits, std::max<int64_t>(g->nnz - o.m, 1), m1};
         st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_trmask");
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
     free_compact_scratch(c, &cs);
+    dfree(c, delbits);
     if (st != SG_OK) {
         delete_graph(c, h);
         return st;
@@ -1035,13 +1107,17 @@ sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev
 }
 
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
-                      const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      const CompactScratch &cs, int grid_per_sm) {
+                      const uint8_t *del, uint32_t *delbits, int64_t *off_out, uint32_t *col_out, float *w_in,
+                      float *w_out, const CompactScratch &cs, int grid_per_sm) {
+    if (o.m > 0) {
+        SG_LAUNCH(c, "compact_final");
+        launch_pack_flags(c->stream, c->num_sms, del, o.m, delbits);
+    }
     // the reverse arcs of graphs without a triangle kernel are not in the
     // reverse list (BatchFinalPol decides those arcs itself); the list has room
-    // for every arc of the union, del for its m edges
+    // for every arc of the union, delbits for its m edges
     BatchFinalPol pol{u->off, b,
-                      MaskPol{o.fwd_bits, o.fwd_excl, o.inl, del, std::max<int64_t>(u->nnz, 1),
+                      MaskPol{o.fwd_bits, o.fwd_excl, o.inl, delbits, std::max<int64_t>(u->nnz, 1),
                               std::max<int64_t>(o.m, 1)},
                       o.fwd_bits, o.fwd_excl};
     return run_compact(c, u, rm, pol, w_in, off_out, col_out, w_out, cs, "compact_final", grid_per_sm);

@@ -221,8 +221,8 @@ struct BatchDev {
 sg_status batch_orient(Ctx *c, const Graph *u, const RowMaps &rm, const BatchDev &b, bool weights, Oriented *o,
                        unsigned long long *scan, int grid_per_sm);
 sg_status batch_final(Ctx *c, const Graph *u, const RowMaps &rm, const Oriented &o, const BatchDev &b,
-                      const uint8_t *del, int64_t *off_out, uint32_t *col_out, float *w_in, float *w_out,
-                      const CompactScratch &cs, int grid_per_sm);
+                      const uint8_t *del, uint32_t *delbits, int64_t *off_out, uint32_t *col_out, float *w_in,
+                      float *w_out, const CompactScratch &cs, int grid_per_sm);
 // the reverse list of o (see Oriented::inl) into inl; in a batch only the
 // graphs with a triangle kernel are listed
 sg_status reverse_list(Ctx *c, const Graph *g, const RowMaps &rm, const Oriented &o, uint2 *inl,
