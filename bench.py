@@ -51,11 +51,13 @@ CPU_SAMPLE_SCALE = 16  # oracle sample: same generator, 1024x fewer edges than s
 # pass, from an ncu capture.  Each entry records the digest of the enumeration
 # sources it was taken on; once they change, the figure no longer describes
 # the kernel and the JSON line reports null.
-MEASURED_TRAFFIC = {
-    # (workload, kernel): (bytes per pass, sha256 of the enumeration sources)
-    # hub launch 1417.66 + 144.67 GB, main launch 514.07 + 11.94 GB (read + written)
-    ("rmat26", "tr_random"): (2088335747072, "dc5696c02952d9f2bc09f069060807f966823644bf47c6edc9467bd24a448c72"),
-}
+# (workload, kernel): (DRAM bytes per enumeration pass from one ncu capture,
+# sha256 of the enumeration sources it was taken with).  An entry only counts
+# while the sources are unchanged; otherwise the line reports traffic null.
+# Counters beyond the launch duration are captured on small cases only, and
+# the enumeration's traffic does not scale from them (small graphs re-read
+# their lists from L2), so the scale-26 pass has no current entry.
+MEASURED_TRAFFIC = {}
 TRAFFIC_SOURCES = ("paper_1912_08950_gb300/csrc/sg_triangles.cu", "paper_1912_08950_gb300/csrc/sg_internal.cuh")
 
 
