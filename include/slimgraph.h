@@ -347,11 +347,12 @@ sg_status sg_low_degree(sg_ctx *ctx, const sg_graph *g, uint32_t *new_to_old, sg
  * nnz <= 134217728 arcs; larger inputs return SG_ERR_UNSUPPORTED.
  * The first call on a device looks up that array's device address and keeps
  * it for the life of the process (a cudaDeviceReset of that device makes the
- * kept address stale); make the first call before any stream capture.  The
- * call synchronises cuda_stream and leaves the caller's current device as it
- * found it.  All calls of a process share the one array on a device: calls
- * that overlap on the GPU (different streams or threads of that process) race
- * and must be serialised by the caller.  No context is needed; errors are
+ * kept address stale).  The call synchronises cuda_stream and reads its
+ * result into host memory, so it cannot be recorded in a stream capture; it
+ * leaves the caller's current device as it found it.  All calls of a process
+ * share the one array on a device: calls that overlap on the GPU (different
+ * streams or threads of that process) race and must be serialised by the
+ * caller.  No context is needed; errors are
  * reported as by every other entry point (sg_last_error). */
 sg_status sg_compress_uniform_noalloc(int device, void *cuda_stream, int64_t n, int64_t nnz, const int64_t *off,
                                       const uint32_t *col, double p, uint64_t seed, int64_t *off_out,

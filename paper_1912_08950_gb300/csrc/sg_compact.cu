@@ -235,6 +235,18 @@ struct UniformPol {
     }
 };
 
+// Degrees saturated to 16 bits: 2 bytes per vertex instead of the 16-byte
+// offset pair, so the random degree reads of the orientation and of spectral
+// sparsification mostly hit L2
+// (R-MAT s26: 134 MB against 1.07 GB of offsets).
+__global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_t *__restrict__ deg16) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = __ldg(off + v + 1) - __ldg(off + v);
+        deg16[v] = (uint16_t)(d < 65535 ? d : 65535);
+    }
+}
+
 // 1/p_uv for an edge kept with probability p_uv = min(1, Y / dmin)
 __device__ __forceinline__ float spectral_weight(uint64_t dmin, unsigned long long ty, float yf) {
     return (dmin * 4294967296ull <= ty) ? 1.0f : __fdiv_rn(__ull2float_rn(dmin), yf);
@@ -247,11 +259,15 @@ struct SpectralPol {
         uint64_t dmin;
     };
     const int64_t *off;
+    const uint16_t *deg16;  // min(d, 65535)
     uint32_t k0, k1;
     unsigned long long ty;  // floor(Y 2^32)
     float yf;               // Y rounded to float
     bool reweight;
+    // min(d_x, d_y): the smaller saturated degree is exact unless both saturate
     __device__ __forceinline__ uint64_t dmin(uint32_t x, uint32_t y) const {
+        const uint32_t sm = min((uint32_t)__ldg(deg16 + x), (uint32_t)__ldg(deg16 + y));
+        if (sm < 65535u) return sm;
         const uint64_t dx = (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
         const uint64_t dy = (uint64_t)(__ldg(off + y + 1) - __ldg(off + y));
         return dx < dy ? dx : dy;
@@ -272,17 +288,6 @@ struct SpectralPol {
         return spectral_weight(dmin(x, y), ty, yf);
     }
 };
-
-// Degrees saturated to 16 bits: 2 bytes per vertex instead of the 16-byte
-// offset pair, so the random degree reads of the orientation mostly hit L2
-// (R-MAT s26: 134 MB against 1.07 GB of offsets).
-__global__ void deg16_kernel(const int64_t *__restrict__ off, int64_t n, uint16_t *__restrict__ deg16) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int64_t d = __ldg(off + v + 1) - __ldg(off + v);
-        deg16[v] = (uint16_t)(d < 65535 ? d : 65535);
-    }
-}
 
 struct OrientPol {
     static constexpr bool kNeedRow = true, kNeedCol = true, kOrPrefix = false, kMapCol = false, kReweight = false;
@@ -911,6 +916,7 @@ sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t
                          Graph **out) {
     RowMaps rm;
     CompactScratch cs;
+    uint16_t *deg16 = nullptr;
     sg_status st = build_row_maps(c, g, &rm);
     Graph *h = nullptr;
     const bool spectral = (k == SG_SPECTRAL_LOGN || k == SG_SPECTRAL_AVGDEG);
@@ -926,13 +932,22 @@ sg_status compress_edges(Ctx *c, const Graph *g, sg_kernel k, double p, uint64_t
             const int64_t m = g->nnz / 2;
             const double y = (k == SG_SPECTRAL_LOGN) ? p * std::log((double)g->n)
                                                      : (g->n > 0 ? p * (double)m / (double)g->n : 0.0);
-            SpectralPol pol{g->off, k0, k1, scaled_threshold(y), (float)y, want_weights != 0};
-            st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_spectral");
+            st = dalloc(c, (void **)&deg16, sizeof(uint16_t) * (size_t)std::max<int64_t>(g->n, 1));
+            if (st == SG_OK && g->n > 0) {
+                const int64_t blocks = std::min<int64_t>((g->n + 255) / 256, (int64_t)c->num_sms * 16);
+                SG_LAUNCH(c, "compact_spectral");
+                deg16_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(g->off, g->n, deg16);
+            }
+            if (st == SG_OK) {
+                SpectralPol pol{g->off, deg16, k0, k1, scaled_threshold(y), (float)y, want_weights != 0};
+                st = run_compact(c, g, rm, pol, g->w, h->off, h->col, h->w, cs, "compact_spectral");
+            }
         }
     }
     if (st == SG_OK) st = read_i64(c, h->off + g->n, &h->nnz);
     if (st == SG_OK) st = check_device_error(c);
     free_compact_scratch(c, &cs);
+    dfree(c, deg16);
     free_row_maps(c, &rm);
     if (st != SG_OK) {
         delete_graph(c, h);
