@@ -624,7 +624,7 @@ __global__ void offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64
 constexpr int kRevK = 4;
 static_assert(CI % kRevK == 0, "a warp's slabs lie in one chunk");
 constexpr int kRevWin = 4;
-constexpr int kRevInterp = 6;
+constexpr int kRevInterp = 10;
 
 __global__ void __launch_bounds__(256, 4) reverse_list_kernel(
     const int64_t *__restrict__ off, int64_t n, int64_t nnz, const uint32_t *__restrict__ col,
