@@ -621,12 +621,12 @@ __global__ void offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64
 // probes).  On rows of uniformly spread ids of length 500 / 3000 that reads
 // about 1.9 / 2.4 distinct 32-byte sectors per lookup instead of 6 / 8.5, and
 // those random sectors are the pass's bound.
-constexpr int kRevK = 4;
+constexpr int kRevK = 2;
 static_assert(CI % kRevK == 0, "a warp's slabs lie in one chunk");
 constexpr int kRevWin = 4;
 constexpr int kRevInterp = 10;
 
-__global__ void __launch_bounds__(256, 4) reverse_list_kernel(
+__global__ void __launch_bounds__(256, 5) reverse_list_kernel(
     const int64_t *__restrict__ off, int64_t n, int64_t nnz, const uint32_t *__restrict__ col,
     const uint32_t *__restrict__ chunk_row, const uint32_t *__restrict__ fwd_bits,
     const int64_t *__restrict__ fwd_excl, const int64_t *__restrict__ offp,
