@@ -217,7 +217,7 @@ def byte_model(n, m, A_out, kernel):
         # output CSR
         return 8 * (n + 1) + 4 * A + A / 8 + 2 * m + 8 * m + 8 * (n + 1) + 4 * A_out
     if kernel == "tri_reverse_list":
-        # offsets and columns, forward bits, the orientation's tile prefixes;
+        # offsets and columns, forward bits, the orientation's chunk prefixes;
         # per reverse arc the E+ row bounds of its tail (16 B), the found column
         # (4 B) and its list entry written (8 B)
         return 8 * (n + 1) + 4 * A + A / 8 + 28 * m
