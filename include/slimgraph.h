@@ -162,11 +162,12 @@ sg_status sg_ctx_set_eo_list_capacity(sg_ctx *ctx, int64_t records);
 sg_status sg_ctx_release_workspace(sg_ctx *ctx);
 
 /* Test hook for the SG_ERR_TIMEOUT contract (the paper has no counterpart).
- * With spin_limit > 0, the first tile of every prefix scan the context runs
- * (the CSR rebuild, the orientation, the edge kernels) never publishes its
- * prefix, and a tile waiting on a predecessor gives up after spin_limit
- * polls: the call returns SG_ERR_TIMEOUT, its outputs are invalid, and the
- * context stays usable.  0 (the default) restores normal operation, where
+ * With spin_limit > 0, the first tile of every chunk-count prefix scan the
+ * context runs (in the CSR rebuild, the orientation, the edge kernels) never
+ * publishes its prefix, and a tile waiting on a predecessor gives up after
+ * spin_limit polls; a graph whose scan has a single tile (under about 262,000
+ * arcs) has no wait to give up.  The call returns SG_ERR_TIMEOUT, its outputs
+ * are invalid, and the context stays usable.  0 (the default) restores normal operation, where
  * a wait gives up only after 2^22 polls.
  * Errors: SG_ERR_INVALID_ARG (ctx == NULL). */
 sg_status sg_ctx_set_scan_hold(sg_ctx *ctx, uint32_t spin_limit);
