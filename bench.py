@@ -228,6 +228,22 @@ def byte_model(n, m, A_out, kernel):
     return None
 
 
+def streaming_rows(kt, steps, n, m, A_out, hbm):
+    """Per-call time and roofline of the step's streaming kernels.  kt maps a
+    kernel name to (total ms, launches) over `steps` profiled steps; each step
+    makes one call of each, and a compaction call is several launches (decide,
+    chunk scan, scatter, offsets; the orientation's degree pass) timed together."""
+    rows = {}
+    for name in ("compact_orient", "tri_reverse_list", "compact_trmask"):
+        t, launches = kt.get(name, (0.0, 0))
+        if launches and t > 0:
+            b = byte_model(n, m, A_out, name)
+            per = t / steps
+            rows[name] = {"ms": per, "launches": launches / steps, "algorithmic_bytes": b,
+                          "achieved": b / per / 1e6, "frac": b / per / 1e6 / hbm}
+    return rows
+
+
 KERNEL_NAMES = ("tri_enum", "tri_hubs", "tri_reverse_list", "tri_eo_fresh_reserve", "tri_eo_list_reserve",
                 "tri_eo_list_accept", "tri_eo_accept", "tri_eo_list_reset", "tri_classify", "compact_orient",
                 "compact_trmask", "row_maps")
@@ -358,16 +374,7 @@ def run_ours(args, rank, world):
     pass_s = enum_ms / passes / 1e3
     enum_achieved = enum_bytes / pass_s / 1e9 if pass_s > 0 else None
     streamed_bytes = enum_streamed_bytes(n, m, pst["probes"] / passes)
-    streams = {}
-    for name in ("compact_orient", "tri_reverse_list", "compact_trmask"):
-        # one call per step; a compaction is several launches (decide, chunk
-        # scan, scatter, offsets; the orientation's degree pass), timed together
-        t, launches = kt[name]
-        if launches:
-            b = byte_model(n, m, A_out, name)
-            per = t / psteps
-            streams[name] = {"ms": per, "launches": launches / psteps, "algorithmic_bytes": b,
-                             "achieved": b / per / 1e6, "frac": b / per / 1e6 / hbm}
+    streams = streaming_rows(kt, psteps, n, m, A_out, hbm)
     step_bytes = tr_step_bytes(n, m, A_out, work["forward_probes"])
 
     # ---- other rows of the hot path (not part of the metric)

@@ -44,3 +44,17 @@ def test_measured_traffic_guarded_by_source_digest(monkeypatch):
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("wl", "k"), (123, "0" * 64))
     assert bench.measured_traffic("wl", "k") is None
     assert bench.measured_traffic("no such workload", "k") is None
+
+
+def test_streaming_rows_are_per_call():
+    n, m, a_out, hbm = 1000, 8000, 9000, 6668.5
+    # two profiled steps; the orientation is five launches per call
+    kt = {"compact_orient": (4.0, 10), "tri_reverse_list": (6.0, 2), "compact_trmask": (0.0, 0)}
+    rows = bench.streaming_rows(kt, 2, n, m, a_out, hbm)
+    assert set(rows) == {"compact_orient", "tri_reverse_list"}
+    o = rows["compact_orient"]
+    assert o["ms"] == 2.0 and o["launches"] == 5.0
+    b = bench.byte_model(n, m, a_out, "compact_orient")
+    assert o["algorithmic_bytes"] == b
+    assert abs(o["achieved"] - b / 2.0 / 1e6) < 1e-9 and abs(o["frac"] - b / 2.0 / 1e6 / hbm) < 1e-12
+    assert rows["tri_reverse_list"]["ms"] == 3.0 and rows["tri_reverse_list"]["launches"] == 1.0
